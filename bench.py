@@ -1,0 +1,330 @@
+"""Benchmark: batched 3D C2C FFT throughput (transforms/s) and fraction of
+the HBM roofline on one GB300, plus end-to-end throughput with host buffers
+and the FP64 oracle timed on the host cores.
+
+Step = one forward 3D FFT (Eq. 1, FP32) of a batch of complex64 grids
+already resident in HBM (default 128^3 x 32 = 537 MB in, 537 MB out, larger
+than L2, so no flush is needed between steps).  Roofline bytes per
+transform = 16 * N^3 (one read and one write of the grid).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload 128x32|64x256]
+
+Under torchrun each rank transforms its own batch (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "128x32": (128, 32),
+    "64x256": (64, 256),
+}
+METRIC = "batched 3D FFT transforms/s and % of HBM roofline at 64^3/128^3 (FP32 vs split-FP16)"
+KERNEL_SOURCES = ["paper_2006_08435_gb300/csrc/persistent.cuh",
+                  "paper_2006_08435_gb300/csrc/codelets.cuh",
+                  "paper_2006_08435_gb300/csrc/sizes.h"]
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(n: int, batch: int):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", f"fused_fft3d_n{n}_traffic.txt")
+    try:
+        kv = {}
+        for line in open(path):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("kernel_source_sha256_16") != kernel_source_hash():
+            return None
+        per_grid = float(kv["dram_bytes_per_grid"])
+        return per_grid * batch
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(n: int, budget_s: float = 12.0):
+    """The FP64 oracle, as it stands, on one n^3 grid of the workload,
+    repeated until about `budget_s` seconds of CPU work."""
+    import numpy as np
+    from oracle import oracle
+    from paper_2006_08435_gb300 import synth
+    x = synth.gaussian_sum_grids(n, 1, seed=0).astype(np.complex128)
+    oracle.dft3d(x[:, :8, :8, :8])         # load / build outside the timing
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.dft3d(x)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or reps >= 50:
+            break
+    return {"value": reps / el, "unit": "transforms/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"{reps} forward transform(s) of one {n}^3 grid of the workload "
+                      f"(FP64 separable direct DFT, {el:.1f} s)"}
+
+
+def run_reference(args, ws, rank):
+    n, batch = WORKLOADS[args.workload]
+    if rank != 0:
+        return 0
+    import numpy as np
+    from oracle import oracle
+    from paper_2006_08435_gb300 import synth
+    x = synth.gaussian_sum_grids(n, 1, seed=0).astype(np.complex128)
+    oracle.dft3d(x[:, :8, :8, :8])
+    for _ in range(args.warmup):
+        oracle.dft3d(x)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.dft3d(x)
+    el = time.perf_counter() - t0
+    value = args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "transforms/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"fft3d_c2c_fwd_{n}cubed_batch{batch}", "n": n, "batch": batch,
+                   "note": "each step is one grid of the batch (bounded sample)"},
+        "cpu_baseline": {"value": value, "unit": "transforms/s", "cores": oracle.num_threads(),
+                         "kind": "oracle",
+                         "sample": f"one {n}^3 grid per step, FP64 separable direct DFT"},
+        "e2e": {"value": value, "unit": "transforms/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_2006_08435_gb300 import Plan, synth
+    from paper_2006_08435_gb300 import build as B
+
+    n, batch = WORKLOADS[args.workload]
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    B.build()
+
+    # seeded Gaussian-sum inputs; distinct grids from one generated grid set
+    base = synth.gaussian_sum_grids(n, min(batch, 4), seed=rank)
+    xb = torch.from_numpy(base).to(dev)
+    reps = (batch + xb.shape[0] - 1) // xb.shape[0]
+    x = xb.repeat(reps, 1, 1, 1)[:batch].contiguous()
+    ph = torch.exp(1j * 0.37 * torch.arange(batch, device=dev, dtype=torch.float32))
+    x = (x * ph.view(-1, 1, 1, 1).to(torch.complex64)).contiguous()
+    y = torch.empty_like(x)
+    plan = Plan(n, n, n, batch)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    warmup = max(args.warmup, 3)
+    for _ in range(warmup):
+        plan.execute(x, y, stream)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    t_all0 = torch.cuda.Event(enable_timing=True)
+    t_all1 = torch.cuda.Event(enable_timing=True)
+    t_all0.record(stream)
+    for i in range(args.steps):
+        starts[i].record(stream)
+        plan.execute(x, y, stream)
+        ends[i].record(stream)
+    t_all1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    total_ms = t_all0.elapsed_time(t_all1)
+    launch_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = ws * batch * args.steps / (total_ms / 1e3)
+    assert plan.device_status() == 0, "device-side wait timed out"
+
+    # end to end through the public API with pinned host buffers
+    hx = x.cpu().pin_memory()
+    hy = torch.empty_like(hx).pin_memory()
+    e_steps = max(2, min(args.steps, 5))
+    for _ in range(2):
+        x.copy_(hx, non_blocking=True)
+        plan.execute(x, y, stream)
+        hy.copy_(y, non_blocking=True)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e_steps):
+        x.copy_(hx, non_blocking=True)
+        plan.execute(x, y, stream)
+        hy.copy_(y, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1) / e_steps
+    if ws > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": ws * batch / (e2e_ms / 1e3), "unit": "transforms/s",
+           "h2d_bytes_per_step": hx.numel() * hx.element_size(),
+           "d2h_bytes_per_step": hy.numel() * hy.element_size()}
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+    peak, peak_kind = measured_peaks()
+    bytes_per_launch = 16.0 * n ** 3 * batch
+    avg_launch_ms = statistics.mean(launch_ms)
+    achieved = bytes_per_launch / (avg_launch_ms / 1e3) / 1e9
+    traffic = recorded_traffic(n, batch)
+    line = {
+        "metric": METRIC, "value": value, "unit": "transforms/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded Gaussian-sum complex64 grids)",
+        "config": {"workload": f"fft3d_c2c_fwd_fp32_{n}cubed_batch{batch}", "n": n,
+                   "batch_per_gpu": batch, "precision": "fp32", "direction": "forward",
+                   "parallelism": f"replicas{ws}", "l2": "inputs larger than L2 (no flush)",
+                   "gflops_nominal": value * 5 * n ** 3 * 3 * math.log2(n) / 1e9},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": f"{peak_kind} hbm_gbs",
+                     "kernel": "fused_fft3d_kernel", "bytes_per_launch": bytes_per_launch,
+                     "avg_launch_ms": avg_launch_ms},
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "clocks": clk,
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(n)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="128x32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+    return run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

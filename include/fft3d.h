@@ -1,0 +1,174 @@
+/*
+ * fft3d.h -- C ABI of the GB300 (sm_103a) 3D complex-to-complex FFT library.
+ *
+ * The operation (the paper, section "Approach", Eq. 1):
+ *
+ *   F(kx,ky,kz) = sum_{z<nz} sum_{y<ny} sum_{x<nx}
+ *                   f(x,y,z) * W_nx^(x*kx) * W_ny^(y*ky) * W_nz^(z*kz),
+ *   W_n = exp(s * 2*pi*i / n),  s = -1 (FFT3D_FORWARD) or +1 (FFT3D_INVERSE),
+ *
+ * computed, as the same section decomposes it, as 1D FFTs along x, then y,
+ * then z.  Eq. 1 prints per-axis roots W_x, W_y, W_z; each axis uses the root
+ * of its own length.
+ *
+ * Data layout (every entry point): interleaved single-precision complex
+ * (re, im float pairs, 8 bytes per point), index ((b*nz + z)*ny + y)*nx + x,
+ * x fastest, grids of one batch packed back to back.  Natural order on input
+ * and output (the paper's FPGA pipeline streams bit-reversed data
+ * internally; that ordering never reaches this interface).
+ *
+ * Pointers: `in`/`out` are DEVICE pointers owned by the caller, 16-byte
+ * aligned, valid for the whole grid set.  `in == out` (in place) is allowed;
+ * other overlaps are not.  A plan owns the device memory it allocates at
+ * create (twiddle tables, schedule, work counters, status word) and frees it
+ * at destroy.  `stream` is a cudaStream_t passed as void* (NULL = legacy
+ * default stream).
+ *
+ * Errors: every function returns 0 on success or one of the negative
+ * FFT3D_ERR_* codes below; no C++ exception crosses this boundary.  Execute
+ * calls are asynchronous: a device-side failure (a bounded wait that ran
+ * out) is recorded in the plan's status word and reported by
+ * fft3d_get_device_status.
+ *
+ * Threads: a plan may be executed from one stream at a time; executes that
+ * overlap on the device on different streams share the plan's work counters
+ * and race.  Different plans are independent.
+ */
+#ifndef FFT3D_H
+#define FFT3D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fft3d_plan_s* fft3d_plan;
+
+/* Arithmetic of the butterflies.  Input/output stay complex64 in all. */
+typedef enum {
+  FFT3D_FP32 = 0,        /* plain single precision (the paper's FP64->FP32 step, Abstract/Results) */
+  FFT3D_SPLIT_FP16 = 1,  /* radix-16 stages on tensor cores, hi+lo FP16 operands, FP32 accumulate */
+  FFT3D_SPLIT_BF16 = 2,  /* same with BF16 hi+lo operands */
+  FFT3D_FP16 = 3         /* radix-16 stages on tensor cores, FP16 hi only (reported, not gated) */
+} fft3d_precision;
+
+/* Sign of the exponent of W (Eq. 1 uses -1). */
+typedef enum { FFT3D_FORWARD = -1, FFT3D_INVERSE = 1 } fft3d_direction;
+
+/* Output scaling: none, 1/(nx*ny*nz), or 1/sqrt(nx*ny*nz). */
+typedef enum { FFT3D_NORM_NONE = 0, FFT3D_NORM_BY_N = 1, FFT3D_NORM_ORTHO = 2 } fft3d_norm;
+
+enum {
+  FFT3D_SUCCESS = 0,
+  FFT3D_ERR_INVALID_ARG = -1,      /* a count, enum or plan handle is out of range */
+  FFT3D_ERR_UNSUPPORTED_SIZE = -2, /* an edge this build does not plan (see fft3d_size_supported) */
+  FFT3D_ERR_NULL_PTR = -3,         /* a required pointer is NULL */
+  FFT3D_ERR_MISALIGNED = -4,       /* a data pointer is not 16-byte aligned */
+  FFT3D_ERR_CUDA = -5,             /* a CUDA runtime call or kernel launch failed */
+  FFT3D_ERR_DEVICE_TIMEOUT = -6,   /* a bounded device-side wait ran out (status word) */
+  FFT3D_ERR_ALLOC = -7,            /* device or host allocation failed at plan create */
+  FFT3D_ERR_NO_DEVICE = -8,        /* no CUDA device, or not compute capability 10.3 */
+  FFT3D_ERR_UNSUPPORTED_PRECISION = -9 /* precision not available for this plan's sizes */
+};
+
+/* Largest number of grids in one mixed plan. */
+#define FFT3D_MAX_MIXED_GRIDS 4096
+
+/*
+ * 1 if an edge length n can be planned on every axis, else 0.  Host only,
+ * needs no GPU.  Supported: n in {2,...,128} whose prime factors are 2, 3
+ * and 5 and which splits as n = L1*L2 with L1, L2 <= 16 (all configs use
+ * 16, 32, 48, 64, 80, 96, 128).
+ */
+int fft3d_size_supported(int n);
+
+/*
+ * Host-only view of the planner's split and twiddle table for edge n (needs
+ * no GPU).  *l1, *l2 receive the split n = L1*L2 of the four-step 1D
+ * transform; out[2*(k2*L1 + n1)] and out[2*(k2*L1 + n1) + 1] receive re and
+ * im of W_n^(n1*k2) = exp(-2 pi i ((n1*k2) mod n) / n), evaluated in FP64 by
+ * the host math library and rounded to nearest FP32 (the table the kernels
+ * use).  `out` holds 2*n floats.  Returns FFT3D_ERR_UNSUPPORTED_SIZE for an
+ * edge without a fused kernel.
+ */
+int fft3d_twiddle_table(int n, float* out, int* l1, int* l2);
+
+/*
+ * Plan `batch` grids of nx*ny*nz points (Eq. 1 per grid).
+ *   nx, ny, nz : edge lengths, each fft3d_size_supported.
+ *   batch      : number of grids, >= 1, packed back to back.
+ *   precision  : fft3d_precision; the split/FP16 forms need cubic grids whose
+ *                edge is a multiple of 16.
+ *   direction  : FFT3D_FORWARD or FFT3D_INVERSE.
+ *   norm       : fft3d_norm.
+ *   out_plan   : receives the handle (set to NULL on failure).
+ * Validates every argument BEFORE touching the GPU, so argument errors are
+ * reported on machines without one.  Allocates the plan's device buffers on
+ * the current device; the plan must be executed on that device.
+ */
+int fft3d_plan_create(int nx, int ny, int nz, int batch, int precision,
+                      int direction, int norm, fft3d_plan* out_plan);
+
+/*
+ * Plan `count` cubic grids of different edges dims[g] (g < count) that are
+ * transformed together in one persistent launch (mixed radix 2/3/5).
+ *   count : 1..FFT3D_MAX_MIXED_GRIDS.
+ *   dims  : HOST array of `count` edge lengths.
+ * Grid g's points live at element offset fft3d_plan_grid_offset(plan, g)
+ * of the packed buffers given to fft3d_execute, or at the pointers given to
+ * fft3d_execute_mixed.  precision must be FFT3D_FP32.
+ */
+int fft3d_plan_create_mixed(int count, const int* dims, int precision,
+                            int direction, int norm, fft3d_plan* out_plan);
+
+/* Element offset (in complex points) of grid g inside the packed buffers,
+ * written to *offset.  Total packed size for g == count. */
+int fft3d_plan_grid_offset(fft3d_plan plan, int g, int64_t* offset);
+
+/*
+ * Transform all grids of the plan: out = F(in) (scaled per norm).
+ *   in, out : device pointers to the packed grids (see layout above).
+ *   stream  : cudaStream_t or NULL.
+ * Asynchronous, allocates nothing, never synchronises, and is capturable in
+ * a CUDA graph (one memset node plus kernel nodes).
+ */
+int fft3d_execute(fft3d_plan plan, const void* in, void* out, void* stream);
+
+/*
+ * Mixed plans only: like fft3d_execute, but grid g is read from in_ptrs[g]
+ * and written to out_ptrs[g].  `in_ptrs` and `out_ptrs` are DEVICE arrays of
+ * `count` device pointers that must stay valid until the launch completes.
+ */
+int fft3d_execute_mixed(fft3d_plan plan, const void* const* in_ptrs,
+                        void* const* out_ptrs, void* stream);
+
+/*
+ * Synchronise `stream`, then read and clear the plan's device status word.
+ * Returns FFT3D_SUCCESS, FFT3D_ERR_DEVICE_TIMEOUT (a bounded inter-block
+ * wait ran out; the affected outputs are undefined) or FFT3D_ERR_CUDA.
+ */
+int fft3d_get_device_status(fft3d_plan plan, void* stream);
+
+/* Release the plan's device memory.  NULL is accepted. */
+int fft3d_plan_destroy(fft3d_plan plan);
+
+/* Static English description of an error code. */
+const char* fft3d_error_string(int code);
+
+/*
+ * Launch one block that waits on a flag nobody sets, with the same bounded
+ * wait the persistent kernel uses between its passes, and return what that
+ * wait reports: FFT3D_ERR_DEVICE_TIMEOUT when the wait gave up after
+ * `timeout_ns` (the expected result), FFT3D_SUCCESS if the flag was seen.
+ * Synchronises the device.  Exists so the timeout path can be tested without
+ * hanging or faulting the GPU.
+ */
+int fft3d_selftest_wait_timeout(int64_t timeout_ns);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FFT3D_H */

@@ -1,0 +1,63 @@
+// Host/device structures shared by the planner (plan.cu) and the kernel
+// translation units.  Not part of the public C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fft3d {
+
+// Device status word values (sticky until read by fft3d_get_device_status).
+constexpr unsigned kStatusOk = 0u;
+constexpr unsigned kStatusTimeout = 1u;
+
+// Default limit of one inter-block wait (nanoseconds of %globaltimer).
+constexpr long long kDefaultWaitNs = 2000000000LL;
+
+// One run of consecutive work items: all plane items (phase 0: x then y
+// transform of plane z = i) or all slab items (phase 1: z transform of the
+// slab y = i) of one grid.  Items [start, start + n) of the global ticket
+// sequence, i = ticket - start.
+struct SchedBlock {
+  int grid;
+  int phase;
+  int start;
+  int n;  // edge of that grid (cubic), also the number of items
+};
+
+struct FusedArgs {
+  const float2* in;             // packed input base (unused when in_ptrs)
+  float2* out;                  // packed output base (unused when out_ptrs)
+  const float2* const* in_ptrs; // device array of per-grid inputs, or null
+  float2* const* out_ptrs;      // device array of per-grid outputs, or null
+  const long long* grid_off;    // per-grid element offsets, or null (g * n^3)
+  const SchedBlock* blocks;
+  int nblocks;
+  int total_items;
+  const float2* twiddles;       // concatenated tables in kernel size order
+  unsigned* work;               // [0] ticket, [1 + g] plane items done for grid g
+  unsigned* status;             // sticky status word
+  float scale;                  // output scale of the last pass
+  int do_scale;
+  long long timeout_ns;
+};
+
+using LaunchFn = cudaError_t (*)(const FusedArgs&, int grid, cudaStream_t);
+
+struct KernelInfo {
+  LaunchFn launch = nullptr;
+  const void* func = nullptr;   // for occupancy / attributes
+  int threads = 0;
+  size_t smem = 0;              // dynamic shared memory bytes
+  int twiddle_entries = 0;      // complex entries in the concatenated table
+  int sizes[8] = {0};           // edges handled, in table order
+  int nsizes = 0;
+};
+
+// Defined in the inst_*.cu translation units.
+KernelInfo fused_kernel_info(int n, int dir);   // single-size kernel
+KernelInfo mixed_kernel_info(int dir);          // all fused sizes
+cudaError_t launch_wait_selftest(unsigned* flag, unsigned* status, long long timeout_ns,
+                                 cudaStream_t stream);
+
+}  // namespace fft3d

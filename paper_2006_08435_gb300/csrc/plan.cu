@@ -1,0 +1,426 @@
+// Host side of the C ABI: argument validation, planning (size split,
+// FP64 twiddle tables rounded to FP32, work schedule), device buffers and
+// launches.  See include/fft3d.h for the contract of each entry point.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/fft3d.h"
+#include "internal.h"
+#include "sizes.h"
+
+namespace fft3d {
+
+KernelInfo fused_kernel_info_n16(int dir);
+KernelInfo fused_kernel_info_n32(int dir);
+KernelInfo fused_kernel_info_n48(int dir);
+KernelInfo fused_kernel_info_n64(int dir);
+KernelInfo fused_kernel_info_n80(int dir);
+KernelInfo fused_kernel_info_n96(int dir);
+KernelInfo fused_kernel_info_n128(int dir);
+
+KernelInfo fused_kernel_info(int n, int dir) {
+  switch (n) {
+    case 16: return fused_kernel_info_n16(dir);
+    case 32: return fused_kernel_info_n32(dir);
+    case 48: return fused_kernel_info_n48(dir);
+    case 64: return fused_kernel_info_n64(dir);
+    case 80: return fused_kernel_info_n80(dir);
+    case 96: return fused_kernel_info_n96(dir);
+    case 128: return fused_kernel_info_n128(dir);
+    default: return KernelInfo{};
+  }
+}
+
+// W_n^m = exp(-2 pi i m / n) for the table entry (n1, k2) of edge n:
+// tw[k2 * L1 + n1] = W_n^((n1 * k2) mod n), evaluated in FP64 by the host
+// math library on the reduced exponent and rounded to nearest FP32.
+static void twiddle_table(int n, float* out /* 2 * n floats */) {
+  const int l1 = split_l1(n), l2 = split_l2(n);
+  for (int k2 = 0; k2 < l2; ++k2)
+    for (int n1 = 0; n1 < l1; ++n1) {
+      const int m = (n1 * k2) % n;
+      const double a = 2.0 * 3.14159265358979323846 * (double)m / (double)n;
+      out[2 * (k2 * l1 + n1)] = (float)std::cos(a);
+      out[2 * (k2 * l1 + n1) + 1] = (float)(-std::sin(a));
+    }
+}
+
+static bool fused_size(int n) { return fused_slot(n) >= 0; }
+
+}  // namespace fft3d
+
+using namespace fft3d;
+
+struct fft3d_plan_s {
+  int device = -1;
+  int nx = 0, ny = 0, nz = 0, batch = 0;
+  int precision = 0, direction = -1, norm = 0;
+  bool mixed = false;
+  std::vector<int> dims;             // per-grid edge
+  std::vector<long long> offsets;    // per-grid element offset in packed buffers
+  long long total_points = 0;
+  KernelInfo kernel;
+  int grid = 0;                      // persistent blocks launched
+  int total_items = 0;
+  int nblocks = 0;
+  float scale = 1.0f;
+  int do_scale = 0;
+  long long timeout_ns = kDefaultWaitNs;
+  // device buffers (owned)
+  float2* d_tw = nullptr;
+  SchedBlock* d_blocks = nullptr;
+  long long* d_off = nullptr;
+  unsigned* d_work = nullptr;
+  size_t work_bytes = 0;
+  unsigned* d_status = nullptr;
+};
+
+namespace {
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+void free_plan_buffers(fft3d_plan p) {
+  if (!p) return;
+  cudaFree(p->d_tw);
+  cudaFree(p->d_blocks);
+  cudaFree(p->d_off);
+  cudaFree(p->d_work);
+  cudaFree(p->d_status);
+  p->d_tw = nullptr;
+  p->d_blocks = nullptr;
+  p->d_off = nullptr;
+  p->d_work = nullptr;
+  p->d_status = nullptr;
+}
+
+int check_device() {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return FFT3D_ERR_NO_DEVICE;
+  }
+  int major = 0, minor = 0;
+  if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return FFT3D_ERR_NO_DEVICE;
+  }
+  if (major != 10 || minor != 3) return FFT3D_ERR_NO_DEVICE;
+  return FFT3D_SUCCESS;
+}
+
+// Ticket order: planes of grid 0, then for each later grid its planes
+// followed by the slabs of the grid before it, then the slabs of the last
+// grid.  `order` lists grids in scheduling order.
+std::vector<SchedBlock> build_schedule(const std::vector<int>& dims, const std::vector<int>& order,
+                                       int* total_items) {
+  std::vector<SchedBlock> blocks;
+  int start = 0;
+  auto push = [&](int g, int phase) {
+    blocks.push_back(SchedBlock{g, phase, start, dims[g]});
+    start += dims[g];
+  };
+  const int count = (int)order.size();
+  for (int j = 0; j < count; ++j) {
+    push(order[j], 0);
+    if (j >= 1) push(order[j - 1], 1);
+  }
+  push(order[count - 1], 1);
+  *total_items = start;
+  return blocks;
+}
+
+int finish_plan(fft3d_plan p, const std::vector<int>& order) {
+  cudaError_t e;
+  // kernel attributes and persistent grid size
+  e = cudaFuncSetAttribute(p->kernel.func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)p->kernel.smem);
+  if (e != cudaSuccess) return FFT3D_ERR_CUDA;
+  int per_sm = 0, sms = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p->kernel.func, p->kernel.threads,
+                                                    p->kernel.smem);
+  if (e != cudaSuccess || per_sm < 1) return FFT3D_ERR_CUDA;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+  if (e != cudaSuccess) return FFT3D_ERR_CUDA;
+
+  int total_items = 0;
+  std::vector<SchedBlock> blocks = build_schedule(p->dims, order, &total_items);
+  p->total_items = total_items;
+  p->nblocks = (int)blocks.size();
+  p->grid = std::max(1, std::min(total_items, per_sm * sms));
+
+  // twiddles for every edge the kernel handles, concatenated in its order
+  std::vector<float> tw(2 * (size_t)p->kernel.twiddle_entries);
+  size_t off = 0;
+  for (int i = 0; i < p->kernel.nsizes; ++i) {
+    twiddle_table(p->kernel.sizes[i], tw.data() + 2 * off);
+    off += p->kernel.sizes[i];
+  }
+  const int count = (int)p->dims.size();
+  p->work_bytes = sizeof(unsigned) * (size_t)(1 + count);
+  if (cudaMalloc(&p->d_tw, tw.size() * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&p->d_blocks, blocks.size() * sizeof(SchedBlock)) != cudaSuccess ||
+      cudaMalloc(&p->d_work, p->work_bytes) != cudaSuccess ||
+      cudaMalloc(&p->d_status, sizeof(unsigned)) != cudaSuccess) {
+    cudaGetLastError();
+    return FFT3D_ERR_ALLOC;
+  }
+  if (p->mixed) {
+    if (cudaMalloc(&p->d_off, sizeof(long long) * (size_t)count) != cudaSuccess) {
+      cudaGetLastError();
+      return FFT3D_ERR_ALLOC;
+    }
+    if (cudaMemcpy(p->d_off, p->offsets.data(), sizeof(long long) * (size_t)count,
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+      return FFT3D_ERR_CUDA;
+  }
+  if (cudaMemcpy(p->d_tw, tw.data(), tw.size() * sizeof(float), cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaMemcpy(p->d_blocks, blocks.data(), blocks.size() * sizeof(SchedBlock),
+                 cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(p->d_work, 0, p->work_bytes) != cudaSuccess ||
+      cudaMemset(p->d_status, 0, sizeof(unsigned)) != cudaSuccess)
+    return FFT3D_ERR_CUDA;
+  return FFT3D_SUCCESS;
+}
+
+void set_scale(fft3d_plan p, double points) {
+  if (p->norm == FFT3D_NORM_BY_N) {
+    p->scale = (float)(1.0 / points);
+    p->do_scale = 1;
+  } else if (p->norm == FFT3D_NORM_ORTHO) {
+    p->scale = (float)(1.0 / std::sqrt(points));
+    p->do_scale = 1;
+  }
+}
+
+int validate_common(int precision, int direction, int norm, fft3d_plan* out_plan) {
+  if (!out_plan) return FFT3D_ERR_NULL_PTR;
+  *out_plan = nullptr;
+  if (precision < FFT3D_FP32 || precision > FFT3D_FP16) return FFT3D_ERR_INVALID_ARG;
+  if (direction != FFT3D_FORWARD && direction != FFT3D_INVERSE) return FFT3D_ERR_INVALID_ARG;
+  if (norm < FFT3D_NORM_NONE || norm > FFT3D_NORM_ORTHO) return FFT3D_ERR_INVALID_ARG;
+  return FFT3D_SUCCESS;
+}
+
+int launch(fft3d_plan p, const float2* in, float2* out, const float2* const* in_ptrs,
+           float2* const* out_ptrs, cudaStream_t stream) {
+  if (cudaMemsetAsync(p->d_work, 0, p->work_bytes, stream) != cudaSuccess) {
+    cudaGetLastError();
+    return FFT3D_ERR_CUDA;
+  }
+  FusedArgs a{};
+  a.in = in;
+  a.out = out;
+  a.in_ptrs = in_ptrs;
+  a.out_ptrs = out_ptrs;
+  a.grid_off = p->d_off;
+  a.blocks = p->d_blocks;
+  a.nblocks = p->nblocks;
+  a.total_items = p->total_items;
+  a.twiddles = p->d_tw;
+  a.work = p->d_work;
+  a.status = p->d_status;
+  a.scale = p->scale;
+  a.do_scale = p->do_scale;
+  a.timeout_ns = p->timeout_ns;
+  if (p->kernel.launch(a, p->grid, stream) != cudaSuccess) {
+    cudaGetLastError();
+    return FFT3D_ERR_CUDA;
+  }
+  return FFT3D_SUCCESS;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fft3d_size_supported(int n) { return fused_size(n) ? 1 : 0; }
+
+int fft3d_twiddle_table(int n, float* out, int* l1, int* l2) {
+  if (!out || !l1 || !l2) return FFT3D_ERR_NULL_PTR;
+  if (!fused_size(n)) return FFT3D_ERR_UNSUPPORTED_SIZE;
+  twiddle_table(n, out);
+  *l1 = split_l1(n);
+  *l2 = split_l2(n);
+  return FFT3D_SUCCESS;
+}
+
+int fft3d_plan_create(int nx, int ny, int nz, int batch, int precision, int direction, int norm,
+                      fft3d_plan* out_plan) {
+  int rc = validate_common(precision, direction, norm, out_plan);
+  if (rc) return rc;
+  if (nx < 1 || ny < 1 || nz < 1 || batch < 1) return FFT3D_ERR_INVALID_ARG;
+  if (batch > (1 << 24)) return FFT3D_ERR_INVALID_ARG;
+  if (!fused_size(nx) || nx != ny || ny != nz) return FFT3D_ERR_UNSUPPORTED_SIZE;
+  if (precision != FFT3D_FP32) return FFT3D_ERR_UNSUPPORTED_PRECISION;
+  const long long pts = (long long)nx * ny * nz;
+  // ticket counters are 32-bit: 2 * n items per grid
+  if ((long long)batch * 2 * nx >= (1LL << 31)) return FFT3D_ERR_INVALID_ARG;
+  if ((rc = check_device())) return rc;
+
+  fft3d_plan p = new (std::nothrow) fft3d_plan_s();
+  if (!p) return FFT3D_ERR_ALLOC;
+  cudaGetDevice(&p->device);
+  p->nx = nx; p->ny = ny; p->nz = nz; p->batch = batch;
+  p->precision = precision; p->direction = direction; p->norm = norm;
+  p->dims.assign(batch, nx);
+  p->offsets.resize(batch);
+  for (int g = 0; g < batch; ++g) p->offsets[g] = (long long)g * pts;
+  p->total_points = pts * batch;
+  set_scale(p, (double)pts);
+  p->kernel = fused_kernel_info(nx, direction);
+  std::vector<int> order(batch);
+  for (int g = 0; g < batch; ++g) order[g] = g;
+  rc = finish_plan(p, order);
+  if (rc) {
+    free_plan_buffers(p);
+    delete p;
+    return rc;
+  }
+  *out_plan = p;
+  return FFT3D_SUCCESS;
+}
+
+int fft3d_plan_create_mixed(int count, const int* dims, int precision, int direction, int norm,
+                            fft3d_plan* out_plan) {
+  int rc = validate_common(precision, direction, norm, out_plan);
+  if (rc) return rc;
+  if (!dims) return FFT3D_ERR_NULL_PTR;
+  if (count < 1 || count > FFT3D_MAX_MIXED_GRIDS) return FFT3D_ERR_INVALID_ARG;
+  long long items = 0;
+  for (int g = 0; g < count; ++g) {
+    if (dims[g] < 1) return FFT3D_ERR_INVALID_ARG;
+    if (!fused_size(dims[g])) return FFT3D_ERR_UNSUPPORTED_SIZE;
+    items += 2LL * dims[g];
+  }
+  if (items >= (1LL << 31)) return FFT3D_ERR_INVALID_ARG;
+  if (precision != FFT3D_FP32) return FFT3D_ERR_UNSUPPORTED_PRECISION;
+  if ((rc = check_device())) return rc;
+
+  fft3d_plan p = new (std::nothrow) fft3d_plan_s();
+  if (!p) return FFT3D_ERR_ALLOC;
+  cudaGetDevice(&p->device);
+  p->mixed = true;
+  p->batch = count;
+  p->precision = precision; p->direction = direction; p->norm = norm;
+  p->dims.assign(dims, dims + count);
+  p->offsets.resize(count);
+  long long off = 0;
+  for (int g = 0; g < count; ++g) {
+    p->offsets[g] = off;
+    off += (long long)dims[g] * dims[g] * dims[g];
+  }
+  p->total_points = off;
+  p->kernel = mixed_kernel_info(direction);
+  // the scale of each grid differs; a mixed plan applies NORM per grid by
+  // its own edge, which the single scale argument cannot express
+  if (norm != FFT3D_NORM_NONE) {
+    bool same = std::all_of(p->dims.begin(), p->dims.end(), [&](int d) { return d == p->dims[0]; });
+    if (!same) {
+      delete p;
+      return FFT3D_ERR_INVALID_ARG;
+    }
+    set_scale(p, (double)p->dims[0] * p->dims[0] * p->dims[0]);
+  }
+  // largest grids first: the tail of the launch is made of small items
+  std::vector<int> order(count);
+  for (int g = 0; g < count; ++g) order[g] = g;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return dims[a] > dims[b]; });
+  rc = finish_plan(p, order);
+  if (rc) {
+    free_plan_buffers(p);
+    delete p;
+    return rc;
+  }
+  *out_plan = p;
+  return FFT3D_SUCCESS;
+}
+
+int fft3d_plan_grid_offset(fft3d_plan plan, int g, int64_t* offset) {
+  if (!plan || !offset) return FFT3D_ERR_NULL_PTR;
+  const int count = (int)plan->dims.size();
+  if (g < 0 || g > count) return FFT3D_ERR_INVALID_ARG;
+  *offset = g == count ? plan->total_points : plan->offsets[g];
+  return FFT3D_SUCCESS;
+}
+
+int fft3d_execute(fft3d_plan plan, const void* in, void* out, void* stream) {
+  if (!plan || !in || !out) return FFT3D_ERR_NULL_PTR;
+  if (!aligned16(in) || !aligned16(out)) return FFT3D_ERR_MISALIGNED;
+  return launch(plan, static_cast<const float2*>(in), static_cast<float2*>(out), nullptr, nullptr,
+                static_cast<cudaStream_t>(stream));
+}
+
+int fft3d_execute_mixed(fft3d_plan plan, const void* const* in_ptrs, void* const* out_ptrs,
+                        void* stream) {
+  if (!plan || !in_ptrs || !out_ptrs) return FFT3D_ERR_NULL_PTR;
+  if (!plan->mixed) return FFT3D_ERR_INVALID_ARG;
+  return launch(plan, nullptr, nullptr, reinterpret_cast<const float2* const*>(in_ptrs),
+                reinterpret_cast<float2* const*>(out_ptrs), static_cast<cudaStream_t>(stream));
+}
+
+int fft3d_get_device_status(fft3d_plan plan, void* stream) {
+  if (!plan) return FFT3D_ERR_NULL_PTR;
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+    cudaGetLastError();
+    return FFT3D_ERR_CUDA;
+  }
+  unsigned s = 0;
+  if (cudaMemcpy(&s, plan->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemset(plan->d_status, 0, sizeof(unsigned)) != cudaSuccess)
+    return FFT3D_ERR_CUDA;
+  return s == kStatusOk ? FFT3D_SUCCESS : FFT3D_ERR_DEVICE_TIMEOUT;
+}
+
+int fft3d_plan_destroy(fft3d_plan plan) {
+  if (!plan) return FFT3D_SUCCESS;
+  free_plan_buffers(plan);
+  delete plan;
+  return FFT3D_SUCCESS;
+}
+
+const char* fft3d_error_string(int code) {
+  switch (code) {
+    case FFT3D_SUCCESS: return "success";
+    case FFT3D_ERR_INVALID_ARG: return "invalid argument";
+    case FFT3D_ERR_UNSUPPORTED_SIZE: return "unsupported grid size";
+    case FFT3D_ERR_NULL_PTR: return "null pointer";
+    case FFT3D_ERR_MISALIGNED: return "data pointer not 16-byte aligned";
+    case FFT3D_ERR_CUDA: return "CUDA runtime error";
+    case FFT3D_ERR_DEVICE_TIMEOUT: return "bounded device-side wait timed out";
+    case FFT3D_ERR_ALLOC: return "allocation failed";
+    case FFT3D_ERR_NO_DEVICE: return "no compute capability 10.3 device";
+    case FFT3D_ERR_UNSUPPORTED_PRECISION: return "precision unsupported for this plan";
+    default: return "unknown error code";
+  }
+}
+
+int fft3d_selftest_wait_timeout(int64_t timeout_ns) {
+  if (timeout_ns <= 0 || timeout_ns > 10000000000LL) return FFT3D_ERR_INVALID_ARG;
+  int rc = check_device();
+  if (rc) return rc;
+  unsigned* buf = nullptr;
+  if (cudaMalloc(&buf, 2 * sizeof(unsigned)) != cudaSuccess) {
+    cudaGetLastError();
+    return FFT3D_ERR_ALLOC;
+  }
+  unsigned host[2] = {0u, 0u};
+  rc = FFT3D_ERR_CUDA;
+  if (cudaMemset(buf, 0, 2 * sizeof(unsigned)) == cudaSuccess &&
+      launch_wait_selftest(buf, buf + 1, (long long)timeout_ns, nullptr) == cudaSuccess &&
+      cudaDeviceSynchronize() == cudaSuccess &&
+      cudaMemcpy(host, buf, sizeof(host), cudaMemcpyDeviceToHost) == cudaSuccess)
+    rc = host[1] == kStatusTimeout ? FFT3D_ERR_DEVICE_TIMEOUT : FFT3D_SUCCESS;
+  cudaGetLastError();
+  cudaFree(buf);
+  return rc;
+}
+
+}  // extern "C"

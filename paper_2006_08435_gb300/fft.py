@@ -1,0 +1,204 @@
+"""PyTorch-facing binding of the C ABI (``include/fft3d.h``).
+
+Argument marshalling only: tensors are passed to the library as raw device
+pointers plus the current CUDA stream; every step of the transform runs in
+the library's sm_103a kernels.  PyTorch supplies device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import torch
+
+from . import _lib as L
+
+_PREC = {"fp32": L.FFT3D_FP32, "split_fp16": L.FFT3D_SPLIT_FP16,
+         "split_bf16": L.FFT3D_SPLIT_BF16, "fp16": L.FFT3D_FP16}
+_NORM = {"none": L.FFT3D_NORM_NONE, "n": L.FFT3D_NORM_BY_N, "by_n": L.FFT3D_NORM_BY_N,
+         "ortho": L.FFT3D_NORM_ORTHO}
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _check_tensor(t: torch.Tensor, name: str) -> None:
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.complex64:
+        raise TypeError(f"{name} must be complex64, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def size_supported(n: int) -> bool:
+    return bool(L.lib().fft3d_size_supported(int(n)))
+
+
+def twiddle_table(n: int):
+    """(L1, L2, table as a list of (re, im) FP32 pairs) the planner uses."""
+    buf = (ctypes.c_float * (2 * n))()
+    l1, l2 = ctypes.c_int(), ctypes.c_int()
+    L.check(L.lib().fft3d_twiddle_table(int(n), buf, ctypes.byref(l1), ctypes.byref(l2)),
+            "fft3d_twiddle_table")
+    return l1.value, l2.value, [(buf[2 * i], buf[2 * i + 1]) for i in range(n)]
+
+
+class Plan:
+    """A plan for ``batch`` grids of nz x ny x nx complex64 points.
+
+    ``execute(x, out)`` computes Eq. 1 per grid on the current stream."""
+
+    def __init__(self, nx: int, ny: int, nz: int, batch: int = 1, precision: str = "fp32",
+                 inverse: bool = False, norm: str = "none"):
+        self.shape = (int(nz), int(ny), int(nx))
+        self.batch = int(batch)
+        self.precision, self.inverse, self.norm = precision, bool(inverse), norm
+        h = ctypes.c_void_p()
+        L.check(L.lib().fft3d_plan_create(int(nx), int(ny), int(nz), int(batch), _PREC[precision],
+                                          L.FFT3D_INVERSE if inverse else L.FFT3D_FORWARD,
+                                          _NORM[norm], ctypes.byref(h)), "fft3d_plan_create")
+        self._h = h
+
+    @property
+    def handle(self) -> int:
+        return self._h.value or 0
+
+    def execute(self, x: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
+        _check_tensor(x, "x")
+        _check_tensor(out, "out")
+        need = self.batch * self.shape[0] * self.shape[1] * self.shape[2]
+        if x.numel() != need or out.numel() != need:
+            raise ValueError(f"expected {need} points, got {x.numel()} and {out.numel()}")
+        L.check(L.lib().fft3d_execute(self._h, x.data_ptr(), out.data_ptr(), _stream_handle(stream)),
+                "fft3d_execute")
+        return out
+
+    def device_status(self, stream=None) -> int:
+        return L.lib().fft3d_get_device_status(self._h, _stream_handle(stream))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            L.lib().fft3d_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MixedPlan:
+    """Cubic grids of different edges transformed in one persistent launch."""
+
+    def __init__(self, dims, precision: str = "fp32", inverse: bool = False, norm: str = "none"):
+        self.dims = [int(d) for d in dims]
+        arr = (ctypes.c_int * len(self.dims))(*self.dims)
+        h = ctypes.c_void_p()
+        L.check(L.lib().fft3d_plan_create_mixed(len(self.dims), arr, _PREC[precision],
+                                                L.FFT3D_INVERSE if inverse else L.FFT3D_FORWARD,
+                                                _NORM[norm], ctypes.byref(h)),
+                "fft3d_plan_create_mixed")
+        self._h = h
+        self.offsets = []
+        for g in range(len(self.dims) + 1):
+            o = ctypes.c_int64()
+            L.check(L.lib().fft3d_plan_grid_offset(self._h, g, ctypes.byref(o)), "grid_offset")
+            self.offsets.append(o.value)
+        self.total_points = self.offsets[-1]
+
+    def execute(self, x: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
+        """Packed buffers: grid g occupies points [offsets[g], offsets[g+1])."""
+        _check_tensor(x, "x")
+        _check_tensor(out, "out")
+        if x.numel() != self.total_points or out.numel() != self.total_points:
+            raise ValueError("packed buffers must hold exactly total_points points")
+        L.check(L.lib().fft3d_execute(self._h, x.data_ptr(), out.data_ptr(), _stream_handle(stream)),
+                "fft3d_execute")
+        return out
+
+    def execute_ptrs(self, in_ptrs: torch.Tensor, out_ptrs: torch.Tensor, stream=None) -> None:
+        """``in_ptrs``/``out_ptrs``: int64 CUDA tensors of per-grid device pointers."""
+        for t in (in_ptrs, out_ptrs):
+            if not (t.is_cuda and t.dtype == torch.int64 and t.numel() == len(self.dims)):
+                raise ValueError("pointer arrays must be int64 CUDA tensors, one per grid")
+        L.check(L.lib().fft3d_execute_mixed(self._h, in_ptrs.data_ptr(), out_ptrs.data_ptr(),
+                                            _stream_handle(stream)), "fft3d_execute_mixed")
+
+    def device_status(self, stream=None) -> int:
+        return L.lib().fft3d_get_device_status(self._h, _stream_handle(stream))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            L.lib().fft3d_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_plan_cache: dict = {}
+_cache_lock = threading.Lock()
+
+
+def get_plan(nx, ny, nz, batch, precision="fp32", inverse=False, norm="none", device=None) -> Plan:
+    dev = torch.cuda.current_device() if device is None else device
+    key = (nx, ny, nz, batch, precision, bool(inverse), norm, dev)
+    with _cache_lock:
+        p = _plan_cache.get(key)
+        if p is None:
+            with torch.cuda.device(dev):
+                p = Plan(nx, ny, nz, batch, precision, inverse, norm)
+            _plan_cache[key] = p
+    return p
+
+
+def fft3d(x: torch.Tensor, inverse: bool = False, norm: str = "none", precision: str = "fp32",
+          out: torch.Tensor | None = None) -> torch.Tensor:
+    """3D DFT (Eq. 1) over the last three dims (nz, ny, nx) of a complex64
+    CUDA tensor; leading dims are a batch.  Forward uses exp(-2 pi i/n),
+    ``inverse=True`` exp(+2 pi i/n); ``norm`` in {"none", "by_n", "ortho"}."""
+    _check_tensor(x, "x")
+    if x.dim() < 3:
+        raise ValueError("need (..., nz, ny, nx)")
+    nz, ny, nx = x.shape[-3:]
+    batch = x.numel() // (nz * ny * nx) if x.numel() else 0
+    if out is None:
+        out = torch.empty_like(x)
+    if batch == 0:
+        return out
+    plan = get_plan(nx, ny, nz, batch, precision, inverse, norm, x.device.index)
+    return plan.execute(x, out)
+
+
+class FFT3d(torch.autograd.Function):
+    """y = F(x) with F the unnormalised forward transform of Eq. 1.
+
+    Backward is the adjoint F^H, i.e. the unnormalised transform with the
+    conjugate root exp(+2 pi i/n), run by the same kernels.  (PyTorch's
+    convention for complex gradients makes grad_x = F^H grad_y for a linear
+    map.)"""
+
+    @staticmethod
+    def forward(ctx, x, precision="fp32"):
+        ctx.precision = precision
+        return fft3d(x.contiguous(), inverse=False, precision=precision)
+
+    @staticmethod
+    def backward(ctx, g):
+        return fft3d(g.contiguous(), inverse=True, precision=ctx.precision), None
+
+
+def selftest_wait_timeout(timeout_ns: int = 1_000_000) -> int:
+    """Run the bounded-wait self test (a wait on a flag nobody sets); returns
+    the library's code, FFT3D_ERR_DEVICE_TIMEOUT when the wait gave up."""
+    return L.lib().fft3d_selftest_wait_timeout(int(timeout_ns))

@@ -1,0 +1,108 @@
+"""The C-ABI library on a machine without a GPU: it loads, exports every
+symbol the header declares, validates arguments before touching a device,
+and its planner's split and FP32 twiddle tables are exact roundings of the
+FP64 values."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2006_08435_gb300 import _lib as L
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+FUSED = [16, 32, 48, 64, 80, 96, 128]
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "fft3d.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fft3d_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(fft3d_lib):
+    names = header_functions()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(fft3d_lib, n), n
+    assert sorted(L.exported_symbols()) == names
+
+
+def test_error_strings(fft3d_lib):
+    for code in range(0, -10, -1):
+        s = fft3d_lib.fft3d_error_string(code).decode()
+        assert s and s != "unknown error code"
+    assert fft3d_lib.fft3d_error_string(-99).decode() == "unknown error code"
+
+
+def _create(lib, *args):
+    h = ctypes.c_void_p(1234)
+    rc = lib.fft3d_plan_create(*args, ctypes.byref(h))
+    return rc, h.value
+
+
+@pytest.mark.parametrize("args,code", [
+    ((64, 64, 64, 0, 0, -1, 0), L.FFT3D_ERR_INVALID_ARG),      # batch 0
+    ((64, 64, 64, 1, 7, -1, 0), L.FFT3D_ERR_INVALID_ARG),      # precision
+    ((64, 64, 64, 1, 0, 0, 0), L.FFT3D_ERR_INVALID_ARG),       # direction
+    ((64, 64, 64, 1, 0, -1, 5), L.FFT3D_ERR_INVALID_ARG),      # norm
+    ((0, 64, 64, 1, 0, -1, 0), L.FFT3D_ERR_INVALID_ARG),       # zero edge
+    ((7, 7, 7, 1, 0, -1, 0), L.FFT3D_ERR_UNSUPPORTED_SIZE),    # prime 7
+    ((256, 256, 256, 1, 0, -1, 0), L.FFT3D_ERR_UNSUPPORTED_SIZE),
+])
+def test_create_validates_before_device(fft3d_lib, args, code):
+    rc, h = _create(fft3d_lib, *args)
+    assert rc == code
+    assert h is None
+
+
+def test_create_null_out(fft3d_lib):
+    assert fft3d_lib.fft3d_plan_create(64, 64, 64, 1, 0, -1, 0, None) == L.FFT3D_ERR_NULL_PTR
+
+
+def test_mixed_validation(fft3d_lib):
+    h = ctypes.c_void_p()
+    dims = (ctypes.c_int * 3)(32, 48, 7)
+    assert fft3d_lib.fft3d_plan_create_mixed(3, dims, 0, -1, 0, ctypes.byref(h)) == L.FFT3D_ERR_UNSUPPORTED_SIZE
+    assert fft3d_lib.fft3d_plan_create_mixed(0, dims, 0, -1, 0, ctypes.byref(h)) == L.FFT3D_ERR_INVALID_ARG
+    assert fft3d_lib.fft3d_plan_create_mixed(3, None, 0, -1, 0, ctypes.byref(h)) == L.FFT3D_ERR_NULL_PTR
+
+
+def test_null_handles(fft3d_lib):
+    assert fft3d_lib.fft3d_execute(None, 16, 16, None) == L.FFT3D_ERR_NULL_PTR
+    assert fft3d_lib.fft3d_plan_destroy(None) == L.FFT3D_SUCCESS
+    assert fft3d_lib.fft3d_get_device_status(None, None) == L.FFT3D_ERR_NULL_PTR
+
+
+def test_valid_args_reach_device_check(fft3d_lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("has a GPU")
+    rc, _ = _create(fft3d_lib, 64, 64, 64, 1, 0, -1, 0)
+    assert rc == L.FFT3D_ERR_NO_DEVICE
+
+
+def test_size_supported(fft3d_lib):
+    for n in FUSED:
+        assert fft3d_lib.fft3d_size_supported(n) == 1
+    for n in (0, 1, 7, 11, 13, 256, 1024):
+        assert fft3d_lib.fft3d_size_supported(n) == 0
+
+
+@pytest.mark.parametrize("n", FUSED)
+def test_twiddle_tables_are_rounded_fp64(fft3d_lib, n):
+    """Each entry is the round-to-nearest FP32 of exp(-2 pi i m / n),
+    m = n1*k2 mod n, with the FP64 value taken from Python's math library,
+    and the split multiplies back to n with factors of at most 16."""
+    buf = (ctypes.c_float * (2 * n))()
+    l1, l2 = ctypes.c_int(), ctypes.c_int()
+    assert fft3d_lib.fft3d_twiddle_table(n, buf, ctypes.byref(l1), ctypes.byref(l2)) == 0
+    assert l1.value * l2.value == n and l1.value <= 16 and l2.value <= 16
+    got = np.frombuffer(buf, dtype=np.float32).reshape(l2.value, l1.value, 2)
+    for k2 in range(l2.value):
+        for n1 in range(l1.value):
+            a = 2 * math.pi * ((n1 * k2) % n) / n
+            assert got[k2, n1, 0] == np.float32(math.cos(a))
+            assert got[k2, n1, 1] == np.float32(-math.sin(a))
