@@ -1,10 +1,16 @@
-// Single-size persistent kernel for 128^3 grids (forward and inverse).
-#include "persistent.cuh"
+// Single-size persistent kernels for 128^3 grids (forward and inverse),
+// in two block sizes: the default and twice as many threads per block
+// (more warps to hide latency, fewer registers per thread), plus the
+// warp-specialised TMA-fed kernel (variant 2).
+#include "pipelined.cuh"
 
 namespace fft3d {
 
-KernelInfo fused_kernel_info_n128(int dir) {
+KernelInfo fused_kernel_info_n128(int dir, int variant) {
   constexpr int T = fused_threads(128);
+  if (variant == 2) return dir < 0 ? piped::info<-1>() : piped::info<1>();
+  if (variant == 1 && 2 * T <= 1024)
+    return dir < 0 ? make_fused_info<2 * T, -1, 128>() : make_fused_info<2 * T, 1, 128>();
   return dir < 0 ? make_fused_info<T, -1, 128>() : make_fused_info<T, 1, 128>();
 }
 

@@ -1,10 +1,14 @@
-// Single-size persistent kernel for 16^3 grids (forward and inverse).
+// Single-size persistent kernels for 16^3 grids (forward and inverse),
+// in two block sizes: the default and twice as many threads per block
+// (more warps to hide latency, fewer registers per thread).
 #include "persistent.cuh"
 
 namespace fft3d {
 
-KernelInfo fused_kernel_info_n16(int dir) {
+KernelInfo fused_kernel_info_n16(int dir, int variant) {
   constexpr int T = fused_threads(16);
+  if (variant == 1 && 2 * T <= 1024)
+    return dir < 0 ? make_fused_info<2 * T, -1, 16>() : make_fused_info<2 * T, 1, 16>();
   return dir < 0 ? make_fused_info<T, -1, 16>() : make_fused_info<T, 1, 16>();
 }
 

@@ -52,10 +52,11 @@ struct KernelInfo {
   int twiddle_entries = 0;      // complex entries in the concatenated table
   int sizes[8] = {0};           // edges handled, in table order
   int nsizes = 0;
+  int items_in_flight = 1;      // work items a block holds at once (schedule lag)
 };
 
 // Defined in the inst_*.cu translation units.
-KernelInfo fused_kernel_info(int n, int dir);   // single-size kernel
+KernelInfo fused_kernel_info(int n, int dir, int variant);   // single-size kernel
 KernelInfo mixed_kernel_info(int dir);          // all fused sizes
 cudaError_t launch_wait_selftest(unsigned* flag, unsigned* status, long long timeout_ns,
                                  cudaStream_t stream);

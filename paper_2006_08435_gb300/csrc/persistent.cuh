@@ -277,19 +277,25 @@ __host__ __device__ constexpr int tw_offset(int n) {
   return found;
 }
 
+// Input and output base of grid g (edge n) for either addressing mode.
+__device__ __forceinline__ void grid_ptrs(const FusedArgs& a, int g, int n, const float2*& gin,
+                                          float2*& gout) {
+  if (a.in_ptrs) {
+    gin = a.in_ptrs[g];
+    gout = a.out_ptrs[g];
+  } else {
+    const long long off = a.grid_off ? a.grid_off[g] : (long long)g * n * n * n;
+    gin = a.in + off;
+    gout = a.out + off;
+  }
+}
+
 template <int N, int T, int DIR>
 __device__ __forceinline__ void run_item(const FusedArgs& a, const SchedBlock& blk, int i,
                                          float2* tile, const float2* tw) {
   const float2* gin;
   float2* gout;
-  if (a.in_ptrs) {
-    gin = a.in_ptrs[blk.grid];
-    gout = a.out_ptrs[blk.grid];
-  } else {
-    const long long off = a.grid_off ? a.grid_off[blk.grid] : (long long)blk.grid * N * N * N;
-    gin = a.in + off;
-    gout = a.out + off;
-  }
+  grid_ptrs(a, blk.grid, N, gin, gout);
   if (blk.phase == 0) {
     const long long o = (long long)i * N * N;
     plane_item<N, T, DIR>(gin + o, gout + o, tile, tw);

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -16,23 +17,23 @@
 
 namespace fft3d {
 
-KernelInfo fused_kernel_info_n16(int dir);
-KernelInfo fused_kernel_info_n32(int dir);
-KernelInfo fused_kernel_info_n48(int dir);
-KernelInfo fused_kernel_info_n64(int dir);
-KernelInfo fused_kernel_info_n80(int dir);
-KernelInfo fused_kernel_info_n96(int dir);
-KernelInfo fused_kernel_info_n128(int dir);
+KernelInfo fused_kernel_info_n16(int dir, int variant);
+KernelInfo fused_kernel_info_n32(int dir, int variant);
+KernelInfo fused_kernel_info_n48(int dir, int variant);
+KernelInfo fused_kernel_info_n64(int dir, int variant);
+KernelInfo fused_kernel_info_n80(int dir, int variant);
+KernelInfo fused_kernel_info_n96(int dir, int variant);
+KernelInfo fused_kernel_info_n128(int dir, int variant);
 
-KernelInfo fused_kernel_info(int n, int dir) {
+KernelInfo fused_kernel_info(int n, int dir, int variant) {
   switch (n) {
-    case 16: return fused_kernel_info_n16(dir);
-    case 32: return fused_kernel_info_n32(dir);
-    case 48: return fused_kernel_info_n48(dir);
-    case 64: return fused_kernel_info_n64(dir);
-    case 80: return fused_kernel_info_n80(dir);
-    case 96: return fused_kernel_info_n96(dir);
-    case 128: return fused_kernel_info_n128(dir);
+    case 16: return fused_kernel_info_n16(dir, variant);
+    case 32: return fused_kernel_info_n32(dir, variant);
+    case 48: return fused_kernel_info_n48(dir, variant);
+    case 64: return fused_kernel_info_n64(dir, variant);
+    case 80: return fused_kernel_info_n80(dir, variant);
+    case 96: return fused_kernel_info_n96(dir, variant);
+    case 128: return fused_kernel_info_n128(dir, variant);
     default: return KernelInfo{};
   }
 }
@@ -52,6 +53,15 @@ static void twiddle_table(int n, float* out /* 2 * n floats */) {
 }
 
 static bool fused_size(int n) { return fused_slot(n) >= 0; }
+
+// Variant of the single-size kernel: FFT3D_VARIANT (0, 1 or 2) overrides
+// the default, which is the TMA-fed warp-specialised kernel (2) for 128^3
+// and the plain persistent kernel (0) otherwise.
+static int default_variant(int n) {
+  const char* e = std::getenv("FFT3D_VARIANT");
+  if (e && e[0] >= '0' && e[0] <= '2' && e[1] == 0) return e[0] - '0';
+  return n == 128 ? 2 : 0;
+}
 
 }  // namespace fft3d
 
@@ -115,23 +125,47 @@ int check_device() {
   return FFT3D_SUCCESS;
 }
 
-// Ticket order: planes of grid 0, then for each later grid its planes
-// followed by the slabs of the grid before it, then the slabs of the last
-// grid.  `order` lists grids in scheduling order.
+// Ticket order.  Plane blocks are emitted grid after grid (in `order`); the
+// slab block of grid g is emitted once at least `concurrency` tickets (the
+// number of blocks resident at once) have been handed out after the last
+// plane ticket of g, so a slab item rarely waits, or earlier when the grids
+// whose planes are done but whose slabs are not yet scheduled would exceed
+// `l2_budget` bytes (their intermediate must stay in L2).
 std::vector<SchedBlock> build_schedule(const std::vector<int>& dims, const std::vector<int>& order,
-                                       int* total_items) {
+                                       int concurrency, double l2_budget, int* total_items) {
   std::vector<SchedBlock> blocks;
   int start = 0;
   auto push = [&](int g, int phase) {
     blocks.push_back(SchedBlock{g, phase, start, dims[g]});
     start += dims[g];
   };
-  const int count = (int)order.size();
-  for (int j = 0; j < count; ++j) {
-    push(order[j], 0);
-    if (j >= 1) push(order[j - 1], 1);
+  struct Pending {
+    int g;
+    int plane_end;
+    double bytes;
+  };
+  std::vector<Pending> pending;  // FIFO
+  double pending_bytes = 0.0;
+  auto flush_ready = [&](bool force_one) {
+    while (!pending.empty()) {
+      const Pending& p = pending.front();
+      const bool ready = start - p.plane_end >= concurrency;
+      if (!ready && !force_one) break;
+      force_one = false;
+      pending_bytes -= p.bytes;
+      push(p.g, 1);
+      pending.erase(pending.begin());
+    }
+  };
+  for (int g : order) {
+    const double bytes = 8.0 * dims[g] * dims[g] * dims[g];
+    while (!pending.empty() && pending_bytes + bytes > l2_budget) flush_ready(true);
+    push(g, 0);
+    pending.push_back(Pending{g, start, bytes});
+    pending_bytes += bytes;
+    flush_ready(false);
   }
-  push(order[count - 1], 1);
+  while (!pending.empty()) flush_ready(true);
   *total_items = start;
   return blocks;
 }
@@ -149,11 +183,16 @@ int finish_plan(fft3d_plan p, const std::vector<int>& order) {
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
   if (e != cudaSuccess) return FFT3D_ERR_CUDA;
 
+  int l2_bytes = 0;
+  if (cudaDeviceGetAttribute(&l2_bytes, cudaDevAttrL2CacheSize, p->device) != cudaSuccess)
+    return FFT3D_ERR_CUDA;
   int total_items = 0;
-  std::vector<SchedBlock> blocks = build_schedule(p->dims, order, &total_items);
+  const int resident = per_sm * sms;
+  std::vector<SchedBlock> blocks = build_schedule(
+      p->dims, order, resident * p->kernel.items_in_flight, 0.4 * (double)l2_bytes, &total_items);
   p->total_items = total_items;
   p->nblocks = (int)blocks.size();
-  p->grid = std::max(1, std::min(total_items, per_sm * sms));
+  p->grid = std::max(1, std::min(total_items, resident));
 
   // twiddles for every edge the kernel handles, concatenated in its order
   std::vector<float> tw(2 * (size_t)p->kernel.twiddle_entries);
@@ -275,7 +314,7 @@ int fft3d_plan_create(int nx, int ny, int nz, int batch, int precision, int dire
   for (int g = 0; g < batch; ++g) p->offsets[g] = (long long)g * pts;
   p->total_points = pts * batch;
   set_scale(p, (double)pts);
-  p->kernel = fused_kernel_info(nx, direction);
+  p->kernel = fused_kernel_info(nx, direction, default_variant(nx));
   std::vector<int> order(batch);
   for (int g = 0; g < batch; ++g) order[g] = g;
   rc = finish_plan(p, order);
