@@ -8,7 +8,7 @@ namespace fft3d {
 
 KernelInfo fused_kernel_info_n128(int dir, int variant) {
   constexpr int T = fused_threads(128);
-  if (variant == 2) return dir < 0 ? piped::info<-1>() : piped::info<1>();
+  if (variant == 2) return dir < 0 ? piped::info<128, -1>() : piped::info<128, 1>();
   if (variant == 1 && 2 * T <= 1024)
     return dir < 0 ? make_fused_info<2 * T, -1, 128>() : make_fused_info<2 * T, 1, 128>();
   return dir < 0 ? make_fused_info<T, -1, 128>() : make_fused_info<T, 1, 128>();
