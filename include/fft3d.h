@@ -70,7 +70,8 @@ enum {
   FFT3D_ERR_DEVICE_TIMEOUT = -6,   /* a bounded device-side wait ran out (status word) */
   FFT3D_ERR_ALLOC = -7,            /* device or host allocation failed at plan create */
   FFT3D_ERR_NO_DEVICE = -8,        /* no CUDA device, or not compute capability 10.3 */
-  FFT3D_ERR_UNSUPPORTED_PRECISION = -9 /* precision not available for this plan's sizes */
+  FFT3D_ERR_UNSUPPORTED_PRECISION = -9, /* precision not available for this plan's sizes */
+  FFT3D_ERR_EXCEEDS_STATIC_SCRATCH = -10 /* fft3d_execute_noalloc: batch above FFT3D_NOALLOC_MAX_BATCH */
 };
 
 /* Largest number of grids in one mixed plan. */
@@ -166,6 +167,38 @@ const char* fft3d_error_string(int code);
  * hanging or faulting the GPU.
  */
 int fft3d_selftest_wait_timeout(int64_t timeout_ns);
+
+/* Largest batch fft3d_execute_noalloc accepts. */
+#define FFT3D_NOALLOC_MAX_BATCH 4096
+
+/*
+ * The batched cubic transform for callers that cannot allocate device
+ * memory when they need it -- for example a solver loop whose framework
+ * hands out all device memory up front and forbids cudaMalloc later (it can
+ * synchronise the device and can fail under memory pressure).  The paper has
+ * no counterpart; this is a deployment convenience.
+ *
+ * Computes what a plan from fft3d_plan_create(n, n, n, batch, FFT3D_FP32,
+ * direction, norm) followed by fft3d_execute(plan, in, out, stream) computes,
+ * with the same kernels, but creates no plan and calls no cudaMalloc,
+ * cudaFree or other allocating routine.  The kernels' scratch (work
+ * counters, ticket schedule, twiddle table, status word) lives in one
+ * file-scope device array of 160 KiB that every GPU which loads this library
+ * holds until the process exits.
+ *   n         : edge, one of 16, 32, 48, 64, 80, 96, 128.
+ *   batch     : 1 .. FFT3D_NOALLOC_MAX_BATCH grids; larger batches return
+ *               FFT3D_ERR_EXCEEDS_STATIC_SCRATCH.
+ *   direction, norm, in, out, stream : as for fft3d_plan_create/execute.
+ * The first call on a device looks up the array's device address (and the
+ * kernel's occupancy) with that device current; make that first call before
+ * any stream capture.  Every call on a device shares the one array and
+ * rewrites it (counters and status are cleared at the start of each call),
+ * so calls whose work overlaps on the GPU -- on different streams, or from
+ * different host threads -- race.  Host threads are serialised inside the
+ * call.  A bounded wait that times out inside such a call is not reported.
+ */
+int fft3d_execute_noalloc(int n, int batch, int direction, int norm,
+                          const void* in, void* out, void* stream);
 
 #ifdef __cplusplus
 }

@@ -25,6 +25,8 @@ FFT3D_ERR_DEVICE_TIMEOUT = -6
 FFT3D_ERR_ALLOC = -7
 FFT3D_ERR_NO_DEVICE = -8
 FFT3D_ERR_UNSUPPORTED_PRECISION = -9
+FFT3D_ERR_EXCEEDS_STATIC_SCRATCH = -10
+FFT3D_NOALLOC_MAX_BATCH = 4096
 
 # name -> (restype, argtypes); every symbol include/fft3d.h declares
 _VP = ctypes.c_void_p
@@ -41,6 +43,7 @@ _SIGS = {
     "fft3d_plan_destroy": (_I, [_VP]),
     "fft3d_error_string": (ctypes.c_char_p, [_I]),
     "fft3d_selftest_wait_timeout": (_I, [ctypes.c_int64]),
+    "fft3d_execute_noalloc": (_I, [_I, _I, _I, _I, _VP, _VP, _VP]),
 }
 
 _lib = None

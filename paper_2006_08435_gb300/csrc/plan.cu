@@ -437,6 +437,7 @@ const char* fft3d_error_string(int code) {
     case FFT3D_ERR_ALLOC: return "allocation failed";
     case FFT3D_ERR_NO_DEVICE: return "no compute capability 10.3 device";
     case FFT3D_ERR_UNSUPPORTED_PRECISION: return "precision unsupported for this plan";
+    case FFT3D_ERR_EXCEEDS_STATIC_SCRATCH: return "batch exceeds the static scratch of fft3d_execute_noalloc";
     default: return "unknown error code";
   }
 }
