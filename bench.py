@@ -8,7 +8,9 @@ than L2, so no flush is needed between steps).  Roofline bytes per
 transform = 16 * N^3 (one read and one write of the grid).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload 128x32|64x256]
+                  [--workload 128x32|64x256|128x16|64x64] [--no-cpu-baseline] [--no-e2e]
+
+The two small workloads exist for profiler captures of the same kernels.
 
 Under torchrun each rank transforms its own batch (weak scaling, no
 collective on the data path); rank 0 prints one JSON line.
@@ -32,11 +34,16 @@ sys.path.insert(0, ROOT)
 WORKLOADS = {
     "128x32": (128, 32),
     "64x256": (64, 256),
+    # smaller cases of the same kernels for ncu captures (inputs still > L2)
+    "128x16": (128, 16),
+    "64x64": (64, 64),
 }
 METRIC = "batched 3D FFT transforms/s and % of HBM roofline at 64^3/128^3 (FP32 vs split-FP16)"
 KERNEL_SOURCES = ["paper_2006_08435_gb300/csrc/persistent.cuh",
+                  "paper_2006_08435_gb300/csrc/pipelined.cuh",
                   "paper_2006_08435_gb300/csrc/codelets.cuh",
                   "paper_2006_08435_gb300/csrc/sizes.h"]
+KERNEL_NAMES = {128: "piped_fft3d_kernel<128>", 64: "fused_fft3d_kernel<256,64>"}
 
 
 def dist_env():
@@ -66,7 +73,7 @@ def kernel_source_hash() -> str:
 def recorded_traffic(n: int, batch: int):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel source; else None."""
-    path = os.path.join(ROOT, "profiles", f"fused_fft3d_n{n}_traffic.txt")
+    path = os.path.join(ROOT, "profiles", f"fft3d_{n}cubed_dram_traffic.txt")
     try:
         kv = {}
         for line in open(path):
@@ -136,7 +143,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(n: int, budget_s: float = 12.0):
+def cpu_baseline(n: int, budget_s: float = 15.0):
     """The FP64 oracle, as it stands, on one n^3 grid of the workload,
     repeated until about `budget_s` seconds of CPU work."""
     import numpy as np
@@ -149,7 +156,7 @@ def cpu_baseline(n: int, budget_s: float = 12.0):
         oracle.dft3d(x)
         reps += 1
         el = time.perf_counter() - t0
-        if el >= budget_s or reps >= 50:
+        if el >= budget_s or reps >= 100000:
             break
     return {"value": reps / el, "unit": "transforms/s", "cores": oracle.num_threads(),
             "kind": "oracle",
@@ -250,31 +257,35 @@ def run_ours(args, ws, rank, local):
     assert plan.device_status() == 0, "device-side wait timed out"
 
     # end to end through the public API with pinned host buffers
-    hx = x.cpu().pin_memory()
-    hy = torch.empty_like(hx).pin_memory()
-    e_steps = max(2, min(args.steps, 5))
-    for _ in range(2):
-        x.copy_(hx, non_blocking=True)
-        plan.execute(x, y, stream)
-        hy.copy_(y, non_blocking=True)
-    barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(e_steps):
-        x.copy_(hx, non_blocking=True)
-        plan.execute(x, y, stream)
-        hy.copy_(y, non_blocking=True)
-    e1.record(stream)
-    barrier()
-    e2e_ms = e0.elapsed_time(e1) / e_steps
-    if ws > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e = {"value": ws * batch / (e2e_ms / 1e3), "unit": "transforms/s",
-           "h2d_bytes_per_step": hx.numel() * hx.element_size(),
-           "d2h_bytes_per_step": hy.numel() * hy.element_size()}
+    e2e = None
+    if args.no_e2e:
+        hx = None
+    else:
+        hx = x.cpu().pin_memory()
+        hy = torch.empty_like(hx).pin_memory()
+        e_steps = max(2, min(args.steps, 5))
+        for _ in range(2):
+            x.copy_(hx, non_blocking=True)
+            plan.execute(x, y, stream)
+            hy.copy_(y, non_blocking=True)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(e_steps):
+            x.copy_(hx, non_blocking=True)
+            plan.execute(x, y, stream)
+            hy.copy_(y, non_blocking=True)
+        e1.record(stream)
+        barrier()
+        e2e_ms = e0.elapsed_time(e1) / e_steps
+        if ws > 1:
+            t = torch.tensor([e2e_ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": ws * batch / (e2e_ms / 1e3), "unit": "transforms/s",
+               "h2d_bytes_per_step": hx.numel() * hx.element_size(),
+               "d2h_bytes_per_step": hy.numel() * hy.element_size()}
 
     if rank != 0:
         if ws > 1:
@@ -297,7 +308,8 @@ def run_ours(args, ws, rank, local):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} hbm_gbs",
-                     "kernel": "fused_fft3d_kernel", "bytes_per_launch": bytes_per_launch,
+                     "kernel": KERNEL_NAMES.get(n, "fused_fft3d_kernel"),
+                     "bytes_per_launch": bytes_per_launch,
                      "avg_launch_ms": avg_launch_ms},
         "e2e": e2e,
         "gpu_launches": args.steps,
@@ -314,11 +326,12 @@ def run_ours(args, ws, rank, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="128x32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":

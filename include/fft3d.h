@@ -168,6 +168,52 @@ const char* fft3d_error_string(int code);
  */
 int fft3d_selftest_wait_timeout(int64_t timeout_ns);
 
+/*
+ * ---------------------------------------------------------------------------
+ * Plane-wave Hartree energy, the use of the 3D FFT in plane-wave DFT that the
+ * paper accelerates (sections "Introduction" and "Results"; the formulas are
+ * the standard Gaussian-and-plane-wave ones, which the paper does not print).
+ * Cubic periodic cell of side L (bohr), volume Omega = L^3, n^3 grid,
+ * G = (2 pi / L) m with m_d = k_d for k_d < n/2 and k_d - n otherwise, G = 0
+ * excluded (neutralising background).  With F = forward transform (Eq. 1,
+ * unnormalised) and s = Omega 4 pi / (n^6 (2 pi / L)^2):
+ *   E_H = (Omega/2) sum_{G!=0} 4 pi |F(rho)(G)/n^3|^2 / |G|^2
+ *       = (s/2) sum_{m!=0} |F(rho)(m)|^2 / |m|^2,
+ *   dE_H/drho = Re F^H( s F(rho) / |m|^2 ).
+ * ---------------------------------------------------------------------------
+ */
+
+/* Bytes of device workspace fft3d_hartree_energy needs (0 on bad args). */
+size_t fft3d_hartree_workspace_bytes(int n, int batch);
+
+/*
+ * energy[b] = E_H of grid b, for `batch` spectra rhohat = F(rho) (device,
+ * complex64, batch * n^3 points, 8-byte aligned).  Accumulated in FP64 in a
+ * fixed order (bit-reproducible).  energy: DEVICE array of `batch` doubles.
+ * workspace: DEVICE buffer of at least fft3d_hartree_workspace_bytes(n,
+ * batch) bytes, owned by the caller; it may be reused by later calls on the
+ * same stream.  Asynchronous on `stream`.
+ */
+int fft3d_hartree_energy(const void* rhohat, int n, int batch, double L,
+                         double* energy, void* workspace, size_t workspace_bytes,
+                         void* stream);
+
+/*
+ * Backward seed of E_H: seed[b] = grad_energy[b] * s * rhohat[b] / |m|^2
+ * (0 at m = 0), complex64, so that Re F^H(seed) (fft3d with
+ * FFT3D_INVERSE, unnormalised) is grad_energy[b] * dE_H/drho.
+ * grad_energy: DEVICE array of `batch` doubles.  All pointers device,
+ * 8-byte aligned.
+ */
+int fft3d_hartree_seed(const void* rhohat, int n, int batch, double L,
+                       const double* grad_energy, void* seed, void* stream);
+
+/* out[i] = (re[i], 0) for i < count (device float -> complex64). */
+int fft3d_real_to_complex(const float* re, void* out, int64_t count, void* stream);
+
+/* re[i] = Re in[i] for i < count (device complex64 -> float). */
+int fft3d_complex_to_real(const void* in, float* re, int64_t count, void* stream);
+
 /* Largest batch fft3d_execute_noalloc accepts. */
 #define FFT3D_NOALLOC_MAX_BATCH 4096
 

@@ -8,13 +8,15 @@ of Eq. 1 computed as 1D FFTs along x, then y, then z, behind the C ABI of
 * ``fft3d(x, inverse=False, norm="none", precision="fp32")``
 * ``Plan`` / ``MixedPlan`` -- explicit plans (batched / mixed edges)
 * ``FFT3d`` -- autograd Function whose backward is the adjoint transform
+* ``hartree_energy`` -- plane-wave Hartree energy with an adjoint-FFT gradient
 
 Importing the package does not load the CUDA library; the first call does,
 and raises if it has not been built (there is no CPU fallback).
 """
 from ._lib import FFT3DError  # noqa: F401
 
-__all__ = ["fft3d", "Plan", "MixedPlan", "FFT3d", "FFT3DError", "size_supported"]
+__all__ = ["fft3d", "Plan", "MixedPlan", "FFT3d", "FFT3DError", "size_supported",
+           "hartree_energy", "HartreeEnergy"]
 
 
 def __getattr__(name):
@@ -22,4 +24,7 @@ def __getattr__(name):
                 "twiddle_table", "selftest_wait_timeout"):
         from . import fft as _fft
         return getattr(_fft, name)
+    if name in ("hartree_energy", "HartreeEnergy"):
+        from . import hartree as _h
+        return getattr(_h, name)
     raise AttributeError(name)

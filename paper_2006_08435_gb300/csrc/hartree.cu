@@ -1,0 +1,209 @@
+// Plane-wave Hartree energy on top of the 3D FFT: the use the paper
+// accelerates (the 3D FFT on the critical path of plane-wave DFT in AIMD,
+// section "Introduction"; CP2K's Gaussian and plane-wave method, section
+// "Results").  The paper gives no formulas for this part; these are the
+// standard ones for a periodic cubic cell of side L and volume Omega = L^3
+// sampled on an n^3 grid:
+//
+//   rho_hat(G) = F(rho)(G) / n^3          (F: forward transform of Eq. 1)
+//   E_H = (Omega/2) sum_{G != 0} 4 pi |rho_hat(G)|^2 / |G|^2
+//   G = (2 pi / L) m,  m_d = k_d for k_d < n/2 else k_d - n
+//   dE_H / drho_j = (Omega / n^6) Re[ F^H (K F(rho)) ]_j,  K = 4 pi / |G|^2
+//
+// so that with s = Omega 4 pi / (n^6 (2 pi / L)^2):
+//   E_H = (s/2) sum_{m != 0} |F(rho)(m)|^2 / |m|^2
+//   seed(m) = dL/dE_H * s * F(rho)(m) / |m|^2,   dL/drho = Re F^H(seed).
+//
+// The energy is accumulated in FP64 (the only FP64 on the GPU) with a fixed
+// reduction order, so repeated calls give bit-identical results.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "fft3d.h"
+
+namespace fft3d {
+namespace {
+
+constexpr int kRedThreads = 256;
+
+__host__ __device__ inline int energy_blocks(long long npts) {
+  long long b = (npts + kRedThreads * 8 - 1) / (kRedThreads * 8);
+  return (int)(b < 1 ? 1 : (b > 512 ? 512 : b));
+}
+
+__device__ __forceinline__ int signed_index(int k, int n) { return k < (n + 1) / 2 ? k : k - n; }
+
+__device__ __forceinline__ int m_squared(long long i, int n) {
+  const int kx = (int)(i % n), ky = (int)((i / n) % n), kz = (int)(i / ((long long)n * n));
+  const int mx = signed_index(kx, n), my = signed_index(ky, n), mz = signed_index(kz, n);
+  return mx * mx + my * my + mz * mz;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// One row of blocks per grid (blockIdx.y).  partials: [batch][gridDim.x];
+// counters: [batch], zero on entry, left at zero by the last block.
+__global__ void __launch_bounds__(kRedThreads) hartree_energy_kernel(
+    const float2* __restrict__ f, int n, long long npts, double half_s,
+    double* __restrict__ partials, unsigned* __restrict__ counters, double* __restrict__ energy) {
+  const int b = blockIdx.y;
+  const float2* fb = f + (long long)b * npts;
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * kRedThreads + threadIdx.x; i < npts;
+       i += (long long)gridDim.x * kRedThreads) {
+    const int m2 = m_squared(i, n);
+    if (m2 != 0) {
+      const float2 v = fb[i];
+      const float inv = 1.0f / (float)m2;
+      acc += ((double)v.x * v.x + (double)v.y * v.y) * (double)inv;
+    }
+  }
+  __shared__ double warp_part[kRedThreads / 32];
+  __shared__ int is_last;
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) warp_part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < kRedThreads / 32; ++w) s += warp_part[w];
+    partials[(long long)b * gridDim.x + blockIdx.x] = s;
+    __threadfence();
+    is_last = atomicAdd(&counters[b], 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (is_last && threadIdx.x == 0) {
+    __threadfence();
+    double s = 0.0;
+    const volatile double* p = partials + (long long)b * gridDim.x;
+    for (unsigned j = 0; j < gridDim.x; ++j) s += p[j];
+    energy[b] = half_s * s;
+    counters[b] = 0u;
+  }
+}
+
+__global__ void hartree_seed_kernel(const float2* __restrict__ f, int n, long long npts, double s,
+                                    const double* __restrict__ grad_e, float2* __restrict__ seed) {
+  const int b = blockIdx.y;
+  const float scale = (float)(s * grad_e[b]);
+  const float2* fb = f + (long long)b * npts;
+  float2* sb = seed + (long long)b * npts;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < npts;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int m2 = m_squared(i, n);
+    float2 o = make_float2(0.0f, 0.0f);
+    if (m2 != 0) {
+      const float2 v = fb[i];
+      const float w = scale / (float)m2;
+      o = make_float2(v.x * w, v.y * w);
+    }
+    sb[i] = o;
+  }
+}
+
+__global__ void real_to_complex_kernel(const float* __restrict__ re, float2* __restrict__ out,
+                                       long long count) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = make_float2(re[i], 0.0f);
+}
+
+__global__ void complex_to_real_kernel(const float2* __restrict__ in, float* __restrict__ re,
+                                       long long count) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    re[i] = in[i].x;
+}
+
+int grid_for(long long count, int threads) {
+  long long b = (count + threads - 1) / threads;
+  return (int)(b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b));
+}
+
+bool valid_grid(int n, int batch, double L) {
+  return n >= 2 && n <= 1024 && batch >= 1 && batch <= 65535 && L > 0.0 && std::isfinite(L);
+}
+
+// s = Omega 4 pi / (n^6 (2 pi / L)^2)
+double hartree_s(int n, double L) {
+  const double n3 = (double)n * n * n, g = 2.0 * 3.14159265358979323846 / L;
+  return L * L * L * 4.0 * 3.14159265358979323846 / (n3 * n3 * g * g);
+}
+
+}  // namespace
+}  // namespace fft3d
+
+using namespace fft3d;
+
+extern "C" {
+
+size_t fft3d_hartree_workspace_bytes(int n, int batch) {
+  if (n < 2 || batch < 1) return 0;
+  const long long npts = (long long)n * n * n;
+  const size_t partials = sizeof(double) * (size_t)batch * (size_t)energy_blocks(npts);
+  return ((partials + 255) & ~size_t(255)) + sizeof(unsigned) * (size_t)batch;
+}
+
+int fft3d_hartree_energy(const void* rhohat, int n, int batch, double L, double* energy,
+                         void* workspace, size_t workspace_bytes, void* stream) {
+  if (!rhohat || !energy || !workspace) return FFT3D_ERR_NULL_PTR;
+  if (!valid_grid(n, batch, L)) return FFT3D_ERR_INVALID_ARG;
+  if (workspace_bytes < fft3d_hartree_workspace_bytes(n, batch)) return FFT3D_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(rhohat) & 7u || reinterpret_cast<uintptr_t>(workspace) & 7u)
+    return FFT3D_ERR_MISALIGNED;
+  const long long npts = (long long)n * n * n;
+  const int blocks = energy_blocks(npts);
+  const size_t partial_bytes = sizeof(double) * (size_t)batch * (size_t)blocks;
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  unsigned* counters = reinterpret_cast<unsigned*>(ws + ((partial_bytes + 255) & ~size_t(255)));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(counters, 0, sizeof(unsigned) * (size_t)batch, s) != cudaSuccess) {
+    cudaGetLastError();
+    return FFT3D_ERR_CUDA;
+  }
+  hartree_energy_kernel<<<dim3(blocks, batch), kRedThreads, 0, s>>>(
+      static_cast<const float2*>(rhohat), n, npts, 0.5 * hartree_s(n, L),
+      reinterpret_cast<double*>(ws), counters, energy);
+  if (cudaGetLastError() != cudaSuccess) return FFT3D_ERR_CUDA;
+  return FFT3D_SUCCESS;
+}
+
+int fft3d_hartree_seed(const void* rhohat, int n, int batch, double L, const double* grad_energy,
+                       void* seed, void* stream) {
+  if (!rhohat || !grad_energy || !seed) return FFT3D_ERR_NULL_PTR;
+  if (!valid_grid(n, batch, L)) return FFT3D_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(rhohat) & 7u || reinterpret_cast<uintptr_t>(seed) & 7u)
+    return FFT3D_ERR_MISALIGNED;
+  const long long npts = (long long)n * n * n;
+  const int bx = grid_for(npts, 256) / batch + 1;
+  hartree_seed_kernel<<<dim3(bx, batch), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      static_cast<const float2*>(rhohat), n, npts, hartree_s(n, L), grad_energy,
+      static_cast<float2*>(seed));
+  if (cudaGetLastError() != cudaSuccess) return FFT3D_ERR_CUDA;
+  return FFT3D_SUCCESS;
+}
+
+int fft3d_real_to_complex(const float* re, void* out, int64_t count, void* stream) {
+  if (!re || !out) return FFT3D_ERR_NULL_PTR;
+  if (count < 0) return FFT3D_ERR_INVALID_ARG;
+  if (count == 0) return FFT3D_SUCCESS;
+  real_to_complex_kernel<<<grid_for(count, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      re, static_cast<float2*>(out), count);
+  return cudaGetLastError() == cudaSuccess ? FFT3D_SUCCESS : FFT3D_ERR_CUDA;
+}
+
+int fft3d_complex_to_real(const void* in, float* re, int64_t count, void* stream) {
+  if (!in || !re) return FFT3D_ERR_NULL_PTR;
+  if (count < 0) return FFT3D_ERR_INVALID_ARG;
+  if (count == 0) return FFT3D_SUCCESS;
+  complex_to_real_kernel<<<grid_for(count, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      static_cast<const float2*>(in), re, count);
+  return cudaGetLastError() == cudaSuccess ? FFT3D_SUCCESS : FFT3D_ERR_CUDA;
+}
+
+}  // extern "C"
