@@ -100,8 +100,9 @@ int fft3d_twiddle_table(int n, float* out, int* l1, int* l2);
  * Plan `batch` grids of nx*ny*nz points (Eq. 1 per grid).
  *   nx, ny, nz : edge lengths, each fft3d_size_supported.
  *   batch      : number of grids, >= 1, packed back to back.
- *   precision  : fft3d_precision; the split/FP16 forms need cubic grids whose
- *                edge is a multiple of 16.
+ *   precision  : fft3d_precision; the tensor-core kinds (SPLIT_FP16,
+ *                SPLIT_BF16, FP16) are planned for cubic n = 64 and 128
+ *                (FFT3D_ERR_UNSUPPORTED_PRECISION otherwise).
  *   direction  : FFT3D_FORWARD or FFT3D_INVERSE.
  *   norm       : fft3d_norm.
  *   out_plan   : receives the handle (set to NULL on failure).

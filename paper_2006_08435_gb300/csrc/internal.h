@@ -40,6 +40,7 @@ struct FusedArgs {
   float scale;                  // output scale of the last pass
   int do_scale;
   long long timeout_ns;
+  const uint32_t* mma_frag;     // tensor-core B fragments (split precisions), or null
 };
 
 using LaunchFn = cudaError_t (*)(const FusedArgs&, int grid, cudaStream_t);
@@ -53,11 +54,13 @@ struct KernelInfo {
   int sizes[8] = {0};           // edges handled, in table order
   int nsizes = 0;
   int items_in_flight = 1;      // work items a block holds at once (schedule lag)
+  int prec = 0;                 // 0 FP32, else fft3d_precision of the tensor-core kinds
 };
 
 // Defined in the inst_*.cu translation units.
 KernelInfo fused_kernel_info(int n, int dir, int variant);   // single-size kernel
 KernelInfo mixed_kernel_info(int dir);          // all fused sizes
+KernelInfo tc_kernel_info(int n, int dir, int prec);  // tensor-core radix-16 kinds
 cudaError_t launch_wait_selftest(unsigned* flag, unsigned* status, long long timeout_ns,
                                  cudaStream_t stream);
 

@@ -27,6 +27,7 @@
 #include "codelets.cuh"
 #include "internal.h"
 #include "sizes.h"
+#include "tc_stage.cuh"
 
 namespace fft3d {
 
@@ -82,10 +83,10 @@ constexpr int plane_pitch() { return N + 1; }
 template <int N>
 constexpr int tile_elems() { return N * (N + 1); }
 
-template <int N, int T, int DIR>
+template <int N, int T, int DIR, int PREC = 0>
 __device__ __forceinline__ void plane_item(const float2* __restrict__ src, float2* __restrict__ dst,
-                                           float2* tile, const float2* tw) {
-  constexpr int L1 = split_l1(N), L2 = split_l2(N), P = plane_pitch<N>();
+                                           float2* tile, const float2* tw, const uint32_t* frag) {
+  constexpr int L1 = item_l1(N, PREC), L2 = N / L1, P = plane_pitch<N>();
   const int tid = threadIdx.x;
 
   // (1) plane -> shared memory
@@ -107,7 +108,17 @@ __device__ __forceinline__ void plane_item(const float2* __restrict__ src, float
 
   // (2) x, first step: per row, L1 DFTs of length L2 on stride-L1 points,
   //     times W_N^(n1 k2), in place.  Lanes walk rows.
-  {
+  if constexpr (PREC != 0) {
+    // 16 rows with the same n1 per warp and group, on tensor cores
+    for (int grp = tid >> 5; grp < N * L1 / 16; grp += T / 32) {
+      const int n1 = (grp * 16) / N, row0 = (grp * 16) % N;
+      tc::dft16_group<PREC, DIR>(
+          frag, [&](int v, int j) { return tile[(row0 + v) * P + n1 + L1 * j]; },
+          [&](int v, int k, float2 y) {
+            tile[(row0 + v) * P + n1 + L1 * k] = cmul_tw<DIR>(y, tw[k * L1 + n1]);
+          });
+    }
+  } else {
     constexpr int IA = N * L1, PA = (IA + T - 1) / T;
 #pragma unroll
     for (int i = 0; i < PA; ++i) {
@@ -159,7 +170,16 @@ __device__ __forceinline__ void plane_item(const float2* __restrict__ src, float
   __syncthreads();
 
   // (4) y, first step, lanes walk columns.
-  {
+  if constexpr (PREC != 0) {
+    for (int grp = tid >> 5; grp < N * L1 / 16; grp += T / 32) {
+      const int n1 = (grp * 16) / N, col0 = (grp * 16) % N;
+      tc::dft16_group<PREC, DIR>(
+          frag, [&](int v, int j) { return tile[(n1 + L1 * j) * P + col0 + v]; },
+          [&](int v, int k, float2 y) {
+            tile[(n1 + L1 * k) * P + col0 + v] = cmul_tw<DIR>(y, tw[k * L1 + n1]);
+          });
+    }
+  } else {
     constexpr int IA = N * L1, PA = (IA + T - 1) / T;
 #pragma unroll
     for (int i = 0; i < PA; ++i) {
@@ -202,13 +222,23 @@ __device__ __forceinline__ void plane_item(const float2* __restrict__ src, float
 
 // Slab item: src/dst point at (x = 0, y, z = 0) of a grid; element (x, z)
 // of the slab is at x + z * N * N.
-template <int N, int T, int DIR>
+template <int N, int T, int DIR, int PREC = 0>
 __device__ __forceinline__ void slab_item(const float2* src, float2* dst, float2* tile,
-                                          const float2* tw, float scale, int do_scale) {
-  constexpr int L1 = split_l1(N), L2 = split_l2(N);
+                                          const float2* tw, const uint32_t* frag, float scale,
+                                          int do_scale) {
+  constexpr int L1 = item_l1(N, PREC), L2 = N / L1;
   constexpr long long NN = (long long)N * N;
   const int tid = threadIdx.x;
-  {
+  if constexpr (PREC != 0) {
+    for (int grp = tid >> 5; grp < N * L1 / 16; grp += T / 32) {
+      const int n1 = (grp * 16) / N, x0 = (grp * 16) % N;
+      tc::dft16_group<PREC, DIR>(
+          frag, [&](int v, int j) { return ld_l2(src + (n1 + L1 * j) * NN + x0 + v); },
+          [&](int v, int k, float2 y) {
+            tile[(n1 + L1 * k) * N + x0 + v] = cmul_tw<DIR>(y, tw[k * L1 + n1]);
+          });
+    }
+  } else {
     constexpr int IA = N * L1, PA = (IA + T - 1) / T;
     float2 v[PA][L2];
 #pragma unroll
@@ -266,7 +296,11 @@ struct SizeList {
     ((m = tile_elems<Ns>() > m ? tile_elems<Ns>() : m), ...);
     return m;
   }();
-  static constexpr size_t smem_bytes = sizeof(float2) * (size_t)(tw_total + max_tile);
+  // twiddles, tensor-core B fragments (when used), tile
+  static constexpr size_t smem_bytes(int prec) {
+    return sizeof(float2) * (size_t)(tw_total + max_tile) +
+           (prec ? sizeof(uint32_t) * tc::kFragWords : 0);
+  }
 };
 
 // Offset of edge n's table inside the concatenation of the list's tables.
@@ -290,18 +324,18 @@ __device__ __forceinline__ void grid_ptrs(const FusedArgs& a, int g, int n, cons
   }
 }
 
-template <int N, int T, int DIR>
+template <int N, int T, int DIR, int PREC>
 __device__ __forceinline__ void run_item(const FusedArgs& a, const SchedBlock& blk, int i,
-                                         float2* tile, const float2* tw) {
+                                         float2* tile, const float2* tw, const uint32_t* frag) {
   const float2* gin;
   float2* gout;
   grid_ptrs(a, blk.grid, N, gin, gout);
   if (blk.phase == 0) {
     const long long o = (long long)i * N * N;
-    plane_item<N, T, DIR>(gin + o, gout + o, tile, tw);
+    plane_item<N, T, DIR, PREC>(gin + o, gout + o, tile, tw, frag);
   } else {
-    slab_item<N, T, DIR>(gout + (long long)i * N, gout + (long long)i * N, tile, tw, a.scale,
-                         a.do_scale);
+    slab_item<N, T, DIR, PREC>(gout + (long long)i * N, gout + (long long)i * N, tile, tw, frag,
+                               a.scale, a.do_scale);
   }
 }
 
@@ -314,14 +348,17 @@ __device__ __forceinline__ int find_block(const SchedBlock* blocks, int nblocks,
   return lo;
 }
 
-template <int T, int DIR, int... Ns>
+template <int T, int DIR, int PREC, int... Ns>
 __global__ void __launch_bounds__(T) fused_fft3d_kernel(const FusedArgs a) {
   extern __shared__ __align__(16) float2 smem[];
   __shared__ int s_item, s_blk;
   using L = SizeList<Ns...>;
   float2* tws = smem;
-  float2* tile = smem + L::tw_total;
+  uint32_t* frag = reinterpret_cast<uint32_t*>(smem + L::tw_total);
+  float2* tile = smem + L::tw_total + (PREC ? tc::kFragWords / 2 : 0);
   for (int i = threadIdx.x; i < L::tw_total; i += T) tws[i] = a.twiddles[i];
+  if constexpr (PREC != 0)
+    for (int i = threadIdx.x; i < tc::kFragWords; i += T) frag[i] = a.mma_frag[i];
 
   for (;;) {
     if (threadIdx.x == 0) {
@@ -343,7 +380,9 @@ __global__ void __launch_bounds__(T) fused_fft3d_kernel(const FusedArgs a) {
     if (item < 0) break;
     const SchedBlock blk = a.blocks[s_blk];
     const int i = item - blk.start;
-    ((blk.n == Ns ? (run_item<Ns, T, DIR>(a, blk, i, tile, tws + tw_offset<Ns...>(Ns)), 0) : 0), ...);
+    ((blk.n == Ns ? (run_item<Ns, T, DIR, PREC>(a, blk, i, tile, tws + tw_offset<Ns...>(Ns), frag), 0)
+                  : 0),
+     ...);
     __syncthreads();
     if (blk.phase == 0 && threadIdx.x == 0) {
       __threadfence();
@@ -352,24 +391,31 @@ __global__ void __launch_bounds__(T) fused_fft3d_kernel(const FusedArgs a) {
   }
 }
 
-template <int T, int DIR, int... Ns>
+template <int T, int DIR, int PREC, int... Ns>
 cudaError_t launch_fused(const FusedArgs& a, int grid, cudaStream_t stream) {
-  fused_fft3d_kernel<T, DIR, Ns...><<<grid, T, SizeList<Ns...>::smem_bytes, stream>>>(a);
+  fused_fft3d_kernel<T, DIR, PREC, Ns...>
+      <<<grid, T, SizeList<Ns...>::smem_bytes(PREC), stream>>>(a);
   return cudaGetLastError();
 }
 
-template <int T, int DIR, int... Ns>
-KernelInfo make_fused_info() {
+template <int T, int DIR, int PREC, int... Ns>
+KernelInfo make_fused_info_prec() {
   KernelInfo k;
-  k.launch = &launch_fused<T, DIR, Ns...>;
-  k.func = (const void*)&fused_fft3d_kernel<T, DIR, Ns...>;
+  k.launch = &launch_fused<T, DIR, PREC, Ns...>;
+  k.func = (const void*)&fused_fft3d_kernel<T, DIR, PREC, Ns...>;
   k.threads = T;
-  k.smem = SizeList<Ns...>::smem_bytes;
+  k.smem = SizeList<Ns...>::smem_bytes(PREC);
+  k.prec = PREC;
   k.twiddle_entries = SizeList<Ns...>::tw_total;
   const int sizes[] = {Ns...};
   k.nsizes = (int)sizeof...(Ns);
   for (int i = 0; i < k.nsizes; ++i) k.sizes[i] = sizes[i];
   return k;
+}
+
+template <int T, int DIR, int... Ns>
+KernelInfo make_fused_info() {
+  return make_fused_info_prec<T, DIR, 0, Ns...>();
 }
 
 }  // namespace fft3d

@@ -1,6 +1,8 @@
 // Host side of the C ABI: argument validation, planning (size split,
 // FP64 twiddle tables rounded to FP32, work schedule), device buffers and
 // launches.  See include/fft3d.h for the contract of each entry point.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -14,6 +16,7 @@
 #include "../../include/fft3d.h"
 #include "internal.h"
 #include "sizes.h"
+#include "tc_stage.cuh"
 
 namespace fft3d {
 
@@ -24,6 +27,17 @@ KernelInfo fused_kernel_info_n64(int dir, int variant);
 KernelInfo fused_kernel_info_n80(int dir, int variant);
 KernelInfo fused_kernel_info_n96(int dir, int variant);
 KernelInfo fused_kernel_info_n128(int dir, int variant);
+KernelInfo tc_kernel_info_n64(int dir, int prec);
+KernelInfo tc_kernel_info_n128(int dir, int prec);
+
+KernelInfo tc_kernel_info(int n, int dir, int prec) {
+  switch (n) {
+    case 64: return tc_kernel_info_n64(dir, prec);
+    case 128: return tc_kernel_info_n128(dir, prec);
+    default: return KernelInfo{};
+  }
+}
+static bool tc_size(int n) { return n == 64 || n == 128; }
 
 KernelInfo fused_kernel_info(int n, int dir, int variant) {
   switch (n) {
@@ -38,11 +52,12 @@ KernelInfo fused_kernel_info(int n, int dir, int variant) {
   }
 }
 
-// W_n^m = exp(-2 pi i m / n) for the table entry (n1, k2) of edge n:
-// tw[k2 * L1 + n1] = W_n^((n1 * k2) mod n), evaluated in FP64 by the host
-// math library on the reduced exponent and rounded to nearest FP32.
-static void twiddle_table(int n, float* out /* 2 * n floats */) {
-  const int l1 = split_l1(n), l2 = split_l2(n);
+// W_n^m = exp(-2 pi i m / n) for the table entry (n1, k2) of edge n split
+// as n = l1 * l2: tw[k2 * l1 + n1] = W_n^((n1 * k2) mod n), evaluated in FP64
+// by the host math library on the reduced exponent and rounded to nearest
+// FP32.
+static void twiddle_table(int n, int l1, float* out /* 2 * n floats */) {
+  const int l2 = n / l1;
   for (int k2 = 0; k2 < l2; ++k2)
     for (int n1 = 0; n1 < l1; ++n1) {
       const int m = (n1 * k2) % n;
@@ -50,6 +65,48 @@ static void twiddle_table(int n, float* out /* 2 * n floats */) {
       out[2 * (k2 * l1 + n1)] = (float)std::cos(a);
       out[2 * (k2 * l1 + n1) + 1] = (float)(-std::sin(a));
     }
+}
+
+// B fragments of the tensor-core radix-16 stage (layout in tc_stage.cuh):
+// the 32 x 32 real form of the forward DFT_16 matrix, B[2j+c][2k+d] from
+// W_16^(jk) = wr + i wi: (c,d) = (0,0) wr, (1,0) -wi, (0,1) wi, (1,1) wr,
+// evaluated in FP64, split as hi = rn(b), lo = rn(b - hi) in FP16 (prec 1,
+// 3) or BF16 (prec 2).
+static void mma_fragments(int prec, uint32_t* out /* tc::kFragWords */) {
+  auto entry = [](int kr, int nr) {
+    const int j = kr / 2, c = kr % 2, k = nr / 2, d = nr % 2;
+    const double a = -2.0 * 3.14159265358979323846 * (double)((j * k) % 16) / 16.0;
+    const double wr = std::cos(a), wi = std::sin(a);
+    return c == 0 ? (d == 0 ? wr : wi) : (d == 0 ? -wi : wr);
+  };
+  auto split = [prec](double v, unsigned short& hi, unsigned short& lo) {
+    if (prec == 2) {
+      const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+      const __nv_bfloat16 l = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
+      hi = __bfloat16_as_ushort(h);
+      lo = __bfloat16_as_ushort(l);
+    } else {
+      const __half h = __float2half_rn((float)v);
+      const __half l = __float2half_rn((float)(v - (double)__half2float(h)));
+      hi = __half_as_ushort(h);
+      lo = __half_as_ushort(l);
+    }
+  };
+  for (int term = 0; term < 2; ++term)
+    for (int s = 0; s < 2; ++s)
+      for (int u = 0; u < 4; ++u)
+        for (int lane = 0; lane < 32; ++lane) {
+          const int g = lane >> 2, t = lane & 3, col = 8 * u + g;
+          for (int reg = 0; reg < 2; ++reg) {
+            const int r0 = 16 * s + 2 * t + 8 * reg;
+            unsigned short h0, l0, h1, l1;
+            split(entry(r0, col), h0, l0);
+            split(entry(r0 + 1, col), h1, l1);
+            const unsigned short a0 = term ? l0 : h0, a1 = term ? l1 : h1;
+            out[(((term * 2 + s) * 4 + u) * 32 + lane) * 2 + reg] =
+                (uint32_t)a0 | ((uint32_t)a1 << 16);
+          }
+        }
 }
 
 static bool fused_size(int n) { return fused_slot(n) >= 0; }
@@ -84,6 +141,7 @@ struct fft3d_plan_s {
   long long timeout_ns = kDefaultWaitNs;
   // device buffers (owned)
   float2* d_tw = nullptr;
+  uint32_t* d_frag = nullptr;
   SchedBlock* d_blocks = nullptr;
   long long* d_off = nullptr;
   unsigned* d_work = nullptr;
@@ -98,11 +156,13 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 void free_plan_buffers(fft3d_plan p) {
   if (!p) return;
   cudaFree(p->d_tw);
+  cudaFree(p->d_frag);
   cudaFree(p->d_blocks);
   cudaFree(p->d_off);
   cudaFree(p->d_work);
   cudaFree(p->d_status);
   p->d_tw = nullptr;
+  p->d_frag = nullptr;
   p->d_blocks = nullptr;
   p->d_off = nullptr;
   p->d_work = nullptr;
@@ -198,8 +258,20 @@ int finish_plan(fft3d_plan p, const std::vector<int>& order) {
   std::vector<float> tw(2 * (size_t)p->kernel.twiddle_entries);
   size_t off = 0;
   for (int i = 0; i < p->kernel.nsizes; ++i) {
-    twiddle_table(p->kernel.sizes[i], tw.data() + 2 * off);
-    off += p->kernel.sizes[i];
+    const int n = p->kernel.sizes[i];
+    twiddle_table(n, item_l1(n, p->kernel.prec), tw.data() + 2 * off);
+    off += n;
+  }
+  if (p->kernel.prec) {
+    std::vector<uint32_t> frag(tc::kFragWords);
+    mma_fragments(p->kernel.prec, frag.data());
+    if (cudaMalloc(&p->d_frag, frag.size() * sizeof(uint32_t)) != cudaSuccess) {
+      cudaGetLastError();
+      return FFT3D_ERR_ALLOC;
+    }
+    if (cudaMemcpy(p->d_frag, frag.data(), frag.size() * sizeof(uint32_t),
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+      return FFT3D_ERR_CUDA;
   }
   const int count = (int)p->dims.size();
   p->work_bytes = sizeof(unsigned) * (size_t)(1 + count);
@@ -269,6 +341,7 @@ int launch(fft3d_plan p, const float2* in, float2* out, const float2* const* in_
   a.scale = p->scale;
   a.do_scale = p->do_scale;
   a.timeout_ns = p->timeout_ns;
+  a.mma_frag = p->d_frag;
   if (p->kernel.launch(a, p->grid, stream) != cudaSuccess) {
     cudaGetLastError();
     return FFT3D_ERR_CUDA;
@@ -285,7 +358,7 @@ int fft3d_size_supported(int n) { return fused_size(n) ? 1 : 0; }
 int fft3d_twiddle_table(int n, float* out, int* l1, int* l2) {
   if (!out || !l1 || !l2) return FFT3D_ERR_NULL_PTR;
   if (!fused_size(n)) return FFT3D_ERR_UNSUPPORTED_SIZE;
-  twiddle_table(n, out);
+  twiddle_table(n, split_l1(n), out);
   *l1 = split_l1(n);
   *l2 = split_l2(n);
   return FFT3D_SUCCESS;
@@ -298,7 +371,7 @@ int fft3d_plan_create(int nx, int ny, int nz, int batch, int precision, int dire
   if (nx < 1 || ny < 1 || nz < 1 || batch < 1) return FFT3D_ERR_INVALID_ARG;
   if (batch > (1 << 24)) return FFT3D_ERR_INVALID_ARG;
   if (!fused_size(nx) || nx != ny || ny != nz) return FFT3D_ERR_UNSUPPORTED_SIZE;
-  if (precision != FFT3D_FP32) return FFT3D_ERR_UNSUPPORTED_PRECISION;
+  if (precision != FFT3D_FP32 && !tc_size(nx)) return FFT3D_ERR_UNSUPPORTED_PRECISION;
   const long long pts = (long long)nx * ny * nz;
   // ticket counters are 32-bit: 2 * n items per grid
   if ((long long)batch * 2 * nx >= (1LL << 31)) return FFT3D_ERR_INVALID_ARG;
@@ -314,7 +387,8 @@ int fft3d_plan_create(int nx, int ny, int nz, int batch, int precision, int dire
   for (int g = 0; g < batch; ++g) p->offsets[g] = (long long)g * pts;
   p->total_points = pts * batch;
   set_scale(p, (double)pts);
-  p->kernel = fused_kernel_info(nx, direction, default_variant(nx));
+  p->kernel = precision == FFT3D_FP32 ? fused_kernel_info(nx, direction, default_variant(nx))
+                                      : tc_kernel_info(nx, direction, precision);
   std::vector<int> order(batch);
   for (int g = 0; g < batch; ++g) order[g] = g;
   rc = finish_plan(p, order);

@@ -21,6 +21,11 @@ __host__ __device__ constexpr int split_l1(int n) {
 __host__ __device__ constexpr int split_l2(int n) {
   return split_l1(n) ? n / split_l1(n) : 0;
 }
+// Split used by a kernel: the FP32 kernels use split_l1; the tensor-core
+// kinds (prec != 0) always make the first step radix 16, n = (n/16) * 16.
+__host__ __device__ constexpr int item_l1(int n, int prec) {
+  return prec ? n / 16 : split_l1(n);
+}
 // Threads per block of the single-size persistent kernel for edge n.
 __host__ __device__ constexpr int fused_threads(int n) {
   return n == 16 ? 64 : n == 32 ? 128 : n == 48 ? 192 : n == 64 ? 256
