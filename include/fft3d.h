@@ -170,6 +170,45 @@ const char* fft3d_error_string(int code);
 int fft3d_selftest_wait_timeout(int64_t timeout_ns);
 
 /*
+ * The kernel variant a plan uses (written to *variant).  Single-edge FP32
+ * plans: 0 plain persistent kernel, 1 the same with twice the threads per
+ * block, 2 the TMA-fed warp-specialised kernel (64^3, 128^3).  Mixed plans:
+ * 0 one launch of the mixed-edge kernel, 1 one launch per distinct edge.
+ * At create the variant comes from FFT3D_VARIANT / FFT3D_MIXED_VARIANT if
+ * set, else from the tuning cache named by FFT3D_TUNE_CACHE (tuned on the
+ * spot when FFT3D_TUNE=1 and the entry is missing), else a built-in default.
+ */
+int fft3d_plan_variant(fft3d_plan plan, int* variant);
+
+/* Milliseconds per execute of `variant`, or a negative value if it failed. */
+typedef double (*fft3d_tune_timer)(int variant, void* ctx);
+
+/*
+ * Autotuner core, usable without a GPU: if the JSON file `cache_path` (may
+ * be NULL) maps `key` to one of `candidates`, return it (*from_cache = 1,
+ * timer not called).  Otherwise time every candidate with `timer`, pick the
+ * fastest (ties: first), skip failed ones (FFT3D_ERR_CUDA if all failed) and
+ * record the choice in the file (atomic rewrite; unreadable entries are
+ * dropped).  from_cache may be NULL.
+ */
+int fft3d_tune_select(const char* key, int ncand, const int* candidates,
+                      fft3d_tune_timer timer, void* ctx, const char* cache_path,
+                      int* best_variant, int* from_cache);
+
+/*
+ * Time the variants of a (n^3 x batch, precision, direction) plan on the
+ * current device with CUDA events (allocates two temporary buffers of the
+ * problem's size), record the fastest under a key of device name, SM count
+ * and problem in `cache_path` (may be NULL), and return it.
+ */
+int fft3d_autotune(int n, int batch, int precision, int direction, const char* cache_path,
+                   int* best_variant);
+
+/* Same for a mixed plan of `count` cubic grids of edges dims[g]. */
+int fft3d_autotune_mixed(int count, const int* dims, int direction, const char* cache_path,
+                         int* best_variant);
+
+/*
  * ---------------------------------------------------------------------------
  * Plane-wave Hartree energy, the use of the 3D FFT in plane-wave DFT that the
  * paper accelerates (sections "Introduction" and "Results"; the formulas are

@@ -21,7 +21,7 @@ __all__ = ["fft3d", "Plan", "MixedPlan", "FFT3d", "FFT3DError", "size_supported"
 
 def __getattr__(name):
     if name in ("fft3d", "Plan", "MixedPlan", "FFT3d", "size_supported", "get_plan",
-                "twiddle_table", "selftest_wait_timeout"):
+                "twiddle_table", "selftest_wait_timeout", "autotune", "autotune_mixed"):
         from . import fft as _fft
         return getattr(_fft, name)
     if name in ("hartree_energy", "HartreeEnergy"):

@@ -48,6 +48,11 @@ _SIGS = {
     "fft3d_hartree_energy": (_I, [_VP, _I, _I, ctypes.c_double, _VP, _VP, ctypes.c_size_t, _VP]),
     "fft3d_hartree_seed": (_I, [_VP, _I, _I, ctypes.c_double, _VP, _VP, _VP]),
     "fft3d_real_to_complex": (_I, [_VP, _VP, ctypes.c_int64, _VP]),
+    "fft3d_plan_variant": (_I, [_VP, ctypes.POINTER(_I)]),
+    "fft3d_tune_select": (_I, [ctypes.c_char_p, _I, ctypes.POINTER(_I), _VP, _VP, ctypes.c_char_p,
+                               ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "fft3d_autotune": (_I, [_I, _I, _I, _I, ctypes.c_char_p, ctypes.POINTER(_I)]),
+    "fft3d_autotune_mixed": (_I, [_I, ctypes.POINTER(_I), _I, ctypes.c_char_p, ctypes.POINTER(_I)]),
     "fft3d_complex_to_real": (_I, [_VP, _VP, ctypes.c_int64, _VP]),
 }
 
@@ -76,6 +81,10 @@ def lib() -> ctypes.CDLL:
                 f.argtypes = args
             _lib = l
     return _lib
+
+
+# fft3d_tune_timer: double (*)(int variant, void* ctx)
+TUNE_TIMER = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_int, ctypes.c_void_p)
 
 
 class FFT3DError(RuntimeError):

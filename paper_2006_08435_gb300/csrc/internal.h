@@ -5,6 +5,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
+#include "fft3d.h"
+
 namespace fft3d {
 
 // Device status word values (sticky until read by fft3d_get_device_status).
@@ -31,6 +35,7 @@ struct FusedArgs {
   const float2* const* in_ptrs; // device array of per-grid inputs, or null
   float2* const* out_ptrs;      // device array of per-grid outputs, or null
   const long long* grid_off;    // per-grid element offsets, or null (g * n^3)
+  const int* grid_map;          // local grid -> plan grid index, or null (identity)
   const SchedBlock* blocks;
   int nblocks;
   int total_items;
@@ -63,5 +68,21 @@ KernelInfo mixed_kernel_info(int dir);          // all fused sizes
 KernelInfo tc_kernel_info(int n, int dir, int prec);  // tensor-core radix-16 kinds
 cudaError_t launch_wait_selftest(unsigned* flag, unsigned* status, long long timeout_ns,
                                  cudaStream_t stream);
+
+// Variant choice at plan creation (tune.cu): FFT3D_VARIANT / FFT3D_MIXED_VARIANT
+// override; else the FFT3D_TUNE_CACHE entry for this device and problem;
+// else, with FFT3D_TUNE=1, tune now (and record); else the built-in default.
+int pick_variant(bool mixed, int n, int batch, int precision, int direction, const int* dims,
+                 int count);
+std::vector<int> variant_candidates(bool mixed, int n, int precision);
+int builtin_default_variant(bool mixed, int n, int precision);
+
+}  // namespace fft3d
+
+// A plan with a forced variant (plan.cu), for the autotuner.
+int fft3d_internal_create_variant(bool mixed, int nx, int batch, int precision, int direction,
+                                  const int* dims, int count, int variant, fft3d_plan* out);
+
+namespace fft3d {
 
 }  // namespace fft3d

@@ -314,6 +314,7 @@ __host__ __device__ constexpr int tw_offset(int n) {
 // Input and output base of grid g (edge n) for either addressing mode.
 __device__ __forceinline__ void grid_ptrs(const FusedArgs& a, int g, int n, const float2*& gin,
                                           float2*& gout) {
+  if (a.grid_map) g = a.grid_map[g];
   if (a.in_ptrs) {
     gin = a.in_ptrs[g];
     gout = a.out_ptrs[g];

@@ -111,41 +111,56 @@ static void mma_fragments(int prec, uint32_t* out /* tc::kFragWords */) {
 
 static bool fused_size(int n) { return fused_slot(n) >= 0; }
 
-// Variant of the single-size kernel: FFT3D_VARIANT (0, 1 or 2) overrides
-// the default, which is the TMA-fed warp-specialised kernel (2) for 128^3
-// and the plain persistent kernel (0) otherwise.
-static int default_variant(int n) {
-  const char* e = std::getenv("FFT3D_VARIANT");
-  if (e && e[0] >= '0' && e[0] <= '2' && e[1] == 0) return e[0] - '0';
-  return n == 128 ? 2 : 0;
+// Kernel variants of a single-size FP32 plan: 0 plain persistent kernel,
+// 1 the same with twice the threads, 2 the TMA-fed warp-specialised kernel
+// (64^3 and 128^3 only).  Mixed plans: 0 one launch of the mixed-edge
+// kernel, 1 one launch per distinct edge with that edge's default kernel.
+std::vector<int> variant_candidates(bool mixed, int n, int precision) {
+  if (mixed) return {0, 1};
+  if (precision != FFT3D_FP32) return {0};
+  if (n == 64 || n == 128) return {0, 1, 2};
+  return {0, 1};
+}
+
+int builtin_default_variant(bool mixed, int n, int precision) {
+  return mixed || precision != FFT3D_FP32 ? 0 : (n == 128 ? 2 : 0);
 }
 
 }  // namespace fft3d
 
 using namespace fft3d;
 
+// One persistent launch: a kernel and the grids it transforms.  Local grid l
+// of the unit is grid grids[l] of the plan (device map d_map, or identity).
+struct Unit {
+  KernelInfo kernel;
+  std::vector<int> grids;
+  int grid = 0;          // persistent blocks launched
+  int total_items = 0;
+  int nblocks = 0;
+  float2* d_tw = nullptr;
+  uint32_t* d_frag = nullptr;
+  SchedBlock* d_blocks = nullptr;
+  unsigned* d_work = nullptr;
+  size_t work_bytes = 0;
+  int* d_map = nullptr;
+};
+
 struct fft3d_plan_s {
   int device = -1;
   int nx = 0, ny = 0, nz = 0, batch = 0;
   int precision = 0, direction = -1, norm = 0;
   bool mixed = false;
+  int variant = 0;
   std::vector<int> dims;             // per-grid edge
   std::vector<long long> offsets;    // per-grid element offset in packed buffers
   long long total_points = 0;
-  KernelInfo kernel;
-  int grid = 0;                      // persistent blocks launched
-  int total_items = 0;
-  int nblocks = 0;
   float scale = 1.0f;
   int do_scale = 0;
   long long timeout_ns = kDefaultWaitNs;
-  // device buffers (owned)
-  float2* d_tw = nullptr;
-  uint32_t* d_frag = nullptr;
-  SchedBlock* d_blocks = nullptr;
+  std::vector<Unit> units;
+  // device buffers shared by the units (owned)
   long long* d_off = nullptr;
-  unsigned* d_work = nullptr;
-  size_t work_bytes = 0;
   unsigned* d_status = nullptr;
 };
 
@@ -155,17 +170,21 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 
 void free_plan_buffers(fft3d_plan p) {
   if (!p) return;
-  cudaFree(p->d_tw);
-  cudaFree(p->d_frag);
-  cudaFree(p->d_blocks);
+  for (Unit& u : p->units) {
+    cudaFree(u.d_tw);
+    cudaFree(u.d_frag);
+    cudaFree(u.d_blocks);
+    cudaFree(u.d_work);
+    cudaFree(u.d_map);
+    u.d_tw = nullptr;
+    u.d_frag = nullptr;
+    u.d_blocks = nullptr;
+    u.d_work = nullptr;
+    u.d_map = nullptr;
+  }
   cudaFree(p->d_off);
-  cudaFree(p->d_work);
   cudaFree(p->d_status);
-  p->d_tw = nullptr;
-  p->d_frag = nullptr;
-  p->d_blocks = nullptr;
   p->d_off = nullptr;
-  p->d_work = nullptr;
   p->d_status = nullptr;
 }
 
@@ -187,7 +206,7 @@ int check_device() {
 
 // Ticket order.  Plane blocks are emitted grid after grid (in `order`); the
 // slab block of grid g is emitted once at least `concurrency` tickets (the
-// number of blocks resident at once) have been handed out after the last
+// number of items resident at once) have been handed out after the last
 // plane ticket of g, so a slab item rarely waits, or earlier when the grids
 // whose planes are done but whose slabs are not yet scheduled would exceed
 // `l2_budget` bytes (their intermediate must stay in L2).
@@ -230,74 +249,85 @@ std::vector<SchedBlock> build_schedule(const std::vector<int>& dims, const std::
   return blocks;
 }
 
-int finish_plan(fft3d_plan p, const std::vector<int>& order) {
-  cudaError_t e;
-  // kernel attributes and persistent grid size
-  e = cudaFuncSetAttribute(p->kernel.func, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)p->kernel.smem);
-  if (e != cudaSuccess) return FFT3D_ERR_CUDA;
-  int per_sm = 0, sms = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p->kernel.func, p->kernel.threads,
-                                                    p->kernel.smem);
-  if (e != cudaSuccess || per_sm < 1) return FFT3D_ERR_CUDA;
-  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
-  if (e != cudaSuccess) return FFT3D_ERR_CUDA;
-
-  int l2_bytes = 0;
-  if (cudaDeviceGetAttribute(&l2_bytes, cudaDevAttrL2CacheSize, p->device) != cudaSuccess)
-    return FFT3D_ERR_CUDA;
-  int total_items = 0;
-  const int resident = per_sm * sms;
-  std::vector<SchedBlock> blocks = build_schedule(
-      p->dims, order, resident * p->kernel.items_in_flight, 0.4 * (double)l2_bytes, &total_items);
-  p->total_items = total_items;
-  p->nblocks = (int)blocks.size();
-  p->grid = std::max(1, std::min(total_items, resident));
-
-  // twiddles for every edge the kernel handles, concatenated in its order
-  std::vector<float> tw(2 * (size_t)p->kernel.twiddle_entries);
-  size_t off = 0;
-  for (int i = 0; i < p->kernel.nsizes; ++i) {
-    const int n = p->kernel.sizes[i];
-    twiddle_table(n, item_l1(n, p->kernel.prec), tw.data() + 2 * off);
-    off += n;
-  }
-  if (p->kernel.prec) {
-    std::vector<uint32_t> frag(tc::kFragWords);
-    mma_fragments(p->kernel.prec, frag.data());
-    if (cudaMalloc(&p->d_frag, frag.size() * sizeof(uint32_t)) != cudaSuccess) {
-      cudaGetLastError();
-      return FFT3D_ERR_ALLOC;
-    }
-    if (cudaMemcpy(p->d_frag, frag.data(), frag.size() * sizeof(uint32_t),
-                   cudaMemcpyHostToDevice) != cudaSuccess)
-      return FFT3D_ERR_CUDA;
-  }
-  const int count = (int)p->dims.size();
-  p->work_bytes = sizeof(unsigned) * (size_t)(1 + count);
-  if (cudaMalloc(&p->d_tw, tw.size() * sizeof(float)) != cudaSuccess ||
-      cudaMalloc(&p->d_blocks, blocks.size() * sizeof(SchedBlock)) != cudaSuccess ||
-      cudaMalloc(&p->d_work, p->work_bytes) != cudaSuccess ||
-      cudaMalloc(&p->d_status, sizeof(unsigned)) != cudaSuccess) {
+template <class T>
+int upload(T** dst, const T* src, size_t count) {
+  if (cudaMalloc(dst, sizeof(T) * count) != cudaSuccess) {
     cudaGetLastError();
     return FFT3D_ERR_ALLOC;
   }
-  if (p->mixed) {
-    if (cudaMalloc(&p->d_off, sizeof(long long) * (size_t)count) != cudaSuccess) {
-      cudaGetLastError();
-      return FFT3D_ERR_ALLOC;
-    }
-    if (cudaMemcpy(p->d_off, p->offsets.data(), sizeof(long long) * (size_t)count,
-                   cudaMemcpyHostToDevice) != cudaSuccess)
-      return FFT3D_ERR_CUDA;
-  }
-  if (cudaMemcpy(p->d_tw, tw.data(), tw.size() * sizeof(float), cudaMemcpyHostToDevice) !=
-          cudaSuccess ||
-      cudaMemcpy(p->d_blocks, blocks.data(), blocks.size() * sizeof(SchedBlock),
-                 cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemset(p->d_work, 0, p->work_bytes) != cudaSuccess ||
-      cudaMemset(p->d_status, 0, sizeof(unsigned)) != cudaSuccess)
+  if (cudaMemcpy(*dst, src, sizeof(T) * count, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
     return FFT3D_ERR_CUDA;
+  }
+  return FFT3D_SUCCESS;
+}
+
+// Device buffers and launch geometry of one unit; `identity` units address
+// grids by their own index (no map).  Local grids are scheduled largest
+// edge first.
+int finish_unit(fft3d_plan p, Unit& u, bool identity) {
+  cudaError_t e = cudaFuncSetAttribute(u.kernel.func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)u.kernel.smem);
+  if (e != cudaSuccess) return FFT3D_ERR_CUDA;
+  int per_sm = 0, sms = 0, l2_bytes = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, u.kernel.func, u.kernel.threads,
+                                                    u.kernel.smem);
+  if (e != cudaSuccess || per_sm < 1) return FFT3D_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&l2_bytes, cudaDevAttrL2CacheSize, p->device) != cudaSuccess)
+    return FFT3D_ERR_CUDA;
+  const int m = (int)u.grids.size();
+  std::vector<int> ldims(m), order(m);
+  for (int l = 0; l < m; ++l) {
+    ldims[l] = p->dims[u.grids[l]];
+    order[l] = l;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ldims[a] > ldims[b]; });
+  const int resident = per_sm * sms;
+  int total_items = 0;
+  const std::vector<SchedBlock> blocks = build_schedule(
+      ldims, order, resident * u.kernel.items_in_flight, 0.4 * (double)l2_bytes, &total_items);
+  u.total_items = total_items;
+  u.nblocks = (int)blocks.size();
+  u.grid = std::max(1, std::min(total_items, resident));
+
+  // twiddles for every edge the kernel handles, concatenated in its order
+  std::vector<float> tw(2 * (size_t)u.kernel.twiddle_entries);
+  size_t off = 0;
+  for (int i = 0; i < u.kernel.nsizes; ++i) {
+    const int n = u.kernel.sizes[i];
+    twiddle_table(n, item_l1(n, u.kernel.prec), tw.data() + 2 * off);
+    off += n;
+  }
+  int rc;
+  if ((rc = upload(&u.d_tw, reinterpret_cast<const float2*>(tw.data()), tw.size() / 2))) return rc;
+  if (u.kernel.prec) {
+    std::vector<uint32_t> frag(tc::kFragWords);
+    mma_fragments(u.kernel.prec, frag.data());
+    if ((rc = upload(&u.d_frag, frag.data(), frag.size()))) return rc;
+  }
+  if ((rc = upload(&u.d_blocks, blocks.data(), blocks.size()))) return rc;
+  if (!identity && (rc = upload(&u.d_map, u.grids.data(), u.grids.size()))) return rc;
+  u.work_bytes = sizeof(unsigned) * (size_t)(1 + m);
+  if (cudaMalloc(&u.d_work, u.work_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return FFT3D_ERR_ALLOC;
+  }
+  if (cudaMemset(u.d_work, 0, u.work_bytes) != cudaSuccess) return FFT3D_ERR_CUDA;
+  return FFT3D_SUCCESS;
+}
+
+int finish_plan(fft3d_plan p) {
+  int rc;
+  if (cudaMalloc(&p->d_status, sizeof(unsigned)) != cudaSuccess) {
+    cudaGetLastError();
+    return FFT3D_ERR_ALLOC;
+  }
+  if (cudaMemset(p->d_status, 0, sizeof(unsigned)) != cudaSuccess) return FFT3D_ERR_CUDA;
+  if (p->mixed && (rc = upload(&p->d_off, p->offsets.data(), p->offsets.size()))) return rc;
+  const bool identity = p->units.size() == 1;
+  for (Unit& u : p->units)
+    if ((rc = finish_unit(p, u, identity))) return rc;
   return FFT3D_SUCCESS;
 }
 
@@ -322,34 +352,166 @@ int validate_common(int precision, int direction, int norm, fft3d_plan* out_plan
 
 int launch(fft3d_plan p, const float2* in, float2* out, const float2* const* in_ptrs,
            float2* const* out_ptrs, cudaStream_t stream) {
-  if (cudaMemsetAsync(p->d_work, 0, p->work_bytes, stream) != cudaSuccess) {
-    cudaGetLastError();
-    return FFT3D_ERR_CUDA;
-  }
-  FusedArgs a{};
-  a.in = in;
-  a.out = out;
-  a.in_ptrs = in_ptrs;
-  a.out_ptrs = out_ptrs;
-  a.grid_off = p->d_off;
-  a.blocks = p->d_blocks;
-  a.nblocks = p->nblocks;
-  a.total_items = p->total_items;
-  a.twiddles = p->d_tw;
-  a.work = p->d_work;
-  a.status = p->d_status;
-  a.scale = p->scale;
-  a.do_scale = p->do_scale;
-  a.timeout_ns = p->timeout_ns;
-  a.mma_frag = p->d_frag;
-  if (p->kernel.launch(a, p->grid, stream) != cudaSuccess) {
-    cudaGetLastError();
-    return FFT3D_ERR_CUDA;
+  for (const Unit& u : p->units) {
+    if (cudaMemsetAsync(u.d_work, 0, u.work_bytes, stream) != cudaSuccess) {
+      cudaGetLastError();
+      return FFT3D_ERR_CUDA;
+    }
+    FusedArgs a{};
+    a.in = in;
+    a.out = out;
+    a.in_ptrs = in_ptrs;
+    a.out_ptrs = out_ptrs;
+    a.grid_off = p->d_off;
+    a.grid_map = u.d_map;
+    a.blocks = u.d_blocks;
+    a.nblocks = u.nblocks;
+    a.total_items = u.total_items;
+    a.twiddles = u.d_tw;
+    a.work = u.d_work;
+    a.status = p->d_status;
+    a.scale = p->scale;
+    a.do_scale = p->do_scale;
+    a.timeout_ns = p->timeout_ns;
+    a.mma_frag = u.d_frag;
+    if (u.kernel.launch(a, u.grid, stream) != cudaSuccess) {
+      cudaGetLastError();
+      return FFT3D_ERR_CUDA;
+    }
   }
   return FFT3D_SUCCESS;
 }
 
+// Validated arguments -> plan (variant < 0: environment override, tuning
+// cache, or the built-in default).
+int create_uniform(int nx, int ny, int nz, int batch, int precision, int direction, int norm,
+                   int variant, fft3d_plan* out_plan) {
+  int rc;
+  if ((rc = check_device())) return rc;
+  if (variant < 0) variant = pick_variant(false, nx, batch, precision, direction, nullptr, 0);
+  const std::vector<int> cand = variant_candidates(false, nx, precision);
+  if (std::find(cand.begin(), cand.end(), variant) == cand.end()) return FFT3D_ERR_INVALID_ARG;
+  fft3d_plan p = new (std::nothrow) fft3d_plan_s();
+  if (!p) return FFT3D_ERR_ALLOC;
+  cudaGetDevice(&p->device);
+  p->nx = nx; p->ny = ny; p->nz = nz; p->batch = batch;
+  p->precision = precision; p->direction = direction; p->norm = norm;
+  p->variant = variant;
+  const long long pts = (long long)nx * ny * nz;
+  p->dims.assign(batch, nx);
+  p->offsets.resize(batch);
+  for (int g = 0; g < batch; ++g) p->offsets[g] = (long long)g * pts;
+  p->total_points = pts * batch;
+  set_scale(p, (double)pts);
+  Unit u;
+  u.kernel = precision == FFT3D_FP32 ? fused_kernel_info(nx, direction, variant)
+                                     : tc_kernel_info(nx, direction, precision);
+  u.grids.resize(batch);
+  for (int g = 0; g < batch; ++g) u.grids[g] = g;
+  p->units.push_back(u);
+  rc = finish_plan(p);
+  if (rc) {
+    free_plan_buffers(p);
+    delete p;
+    return rc;
+  }
+  *out_plan = p;
+  return FFT3D_SUCCESS;
+}
+
+int create_mixed(int count, const int* dims, int direction, int norm, int variant,
+                 fft3d_plan* out_plan) {
+  int rc;
+  if ((rc = check_device())) return rc;
+  if (variant < 0) variant = pick_variant(true, 0, count, FFT3D_FP32, direction, dims, count);
+  if (variant != 0 && variant != 1) return FFT3D_ERR_INVALID_ARG;
+  fft3d_plan p = new (std::nothrow) fft3d_plan_s();
+  if (!p) return FFT3D_ERR_ALLOC;
+  cudaGetDevice(&p->device);
+  p->mixed = true;
+  p->variant = variant;
+  p->batch = count;
+  p->precision = FFT3D_FP32; p->direction = direction; p->norm = norm;
+  p->dims.assign(dims, dims + count);
+  p->offsets.resize(count);
+  long long off = 0;
+  for (int g = 0; g < count; ++g) {
+    p->offsets[g] = off;
+    off += (long long)dims[g] * dims[g] * dims[g];
+  }
+  p->total_points = off;
+  if (norm != FFT3D_NORM_NONE) {
+    // one scale per plan: every grid must have the same edge
+    const bool same =
+        std::all_of(p->dims.begin(), p->dims.end(), [&](int d) { return d == p->dims[0]; });
+    if (!same) {
+      delete p;
+      return FFT3D_ERR_INVALID_ARG;
+    }
+    set_scale(p, (double)p->dims[0] * p->dims[0] * p->dims[0]);
+  }
+  if (variant == 0) {
+    Unit u;
+    u.kernel = mixed_kernel_info(direction);
+    u.grids.resize(count);
+    for (int g = 0; g < count; ++g) u.grids[g] = g;
+    p->units.push_back(u);
+  } else {
+    // one unit per distinct edge, largest edges first
+    std::vector<int> edges(p->dims);
+    std::sort(edges.begin(), edges.end(), std::greater<int>());
+    edges.erase(std::unique(edges.begin(), edges.end()), edges.end());
+    for (int n : edges) {
+      Unit u;
+      u.kernel = fused_kernel_info(n, direction, builtin_default_variant(false, n, FFT3D_FP32));
+      for (int g = 0; g < count; ++g)
+        if (p->dims[g] == n) u.grids.push_back(g);
+      p->units.push_back(u);
+    }
+  }
+  rc = finish_plan(p);
+  if (rc) {
+    free_plan_buffers(p);
+    delete p;
+    return rc;
+  }
+  *out_plan = p;
+  return FFT3D_SUCCESS;
+}
+
+int validate_uniform(int nx, int ny, int nz, int batch, int precision) {
+  if (nx < 1 || ny < 1 || nz < 1 || batch < 1) return FFT3D_ERR_INVALID_ARG;
+  if (batch > (1 << 24)) return FFT3D_ERR_INVALID_ARG;
+  if (!fused_size(nx) || nx != ny || ny != nz) return FFT3D_ERR_UNSUPPORTED_SIZE;
+  if (precision != FFT3D_FP32 && !tc_size(nx)) return FFT3D_ERR_UNSUPPORTED_PRECISION;
+  // ticket counters are 32-bit: 2 * n items per grid
+  if ((long long)batch * 2 * nx >= (1LL << 31)) return FFT3D_ERR_INVALID_ARG;
+  return FFT3D_SUCCESS;
+}
+
+int validate_mixed(int count, const int* dims, int precision) {
+  if (!dims) return FFT3D_ERR_NULL_PTR;
+  if (count < 1 || count > FFT3D_MAX_MIXED_GRIDS) return FFT3D_ERR_INVALID_ARG;
+  long long items = 0;
+  for (int g = 0; g < count; ++g) {
+    if (dims[g] < 1) return FFT3D_ERR_INVALID_ARG;
+    if (!fused_size(dims[g])) return FFT3D_ERR_UNSUPPORTED_SIZE;
+    items += 2LL * dims[g];
+  }
+  if (items >= (1LL << 31)) return FFT3D_ERR_INVALID_ARG;
+  if (precision != FFT3D_FP32) return FFT3D_ERR_UNSUPPORTED_PRECISION;
+  return FFT3D_SUCCESS;
+}
+
 }  // namespace
+
+// Plan creation for the autotuner (tune.cu): a plan with a forced variant.
+int fft3d_internal_create_variant(bool mixed, int nx, int batch, int precision, int direction,
+                                  const int* dims, int count, int variant, fft3d_plan* out) {
+  *out = nullptr;
+  if (mixed) return create_mixed(count, dims, direction, FFT3D_NORM_NONE, variant, out);
+  return create_uniform(nx, nx, nx, batch, precision, direction, FFT3D_NORM_NONE, variant, out);
+}
 
 extern "C" {
 
@@ -368,91 +530,21 @@ int fft3d_plan_create(int nx, int ny, int nz, int batch, int precision, int dire
                       fft3d_plan* out_plan) {
   int rc = validate_common(precision, direction, norm, out_plan);
   if (rc) return rc;
-  if (nx < 1 || ny < 1 || nz < 1 || batch < 1) return FFT3D_ERR_INVALID_ARG;
-  if (batch > (1 << 24)) return FFT3D_ERR_INVALID_ARG;
-  if (!fused_size(nx) || nx != ny || ny != nz) return FFT3D_ERR_UNSUPPORTED_SIZE;
-  if (precision != FFT3D_FP32 && !tc_size(nx)) return FFT3D_ERR_UNSUPPORTED_PRECISION;
-  const long long pts = (long long)nx * ny * nz;
-  // ticket counters are 32-bit: 2 * n items per grid
-  if ((long long)batch * 2 * nx >= (1LL << 31)) return FFT3D_ERR_INVALID_ARG;
-  if ((rc = check_device())) return rc;
-
-  fft3d_plan p = new (std::nothrow) fft3d_plan_s();
-  if (!p) return FFT3D_ERR_ALLOC;
-  cudaGetDevice(&p->device);
-  p->nx = nx; p->ny = ny; p->nz = nz; p->batch = batch;
-  p->precision = precision; p->direction = direction; p->norm = norm;
-  p->dims.assign(batch, nx);
-  p->offsets.resize(batch);
-  for (int g = 0; g < batch; ++g) p->offsets[g] = (long long)g * pts;
-  p->total_points = pts * batch;
-  set_scale(p, (double)pts);
-  p->kernel = precision == FFT3D_FP32 ? fused_kernel_info(nx, direction, default_variant(nx))
-                                      : tc_kernel_info(nx, direction, precision);
-  std::vector<int> order(batch);
-  for (int g = 0; g < batch; ++g) order[g] = g;
-  rc = finish_plan(p, order);
-  if (rc) {
-    free_plan_buffers(p);
-    delete p;
-    return rc;
-  }
-  *out_plan = p;
-  return FFT3D_SUCCESS;
+  if ((rc = validate_uniform(nx, ny, nz, batch, precision))) return rc;
+  return create_uniform(nx, ny, nz, batch, precision, direction, norm, -1, out_plan);
 }
 
 int fft3d_plan_create_mixed(int count, const int* dims, int precision, int direction, int norm,
                             fft3d_plan* out_plan) {
   int rc = validate_common(precision, direction, norm, out_plan);
   if (rc) return rc;
-  if (!dims) return FFT3D_ERR_NULL_PTR;
-  if (count < 1 || count > FFT3D_MAX_MIXED_GRIDS) return FFT3D_ERR_INVALID_ARG;
-  long long items = 0;
-  for (int g = 0; g < count; ++g) {
-    if (dims[g] < 1) return FFT3D_ERR_INVALID_ARG;
-    if (!fused_size(dims[g])) return FFT3D_ERR_UNSUPPORTED_SIZE;
-    items += 2LL * dims[g];
-  }
-  if (items >= (1LL << 31)) return FFT3D_ERR_INVALID_ARG;
-  if (precision != FFT3D_FP32) return FFT3D_ERR_UNSUPPORTED_PRECISION;
-  if ((rc = check_device())) return rc;
+  if ((rc = validate_mixed(count, dims, precision))) return rc;
+  return create_mixed(count, dims, direction, norm, -1, out_plan);
+}
 
-  fft3d_plan p = new (std::nothrow) fft3d_plan_s();
-  if (!p) return FFT3D_ERR_ALLOC;
-  cudaGetDevice(&p->device);
-  p->mixed = true;
-  p->batch = count;
-  p->precision = precision; p->direction = direction; p->norm = norm;
-  p->dims.assign(dims, dims + count);
-  p->offsets.resize(count);
-  long long off = 0;
-  for (int g = 0; g < count; ++g) {
-    p->offsets[g] = off;
-    off += (long long)dims[g] * dims[g] * dims[g];
-  }
-  p->total_points = off;
-  p->kernel = mixed_kernel_info(direction);
-  // the scale of each grid differs; a mixed plan applies NORM per grid by
-  // its own edge, which the single scale argument cannot express
-  if (norm != FFT3D_NORM_NONE) {
-    bool same = std::all_of(p->dims.begin(), p->dims.end(), [&](int d) { return d == p->dims[0]; });
-    if (!same) {
-      delete p;
-      return FFT3D_ERR_INVALID_ARG;
-    }
-    set_scale(p, (double)p->dims[0] * p->dims[0] * p->dims[0]);
-  }
-  // largest grids first: the tail of the launch is made of small items
-  std::vector<int> order(count);
-  for (int g = 0; g < count; ++g) order[g] = g;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return dims[a] > dims[b]; });
-  rc = finish_plan(p, order);
-  if (rc) {
-    free_plan_buffers(p);
-    delete p;
-    return rc;
-  }
-  *out_plan = p;
+int fft3d_plan_variant(fft3d_plan plan, int* variant) {
+  if (!plan || !variant) return FFT3D_ERR_NULL_PTR;
+  *variant = plan->variant;
   return FFT3D_SUCCESS;
 }
 

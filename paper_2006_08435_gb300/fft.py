@@ -69,6 +69,12 @@ class Plan:
     def handle(self) -> int:
         return self._h.value or 0
 
+    @property
+    def variant(self) -> int:
+        v = ctypes.c_int()
+        L.check(L.lib().fft3d_plan_variant(self._h, ctypes.byref(v)), "fft3d_plan_variant")
+        return v.value
+
     def execute(self, x: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
         _check_tensor(x, "x")
         _check_tensor(out, "out")
@@ -122,6 +128,12 @@ class MixedPlan:
         L.check(L.lib().fft3d_execute(self._h, x.data_ptr(), out.data_ptr(), _stream_handle(stream)),
                 "fft3d_execute")
         return out
+
+    @property
+    def variant(self) -> int:
+        v = ctypes.c_int()
+        L.check(L.lib().fft3d_plan_variant(self._h, ctypes.byref(v)), "fft3d_plan_variant")
+        return v.value
 
     def execute_ptrs(self, in_ptrs: torch.Tensor, out_ptrs: torch.Tensor, stream=None) -> None:
         """``in_ptrs``/``out_ptrs``: int64 CUDA tensors of per-grid device pointers."""
@@ -196,6 +208,28 @@ class FFT3d(torch.autograd.Function):
     @staticmethod
     def backward(ctx, g):
         return fft3d(g.contiguous(), inverse=True, precision=ctx.precision), None
+
+
+def autotune(n: int, batch: int, precision: str = "fp32", inverse: bool = False,
+             cache_path: str | None = None) -> int:
+    """Time the kernel variants of an n^3 x batch plan on the current device
+    and return (and record in ``cache_path``) the fastest."""
+    best = ctypes.c_int()
+    L.check(L.lib().fft3d_autotune(int(n), int(batch), _PREC[precision],
+                                   L.FFT3D_INVERSE if inverse else L.FFT3D_FORWARD,
+                                   cache_path.encode() if cache_path else None, ctypes.byref(best)),
+            "fft3d_autotune")
+    return best.value
+
+
+def autotune_mixed(dims, inverse: bool = False, cache_path: str | None = None) -> int:
+    arr = (ctypes.c_int * len(dims))(*[int(d) for d in dims])
+    best = ctypes.c_int()
+    L.check(L.lib().fft3d_autotune_mixed(len(dims), arr,
+                                         L.FFT3D_INVERSE if inverse else L.FFT3D_FORWARD,
+                                         cache_path.encode() if cache_path else None,
+                                         ctypes.byref(best)), "fft3d_autotune_mixed")
+    return best.value
 
 
 def selftest_wait_timeout(timeout_ns: int = 1_000_000) -> int:

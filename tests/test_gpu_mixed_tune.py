@@ -1,0 +1,117 @@
+"""Mixed-edge batches (64 grids, edges from {32, 48, 64, 80, 96, 128}):
+forward then inverse inside one captured CUDA graph, both launch schedules
+of a mixed plan, and the autotuner on the device."""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle
+from paper_2006_08435_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 5e-6
+
+
+def _packed(sizes, seed):
+    grids = synth.mixed_grids(sizes, seed=seed)
+    return grids, torch.from_numpy(np.concatenate([g.ravel() for g in grids])).cuda()
+
+
+@pytest.fixture
+def mixed_env():
+    old = os.environ.get("FFT3D_MIXED_VARIANT")
+    yield
+    if old is None:
+        os.environ.pop("FFT3D_MIXED_VARIANT", None)
+    else:
+        os.environ["FFT3D_MIXED_VARIANT"] = old
+
+
+def test_config2_forward_inverse_in_one_graph(cuda):
+    """Both transforms of all 64 grids are captured once and replayed on new
+    data; every grid round-trips and one grid of each edge matches the
+    oracle."""
+    from paper_2006_08435_gb300 import MixedPlan
+    sizes = synth.mixed_sizes(64, seed=0)
+    fwd = MixedPlan(sizes)
+    inv = MixedPlan(sizes, inverse=True)
+    x = torch.zeros(fwd.total_points, dtype=torch.complex64, device="cuda")
+    y, back = torch.empty_like(x), torch.empty_like(x)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        fwd.execute(x, y)
+        inv.execute(y, back)
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fwd.execute(x, y)
+        inv.execute(y, back)
+    grids, packed = _packed(sizes, seed=1)
+    x.copy_(packed)
+    g.replay()
+    torch.cuda.synchronize()
+    assert fwd.device_status() == 0 and inv.device_status() == 0
+    off = fwd.offsets
+    yc, bc = y.cpu().numpy(), back.cpu().numpy()
+    seen = set()
+    for i, n in enumerate(sizes):
+        seg = bc[off[i]:off[i + 1]] / float(n) ** 3
+        assert oracle.rel_l2(seg, grids[i].ravel()) <= 2 * FP32_TOL
+        if n not in seen:
+            seen.add(n)
+            ref = oracle.dft3d(grids[i].astype(np.complex128), -1)
+            assert oracle.rel_l2(yc[off[i]:off[i + 1]].reshape(n, n, n), ref) <= FP32_TOL
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_mixed_schedules_agree(cuda, mixed_env, variant):
+    """One mixed-edge launch (0) and one launch per edge (1), packed and
+    pointer-array addressing, give the same spectra."""
+    from paper_2006_08435_gb300 import MixedPlan
+    sizes = [128, 32, 48, 128, 64, 96, 80, 32, 64]
+    grids, packed = _packed(sizes, seed=2)
+    os.environ["FFT3D_MIXED_VARIANT"] = str(variant)
+    p = MixedPlan(sizes)
+    assert p.variant == variant
+    y = torch.empty_like(packed)
+    p.execute(packed, y)
+    outs = [torch.empty(n ** 3, dtype=torch.complex64, device="cuda") for n in sizes]
+    ins = [packed[p.offsets[i]:p.offsets[i + 1]].clone() for i in range(len(sizes))]
+    ip = torch.tensor([t.data_ptr() for t in ins], dtype=torch.int64, device="cuda")
+    op = torch.tensor([t.data_ptr() for t in outs], dtype=torch.int64, device="cuda")
+    p.execute_ptrs(ip, op)
+    torch.cuda.synchronize()
+    assert p.device_status() == 0
+    yc = y.cpu().numpy()
+    for i, n in enumerate(sizes):
+        ref = oracle.dft3d(grids[i].astype(np.complex128), -1)
+        assert oracle.rel_l2(yc[p.offsets[i]:p.offsets[i + 1]].reshape(n, n, n), ref) <= FP32_TOL
+        assert oracle.rel_l2(outs[i].cpu().numpy().reshape(n, n, n), ref) <= FP32_TOL
+
+
+def test_autotune_records_and_plans_use_the_choice(cuda, tmp_path, monkeypatch):
+    from paper_2006_08435_gb300 import Plan, MixedPlan, autotune, autotune_mixed
+    cache = str(tmp_path / "tune.json")
+    best = autotune(64, 16, cache_path=cache)
+    assert best in (0, 1, 2)
+    sizes = synth.mixed_sizes(16, seed=3)
+    best_m = autotune_mixed(sizes, cache_path=cache)
+    assert best_m in (0, 1)
+    entries = json.load(open(cache))
+    assert len(entries) == 2 and best in entries.values()
+    monkeypatch.delenv("FFT3D_VARIANT", raising=False)
+    monkeypatch.delenv("FFT3D_MIXED_VARIANT", raising=False)
+    monkeypatch.setenv("FFT3D_TUNE_CACHE", cache)
+    assert Plan(64, 64, 64, 16).variant == best
+    assert MixedPlan(sizes).variant == best_m
+    # a tuned plan still computes Eq. 1
+    x = torch.from_numpy(synth.uniform_grids(64, 16, seed=4)).cuda()
+    y = torch.empty_like(x)
+    Plan(64, 64, 64, 16).execute(x, y)
+    ref = oracle.dft3d(x[5].cpu().numpy().astype(np.complex128), -1)
+    assert oracle.rel_l2(y[5].cpu().numpy(), ref) <= FP32_TOL
