@@ -134,7 +134,8 @@ int fft3d_plan_grid_offset(fft3d_plan plan, int g, int64_t* offset);
  *   in, out : device pointers to the packed grids (see layout above).
  *   stream  : cudaStream_t or NULL.
  * Asynchronous, allocates nothing, never synchronises, and is capturable in
- * a CUDA graph (one memset node plus kernel nodes).
+ * a CUDA graph (per launch unit a memset node for its work counters, when
+ * its kernel uses them, and a kernel node).
  */
 int fft3d_execute(fft3d_plan plan, const void* in, void* out, void* stream);
 
@@ -172,7 +173,8 @@ int fft3d_selftest_wait_timeout(int64_t timeout_ns);
 /*
  * The kernel variant a plan uses (written to *variant).  Single-edge FP32
  * plans: 0 plain persistent kernel, 1 the same with twice the threads per
- * block, 2 the TMA-fed warp-specialised kernel (64^3, 128^3).  Mixed plans:
+ * block, 2 the TMA-fed warp-specialised kernel (64^3, 128^3), 3 the
+ * cluster-fused single-pass kernel (16^3, 32^3, 64^3).  Mixed plans:
  * 0 one launch of the mixed-edge kernel, 1 one launch per distinct edge.
  * At create the variant comes from FFT3D_VARIANT / FFT3D_MIXED_VARIANT if
  * set, else from the tuning cache named by FFT3D_TUNE_CACHE (tuned on the

@@ -1,13 +1,16 @@
 // Single-size persistent kernels for 64^3 grids (forward and inverse),
 // in two block sizes: the default and twice as many threads per block
 // (more warps to hide latency, fewer registers per thread), plus the
-// warp-specialised TMA-fed kernel (variant 2).
+// warp-specialised TMA-fed kernel (variant 2) and the cluster-fused
+// single-pass kernel (variant 3).
+#include "cluster.cuh"
 #include "pipelined.cuh"
 
 namespace fft3d {
 
 KernelInfo fused_kernel_info_n64(int dir, int variant) {
   constexpr int T = fused_threads(64);
+  if (variant == 3) return dir < 0 ? clus::info<64, -1>() : clus::info<64, 1>();
   if (variant == 2) return dir < 0 ? piped::info<64, -1>() : piped::info<64, 1>();
   if (variant == 1 && 2 * T <= 1024)
     return dir < 0 ? make_fused_info<2 * T, -1, 64>() : make_fused_info<2 * T, 1, 64>();

@@ -46,6 +46,7 @@ struct FusedArgs {
   int do_scale;
   long long timeout_ns;
   const uint32_t* mma_frag;     // tensor-core B fragments (split precisions), or null
+  int ngrids;                   // grids of the launch unit
 };
 
 using LaunchFn = cudaError_t (*)(const FusedArgs&, int grid, cudaStream_t);
@@ -60,6 +61,7 @@ struct KernelInfo {
   int nsizes = 0;
   int items_in_flight = 1;      // work items a block holds at once (schedule lag)
   int prec = 0;                 // 0 FP32, else fft3d_precision of the tensor-core kinds
+  int cluster = 0;              // > 0: cluster kernel of this many blocks per cluster
 };
 
 // Defined in the inst_*.cu translation units.
@@ -75,7 +77,7 @@ cudaError_t launch_wait_selftest(unsigned* flag, unsigned* status, long long tim
 int pick_variant(bool mixed, int n, int batch, int precision, int direction, const int* dims,
                  int count);
 std::vector<int> variant_candidates(bool mixed, int n, int precision);
-int builtin_default_variant(bool mixed, int n, int precision);
+int builtin_default_variant(bool mixed, int n, int batch, int precision);
 
 }  // namespace fft3d
 

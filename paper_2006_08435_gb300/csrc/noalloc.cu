@@ -202,6 +202,7 @@ extern "C" int fft3d_execute_noalloc(int n, int batch, int direction, int norm, 
     a.scale = 1.0f;
   }
   a.timeout_ns = kDefaultWaitNs;
+  a.ngrids = batch;
   const int grid = std::max(1, std::min(total_items, resident));
   if (k.launch(a, grid, s) != cudaSuccess) {
     cudaGetLastError();

@@ -113,17 +113,26 @@ static bool fused_size(int n) { return fused_slot(n) >= 0; }
 
 // Kernel variants of a single-size FP32 plan: 0 plain persistent kernel,
 // 1 the same with twice the threads, 2 the TMA-fed warp-specialised kernel
-// (64^3 and 128^3 only).  Mixed plans: 0 one launch of the mixed-edge
-// kernel, 1 one launch per distinct edge with that edge's default kernel.
+// (64^3 and 128^3), 3 the cluster-fused single-pass kernel (16^3, 32^3,
+// 64^3).  Mixed plans: 0 one launch of the mixed-edge kernel, 1 one launch
+// per distinct edge with that edge's default kernel.
 std::vector<int> variant_candidates(bool mixed, int n, int precision) {
   if (mixed) return {0, 1};
   if (precision != FFT3D_FP32) return {0};
-  if (n == 64 || n == 128) return {0, 1, 2};
+  if (n == 64) return {0, 1, 2, 3};
+  if (n == 128) return {0, 1, 2};
+  if (n == 16 || n == 32) return {0, 1, 3};
   return {0, 1};
 }
 
-int builtin_default_variant(bool mixed, int n, int precision) {
-  return mixed || precision != FFT3D_FP32 ? 0 : (n == 128 ? 2 : 0);
+// Measured on GB300 (see profiles/): the TMA-fed kernel at 128^3, the
+// cluster-fused kernel for 16^3 and 32^3 batches of 64 grids or more, the
+// plain persistent kernel otherwise.
+int builtin_default_variant(bool mixed, int n, int batch, int precision) {
+  if (mixed || precision != FFT3D_FP32) return 0;
+  if (n == 128) return 2;
+  if ((n == 16 || n == 32) && batch >= 64) return 3;
+  return 0;
 }
 
 }  // namespace fft3d
@@ -277,6 +286,33 @@ int finish_unit(fft3d_plan p, Unit& u, bool identity) {
       cudaDeviceGetAttribute(&l2_bytes, cudaDevAttrL2CacheSize, p->device) != cudaSuccess)
     return FFT3D_ERR_CUDA;
   const int m = (int)u.grids.size();
+  int cluster_blocks = 0;  // > 0: launch this many blocks (whole clusters)
+  if (u.kernel.cluster > 0) {
+    if (u.kernel.cluster > 8 &&
+        cudaFuncSetAttribute(u.kernel.func, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      return FFT3D_ERR_UNSUPPORTED_SIZE;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = u.kernel.cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(u.kernel.cluster * sms, 1, 1);
+    cfg.blockDim = dim3(u.kernel.threads, 1, 1);
+    cfg.dynamicSmemBytes = u.kernel.smem;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, u.kernel.func, &cfg) != cudaSuccess ||
+        clusters < 1) {
+      cudaGetLastError();
+      return FFT3D_ERR_UNSUPPORTED_SIZE;
+    }
+    cluster_blocks = std::min(clusters, m) * u.kernel.cluster;
+  }
   std::vector<int> ldims(m), order(m);
   for (int l = 0; l < m; ++l) {
     ldims[l] = p->dims[u.grids[l]];
@@ -289,7 +325,7 @@ int finish_unit(fft3d_plan p, Unit& u, bool identity) {
       ldims, order, resident * u.kernel.items_in_flight, 0.4 * (double)l2_bytes, &total_items);
   u.total_items = total_items;
   u.nblocks = (int)blocks.size();
-  u.grid = std::max(1, std::min(total_items, resident));
+  u.grid = cluster_blocks > 0 ? cluster_blocks : std::max(1, std::min(total_items, resident));
 
   // twiddles for every edge the kernel handles, concatenated in its order
   std::vector<float> tw(2 * (size_t)u.kernel.twiddle_entries);
@@ -353,7 +389,8 @@ int validate_common(int precision, int direction, int norm, fft3d_plan* out_plan
 int launch(fft3d_plan p, const float2* in, float2* out, const float2* const* in_ptrs,
            float2* const* out_ptrs, cudaStream_t stream) {
   for (const Unit& u : p->units) {
-    if (cudaMemsetAsync(u.d_work, 0, u.work_bytes, stream) != cudaSuccess) {
+    // ticket kernels start from zeroed counters; cluster kernels use none
+    if (u.kernel.cluster == 0 && cudaMemsetAsync(u.d_work, 0, u.work_bytes, stream) != cudaSuccess) {
       cudaGetLastError();
       return FFT3D_ERR_CUDA;
     }
@@ -374,6 +411,7 @@ int launch(fft3d_plan p, const float2* in, float2* out, const float2* const* in_
     a.do_scale = p->do_scale;
     a.timeout_ns = p->timeout_ns;
     a.mma_frag = u.d_frag;
+    a.ngrids = (int)u.grids.size();
     if (u.kernel.launch(a, u.grid, stream) != cudaSuccess) {
       cudaGetLastError();
       return FFT3D_ERR_CUDA;
@@ -463,9 +501,10 @@ int create_mixed(int count, const int* dims, int direction, int norm, int varian
     edges.erase(std::unique(edges.begin(), edges.end()), edges.end());
     for (int n : edges) {
       Unit u;
-      u.kernel = fused_kernel_info(n, direction, builtin_default_variant(false, n, FFT3D_FP32));
       for (int g = 0; g < count; ++g)
         if (p->dims[g] == n) u.grids.push_back(g);
+      u.kernel = fused_kernel_info(
+          n, direction, builtin_default_variant(false, n, (int)u.grids.size(), FFT3D_FP32));
       p->units.push_back(u);
     }
   }

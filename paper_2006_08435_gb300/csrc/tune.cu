@@ -201,7 +201,7 @@ int pick_variant(bool mixed, int n, int batch, int precision, int direction, con
         allowed(v))
       return v;
   }
-  return builtin_default_variant(mixed, n, precision);
+  return builtin_default_variant(mixed, n, batch, precision);
 }
 
 }  // namespace fft3d

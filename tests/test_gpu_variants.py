@@ -1,0 +1,52 @@
+"""Every kernel variant of every edge it applies to, against the FP64
+oracle: 0 plain persistent, 1 twice the threads, 2 TMA-fed pipelined
+(64^3, 128^3), 3 cluster-fused single pass (16^3, 32^3, 64^3).  Odd batch
+sizes leave a ragged tail of work items / clusters."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle
+from paper_2006_08435_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 5e-6
+CASES = [(n, v) for n in (16, 32, 48, 64, 80, 96, 128) for v in (0, 1)]
+CASES += [(64, 2), (128, 2), (16, 3), (32, 3), (64, 3)]
+
+
+@pytest.mark.parametrize("n,variant", CASES)
+def test_variant_matches_oracle(cuda, monkeypatch, n, variant):
+    from paper_2006_08435_gb300 import Plan
+    monkeypatch.setenv("FFT3D_VARIANT", str(variant))
+    batch = 3 if n <= 64 else 2
+    x = torch.from_numpy(synth.uniform_grids(n, batch, seed=30 + n + variant)).cuda()
+    for inverse, norm in ((False, "none"), (True, "by_n")):
+        p = Plan(n, n, n, batch, inverse=inverse, norm=norm)
+        assert p.variant == variant
+        y = torch.empty_like(x)
+        p.execute(x, y)
+        assert p.device_status() == 0
+        ref = oracle.dft3d(x.cpu().numpy().astype(np.complex128), 1 if inverse else -1)
+        if norm == "by_n":
+            ref /= float(n) ** 3
+        yc = y.cpu().numpy()
+        for b in range(batch):
+            assert oracle.rel_l2(yc[b], ref[b]) <= FP32_TOL
+
+
+@pytest.mark.parametrize("n", [16, 32, 64])
+def test_cluster_variant_in_place_and_many_grids(cuda, monkeypatch, n):
+    """More grids than clusters (each cluster loops) and in == out."""
+    from paper_2006_08435_gb300 import Plan
+    monkeypatch.setenv("FFT3D_VARIANT", "3")
+    batch = 200 if n == 64 else 700
+    x = torch.from_numpy(synth.uniform_grids(n, 1, seed=n)).cuda().repeat(batch, 1, 1, 1)
+    x = (x * torch.arange(1, batch + 1, device="cuda").view(-1, 1, 1, 1)).contiguous()
+    ref0 = oracle.dft3d(x[0].cpu().numpy().astype(np.complex128), -1)
+    p = Plan(n, n, n, batch)
+    p.execute(x, x)
+    assert p.device_status() == 0
+    for b in (0, batch // 2, batch - 1):
+        assert oracle.rel_l2(x[b].cpu().numpy(), (b + 1) * ref0) <= FP32_TOL
