@@ -9,6 +9,7 @@ transform = 16 * N^3 (one read and one write of the grid).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload 128x32|64x256|128x16|64x64] [--no-cpu-baseline] [--no-e2e]
+                  [--no-split]
 
 The two small workloads exist for profiler captures of the same kernels.
 
@@ -42,8 +43,9 @@ METRIC = "batched 3D FFT transforms/s and % of HBM roofline at 64^3/128^3 (FP32 
 KERNEL_SOURCES = ["paper_2006_08435_gb300/csrc/persistent.cuh",
                   "paper_2006_08435_gb300/csrc/pipelined.cuh",
                   "paper_2006_08435_gb300/csrc/codelets.cuh",
+                  "paper_2006_08435_gb300/csrc/tc_stage.cuh",
                   "paper_2006_08435_gb300/csrc/sizes.h"]
-KERNEL_NAMES = {128: "piped_fft3d_kernel<128>", 64: "fused_fft3d_kernel<256,64>"}
+KERNEL_NAMES = {128: "piped_fft3d_kernel<128,-1>", 64: "fused_fft3d_kernel<256,-1,0,64>"}
 
 
 def dist_env():
@@ -287,6 +289,27 @@ def run_ours(args, ws, rank, local):
                "h2d_bytes_per_step": hx.numel() * hx.element_size(),
                "d2h_bytes_per_step": hy.numel() * hy.element_size()}
 
+    # the same workload through the split-FP16 tensor-core kind (the metric
+    # compares FP32 with split FP16); timed like the FP32 steps, fewer of them
+    split = None
+    if not args.no_split:
+        plan16 = Plan(n, n, n, batch, precision="split_fp16")
+        for _ in range(3):
+            plan16.execute(x, y, stream)
+        barrier()
+        k16 = max(1, args.steps // 4)
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(k16):
+            plan16.execute(x, y, stream)
+        s1.record(stream)
+        barrier()
+        ms16 = s0.elapsed_time(s1) / k16
+        assert plan16.device_status() == 0
+        split = {"value": ws * batch / (ms16 / 1e3), "unit": "transforms/s", "steps": k16,
+                 "ms_per_step": ms16}
+
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -315,6 +338,9 @@ def run_ours(args, ws, rank, local):
         "gpu_launches": args.steps,
         "clocks": clk,
     }
+    if split is not None:
+        split["roofline_frac"] = 16.0 * n ** 3 * batch / (split["ms_per_step"] / 1e3) / 1e9 / peak
+        line["split_fp16"] = split
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(n)
     print(json.dumps(line), flush=True)
@@ -332,6 +358,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="128x32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-split", action="store_true")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
