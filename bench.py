@@ -263,21 +263,20 @@ def run_ours(args, ws, rank, local):
     if args.no_e2e:
         hx = None
     else:
+        # fft3d_execute_host: chunks copied in, transformed and copied out on
+        # the plan's three streams, both copy directions overlapping
         hx = x.cpu().pin_memory()
         hy = torch.empty_like(hx).pin_memory()
-        e_steps = max(2, min(args.steps, 5))
+        plan.enable_host_io()
+        e_steps = max(2, min(args.steps, 10))
         for _ in range(2):
-            x.copy_(hx, non_blocking=True)
-            plan.execute(x, y, stream)
-            hy.copy_(y, non_blocking=True)
+            plan.execute_host(hx, hy, stream)
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(e_steps):
-            x.copy_(hx, non_blocking=True)
-            plan.execute(x, y, stream)
-            hy.copy_(y, non_blocking=True)
+            plan.execute_host(hx, hy, stream)
         e1.record(stream)
         barrier()
         e2e_ms = e0.elapsed_time(e1) / e_steps

@@ -148,6 +148,29 @@ int fft3d_execute_mixed(fft3d_plan plan, const void* const* in_ptrs,
                         void* const* out_ptrs, void* stream);
 
 /*
+ * Prepare a single-edge plan for fft3d_execute_host: a chunk plan of
+ * `chunk_grids` grids (and one for the shorter last chunk), two device input
+ * and two device output buffers of chunk_grids grids each, three internal
+ * streams and their events.  All allocated here, freed by
+ * fft3d_plan_destroy; calling it again replaces them.  The paper measures
+ * the host <-> accelerator transfer next to the transform (Table 1); this
+ * overlaps the two.
+ */
+int fft3d_plan_host_io(fft3d_plan plan, int chunk_grids);
+
+/*
+ * Transform `batch` grids that live in HOST memory: host_in and host_out are
+ * host pointers to the packed grids (page-locked memory for asynchronous
+ * copies; pageable memory works but the copies then serialise with the
+ * host).  Chunks are copied in, transformed and copied out on the plan's
+ * internal streams so that both copy directions and the transforms overlap.
+ * Ordered after prior work on `stream`; `stream` waits for the last copy
+ * back, so synchronising `stream` means host_out is complete.  Requires
+ * fft3d_plan_host_io; allocates nothing.
+ */
+int fft3d_execute_host(fft3d_plan plan, const void* host_in, void* host_out, void* stream);
+
+/*
  * Synchronise `stream`, then read and clear the plan's device status word.
  * Returns FFT3D_SUCCESS, FFT3D_ERR_DEVICE_TIMEOUT (a bounded inter-block
  * wait ran out; the affected outputs are undefined) or FFT3D_ERR_CUDA.
@@ -174,7 +197,8 @@ int fft3d_selftest_wait_timeout(int64_t timeout_ns);
  * The kernel variant a plan uses (written to *variant).  Single-edge FP32
  * plans: 0 plain persistent kernel, 1 the same with twice the threads per
  * block, 2 the TMA-fed warp-specialised kernel (64^3, 128^3), 3 the
- * cluster-fused single-pass kernel (16^3, 32^3, 64^3).  Mixed plans:
+ * cluster-fused single-pass kernel (16^3, 32^3, 64^3), 4 the double-buffered
+ * persistent kernel (32^3 .. 96^3, except 128^3).  Mixed plans:
  * 0 one launch of the mixed-edge kernel, 1 one launch per distinct edge.
  * At create the variant comes from FFT3D_VARIANT / FFT3D_MIXED_VARIANT if
  * set, else from the tuning cache named by FFT3D_TUNE_CACHE (tuned on the

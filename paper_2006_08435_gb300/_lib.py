@@ -49,6 +49,8 @@ _SIGS = {
     "fft3d_hartree_seed": (_I, [_VP, _I, _I, ctypes.c_double, _VP, _VP, _VP]),
     "fft3d_real_to_complex": (_I, [_VP, _VP, ctypes.c_int64, _VP]),
     "fft3d_plan_variant": (_I, [_VP, ctypes.POINTER(_I)]),
+    "fft3d_plan_host_io": (_I, [_VP, _I]),
+    "fft3d_execute_host": (_I, [_VP, _VP, _VP, _VP]),
     "fft3d_tune_select": (_I, [ctypes.c_char_p, _I, ctypes.POINTER(_I), _VP, _VP, ctypes.c_char_p,
                                ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "fft3d_autotune": (_I, [_I, _I, _I, _I, ctypes.c_char_p, ctypes.POINTER(_I)]),

@@ -3,13 +3,16 @@
 // (more warps to hide latency, fewer registers per thread), plus the
 // warp-specialised TMA-fed kernel (variant 2) and the cluster-fused
 // single-pass kernel (variant 3).
+// Variant 4: the double-buffered (cp.async prefetch) persistent kernel.
 #include "cluster.cuh"
+#include "prefetch.cuh"
 #include "pipelined.cuh"
 
 namespace fft3d {
 
 KernelInfo fused_kernel_info_n64(int dir, int variant) {
   constexpr int T = fused_threads(64);
+  if (variant == 4) return dir < 0 ? pref::info<T, -1, 64>() : pref::info<T, 1, 64>();
   if (variant == 3) return dir < 0 ? clus::info<64, -1>() : clus::info<64, 1>();
   if (variant == 2) return dir < 0 ? piped::info<64, -1>() : piped::info<64, 1>();
   if (variant == 1 && 2 * T <= 1024)

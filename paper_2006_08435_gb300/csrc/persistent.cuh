@@ -83,14 +83,16 @@ constexpr int plane_pitch() { return N + 1; }
 template <int N>
 constexpr int tile_elems() { return N * (N + 1); }
 
-template <int N, int T, int DIR, int PREC = 0>
+// STAGED: the plane is already in `tile` (row pitch N + 1) and visible to
+// all threads; otherwise it is loaded from src first.
+template <int N, int T, int DIR, int PREC = 0, bool STAGED = false>
 __device__ __forceinline__ void plane_item(const float2* __restrict__ src, float2* __restrict__ dst,
                                            float2* tile, const float2* tw, const uint32_t* frag) {
   constexpr int L1 = item_l1(N, PREC), L2 = N / L1, P = plane_pitch<N>();
   const int tid = threadIdx.x;
 
   // (1) plane -> shared memory
-  {
+  if constexpr (!STAGED) {
     constexpr int NE = N * N, PL = (NE + T - 1) / T;
     float2 r[PL];
 #pragma unroll
@@ -103,8 +105,8 @@ __device__ __forceinline__ void plane_item(const float2* __restrict__ src, float
       const int idx = tid + i * T;
       if (NE % T == 0 || idx < NE) tile[(idx / N) * P + idx % N] = r[i];
     }
+    __syncthreads();
   }
-  __syncthreads();
 
   // (2) x, first step: per row, L1 DFTs of length L2 on stride-L1 points,
   //     times W_N^(n1 k2), in place.  Lanes walk rows.
@@ -222,7 +224,9 @@ __device__ __forceinline__ void plane_item(const float2* __restrict__ src, float
 
 // Slab item: src/dst point at (x = 0, y, z = 0) of a grid; element (x, z)
 // of the slab is at x + z * N * N.
-template <int N, int T, int DIR, int PREC = 0>
+// STAGED: the slab is already in `tile` as [z][x] (pitch N) and visible to
+// all threads; otherwise its first step reads it from src (L2).
+template <int N, int T, int DIR, int PREC = 0, bool STAGED = false>
 __device__ __forceinline__ void slab_item(const float2* src, float2* dst, float2* tile,
                                           const float2* tw, const uint32_t* frag, float scale,
                                           int do_scale) {
@@ -233,10 +237,33 @@ __device__ __forceinline__ void slab_item(const float2* src, float2* dst, float2
     for (int grp = tid >> 5; grp < N * L1 / 16; grp += T / 32) {
       const int n1 = (grp * 16) / N, x0 = (grp * 16) % N;
       tc::dft16_group<PREC, DIR>(
-          frag, [&](int v, int j) { return ld_l2(src + (n1 + L1 * j) * NN + x0 + v); },
+          frag,
+          [&](int v, int j) {
+            if constexpr (STAGED) return tile[(n1 + L1 * j) * N + x0 + v];
+            else return ld_l2(src + (n1 + L1 * j) * NN + x0 + v);
+          },
           [&](int v, int k, float2 y) {
             tile[(n1 + L1 * k) * N + x0 + v] = cmul_tw<DIR>(y, tw[k * L1 + n1]);
           });
+    }
+  } else if constexpr (STAGED) {
+    // each item reads and writes its own points of the tile
+    constexpr int IA = N * L1, PA = (IA + T - 1) / T;
+#pragma unroll
+    for (int i = 0; i < PA; ++i) {
+      const int item = tid + i * T;
+      if (IA % T == 0 || item < IA) {
+        const int x = item % N, n1 = item / N;
+        float2* base = tile + n1 * N + x;
+        float2 v[L2];
+#pragma unroll
+        for (int n2 = 0; n2 < L2; ++n2) v[n2] = base[L1 * n2 * N];
+        DFT<L2, DIR>::run(v);
+#pragma unroll
+        for (int k2 = 1; k2 < L2; ++k2) v[k2] = cmul_tw<DIR>(v[k2], tw[k2 * L1 + n1]);
+#pragma unroll
+        for (int k2 = 0; k2 < L2; ++k2) base[L1 * k2 * N] = v[k2];
+      }
     }
   } else {
     constexpr int IA = N * L1, PA = (IA + T - 1) / T;

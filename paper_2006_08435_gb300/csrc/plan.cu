@@ -114,15 +114,18 @@ static bool fused_size(int n) { return fused_slot(n) >= 0; }
 // Kernel variants of a single-size FP32 plan: 0 plain persistent kernel,
 // 1 the same with twice the threads, 2 the TMA-fed warp-specialised kernel
 // (64^3 and 128^3), 3 the cluster-fused single-pass kernel (16^3, 32^3,
-// 64^3).  Mixed plans: 0 one launch of the mixed-edge kernel, 1 one launch
+// 64^3), 4 the double-buffered persistent kernel (32^3 to 96^3).  Mixed plans: 0 one launch of the mixed-edge kernel, 1 one launch
 // per distinct edge with that edge's default kernel.
 std::vector<int> variant_candidates(bool mixed, int n, int precision) {
   if (mixed) return {0, 1};
   if (precision != FFT3D_FP32) return {0};
-  if (n == 64) return {0, 1, 2, 3};
-  if (n == 128) return {0, 1, 2};
-  if (n == 16 || n == 32) return {0, 1, 3};
-  return {0, 1};
+  switch (n) {
+    case 16: return {0, 1, 3};
+    case 32: return {0, 1, 3, 4};
+    case 64: return {0, 1, 2, 3, 4};
+    case 128: return {0, 1, 2};
+    default: return {0, 1, 4};  // 48, 80, 96
+  }
 }
 
 // Measured on GB300 (see profiles/): the TMA-fed kernel at 128^3, the
@@ -155,7 +158,10 @@ struct Unit {
   int* d_map = nullptr;
 };
 
+struct HostIO;
+
 struct fft3d_plan_s {
+  HostIO* hio = nullptr;             // host-buffer pipeline (fft3d_plan_host_io)
   int device = -1;
   int nx = 0, ny = 0, nz = 0, batch = 0;
   int precision = 0, direction = -1, norm = 0;
@@ -552,6 +558,133 @@ int fft3d_internal_create_variant(bool mixed, int nx, int batch, int precision, 
   return create_uniform(nx, nx, nx, batch, precision, direction, FFT3D_NORM_NONE, variant, out);
 }
 
+// Host-buffer pipeline: chunks of `grids` grids go host -> device on one
+// stream, through the chunk plan on a second, device -> host on a third, with
+// two device buffers of each kind so that copies in both directions overlap
+// the transforms of neighbouring chunks.
+struct HostIO {
+  fft3d_plan chunk = nullptr;  // plan for `grids` grids
+  fft3d_plan tail = nullptr;   // plan for the last, shorter chunk (if any)
+  int grids = 0;
+  size_t grid_bytes = 0;
+  void* in_buf[2] = {nullptr, nullptr};
+  void* out_buf[2] = {nullptr, nullptr};
+  cudaStream_t s_h2d = nullptr, s_cmp = nullptr, s_d2h = nullptr;
+  cudaEvent_t in_ready[2] = {}, in_free[2] = {}, out_ready[2] = {}, out_free[2] = {};
+  cudaEvent_t start = nullptr, done = nullptr;
+};
+
+static void free_host_io(HostIO* h) {
+  if (!h) return;
+  fft3d_plan_destroy(h->chunk);
+  fft3d_plan_destroy(h->tail);
+  for (int b = 0; b < 2; ++b) {
+    cudaFree(h->in_buf[b]);
+    cudaFree(h->out_buf[b]);
+    if (h->in_ready[b]) cudaEventDestroy(h->in_ready[b]);
+    if (h->in_free[b]) cudaEventDestroy(h->in_free[b]);
+    if (h->out_ready[b]) cudaEventDestroy(h->out_ready[b]);
+    if (h->out_free[b]) cudaEventDestroy(h->out_free[b]);
+  }
+  if (h->start) cudaEventDestroy(h->start);
+  if (h->done) cudaEventDestroy(h->done);
+  if (h->s_h2d) cudaStreamDestroy(h->s_h2d);
+  if (h->s_cmp) cudaStreamDestroy(h->s_cmp);
+  if (h->s_d2h) cudaStreamDestroy(h->s_d2h);
+  delete h;
+}
+
+extern "C" {
+
+int fft3d_plan_host_io(fft3d_plan plan, int chunk_grids) {
+  if (!plan) return FFT3D_ERR_NULL_PTR;
+  if (plan->mixed || chunk_grids < 1 || chunk_grids > plan->batch) return FFT3D_ERR_INVALID_ARG;
+  if (plan->hio) {
+    free_host_io(plan->hio);
+    plan->hio = nullptr;
+  }
+  HostIO* h = new (std::nothrow) HostIO();
+  if (!h) return FFT3D_ERR_ALLOC;
+  const int n = plan->nx;
+  h->grids = chunk_grids;
+  h->grid_bytes = sizeof(float2) * (size_t)n * n * n;
+  int rc = create_uniform(n, n, n, chunk_grids, plan->precision, plan->direction, plan->norm,
+                          plan->precision == FFT3D_FP32 ? plan->variant : 0, &h->chunk);
+  const int rem = plan->batch % chunk_grids;
+  if (!rc && rem)
+    rc = create_uniform(n, n, n, rem, plan->precision, plan->direction, plan->norm,
+                        plan->precision == FFT3D_FP32 ? plan->variant : 0, &h->tail);
+  const size_t bytes = h->grid_bytes * (size_t)chunk_grids;
+  for (int b = 0; b < 2 && !rc; ++b)
+    if (cudaMalloc(&h->in_buf[b], bytes) != cudaSuccess ||
+        cudaMalloc(&h->out_buf[b], bytes) != cudaSuccess)
+      rc = FFT3D_ERR_ALLOC;
+  if (!rc &&
+      (cudaStreamCreateWithFlags(&h->s_h2d, cudaStreamNonBlocking) != cudaSuccess ||
+       cudaStreamCreateWithFlags(&h->s_cmp, cudaStreamNonBlocking) != cudaSuccess ||
+       cudaStreamCreateWithFlags(&h->s_d2h, cudaStreamNonBlocking) != cudaSuccess))
+    rc = FFT3D_ERR_CUDA;
+  for (int b = 0; b < 2 && !rc; ++b)
+    if (cudaEventCreateWithFlags(&h->in_ready[b], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->in_free[b], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->out_ready[b], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->out_free[b], cudaEventDisableTiming) != cudaSuccess)
+      rc = FFT3D_ERR_CUDA;
+  if (!rc && (cudaEventCreateWithFlags(&h->start, cudaEventDisableTiming) != cudaSuccess ||
+              cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming) != cudaSuccess))
+    rc = FFT3D_ERR_CUDA;
+  if (rc) {
+    cudaGetLastError();
+    free_host_io(h);
+    return rc;
+  }
+  plan->hio = h;
+  return FFT3D_SUCCESS;
+}
+
+int fft3d_execute_host(fft3d_plan plan, const void* host_in, void* host_out, void* stream) {
+  if (!plan || !host_in || !host_out) return FFT3D_ERR_NULL_PTR;
+  HostIO* h = plan->hio;
+  if (!h) return FFT3D_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const char* hin = static_cast<const char*>(host_in);
+  char* hout = static_cast<char*>(host_out);
+  bool ok = cudaEventRecord(h->start, s) == cudaSuccess &&
+            cudaStreamWaitEvent(h->s_h2d, h->start, 0) == cudaSuccess &&
+            cudaStreamWaitEvent(h->s_cmp, h->start, 0) == cudaSuccess &&
+            cudaStreamWaitEvent(h->s_d2h, h->start, 0) == cudaSuccess;
+  const int nchunks = (plan->batch + h->grids - 1) / h->grids;
+  for (int c = 0; c < nchunks && ok; ++c) {
+    const int b = c & 1, g0 = c * h->grids, m = std::min(h->grids, plan->batch - g0);
+    const size_t off = h->grid_bytes * (size_t)g0, bytes = h->grid_bytes * (size_t)m;
+    fft3d_plan cp = m == h->grids ? h->chunk : h->tail;
+    ok = (c < 2 || cudaStreamWaitEvent(h->s_h2d, h->in_free[b], 0) == cudaSuccess) &&
+         cudaMemcpyAsync(h->in_buf[b], hin + off, bytes, cudaMemcpyHostToDevice, h->s_h2d) ==
+             cudaSuccess &&
+         cudaEventRecord(h->in_ready[b], h->s_h2d) == cudaSuccess &&
+         cudaStreamWaitEvent(h->s_cmp, h->in_ready[b], 0) == cudaSuccess &&
+         (c < 2 || cudaStreamWaitEvent(h->s_cmp, h->out_free[b], 0) == cudaSuccess) &&
+         fft3d_execute(cp, h->in_buf[b], h->out_buf[b], h->s_cmp) == FFT3D_SUCCESS &&
+         cudaEventRecord(h->in_free[b], h->s_cmp) == cudaSuccess &&
+         cudaEventRecord(h->out_ready[b], h->s_cmp) == cudaSuccess &&
+         cudaStreamWaitEvent(h->s_d2h, h->out_ready[b], 0) == cudaSuccess &&
+         cudaMemcpyAsync(hout + off, h->out_buf[b], bytes, cudaMemcpyDeviceToHost, h->s_d2h) ==
+             cudaSuccess &&
+         cudaEventRecord(h->out_free[b], h->s_d2h) == cudaSuccess;
+  }
+  // the caller's stream continues after the last copy back (and after the
+  // last transform, which every copy back follows)
+  ok = ok && cudaEventRecord(h->done, h->s_d2h) == cudaSuccess &&
+       cudaStreamWaitEvent(s, h->done, 0) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    return FFT3D_ERR_CUDA;
+  }
+  return FFT3D_SUCCESS;
+}
+
+}  // extern "C"
+
 extern "C" {
 
 int fft3d_size_supported(int n) { return fused_size(n) ? 1 : 0; }
@@ -620,11 +753,21 @@ int fft3d_get_device_status(fft3d_plan plan, void* stream) {
   if (cudaMemcpy(&s, plan->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess ||
       cudaMemset(plan->d_status, 0, sizeof(unsigned)) != cudaSuccess)
     return FFT3D_ERR_CUDA;
+  if (plan->hio) {  // the chunk plans of the host-buffer pipeline
+    for (fft3d_plan cp : {plan->hio->chunk, plan->hio->tail})
+      if (cp) {
+        const int rc = fft3d_get_device_status(cp, plan->hio->s_cmp);
+        if (rc == FFT3D_ERR_DEVICE_TIMEOUT) s = kStatusTimeout;
+        else if (rc != FFT3D_SUCCESS) return rc;
+      }
+  }
   return s == kStatusOk ? FFT3D_SUCCESS : FFT3D_ERR_DEVICE_TIMEOUT;
 }
 
 int fft3d_plan_destroy(fft3d_plan plan) {
   if (!plan) return FFT3D_SUCCESS;
+  free_host_io(plan->hio);
+  plan->hio = nullptr;
   free_plan_buffers(plan);
   delete plan;
   return FFT3D_SUCCESS;

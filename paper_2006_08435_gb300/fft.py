@@ -85,6 +85,25 @@ class Plan:
                 "fft3d_execute")
         return out
 
+    def enable_host_io(self, chunk_grids: int | None = None) -> None:
+        """Allocate the staging of execute_host (default: ~32 MB chunks)."""
+        if chunk_grids is None:
+            grid_bytes = 8 * self.shape[0] * self.shape[1] * self.shape[2]
+            chunk_grids = max(1, min(self.batch, (32 << 20) // grid_bytes))
+        L.check(L.lib().fft3d_plan_host_io(self._h, int(chunk_grids)), "fft3d_plan_host_io")
+
+    def execute_host(self, x: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
+        """x, out: complex64 CPU tensors (pin them for overlapped copies)."""
+        for t, name in ((x, "x"), (out, "out")):
+            if t.is_cuda or t.dtype != torch.complex64 or not t.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous complex64 CPU tensor")
+        need = self.batch * self.shape[0] * self.shape[1] * self.shape[2]
+        if x.numel() != need or out.numel() != need:
+            raise ValueError(f"expected {need} points")
+        L.check(L.lib().fft3d_execute_host(self._h, x.data_ptr(), out.data_ptr(),
+                                           _stream_handle(stream)), "fft3d_execute_host")
+        return out
+
     def device_status(self, stream=None) -> int:
         return L.lib().fft3d_get_device_status(self._h, _stream_handle(stream))
 
