@@ -198,7 +198,8 @@ int fft3d_selftest_wait_timeout(int64_t timeout_ns);
  * plans: 0 plain persistent kernel, 1 the same with twice the threads per
  * block, 2 the TMA-fed warp-specialised kernel (64^3, 128^3), 3 the
  * cluster-fused single-pass kernel (16^3, 32^3, 64^3), 4 the double-buffered
- * persistent kernel (32^3 .. 96^3, except 128^3).  Mixed plans:
+ * persistent kernel (32^3 .. 96^3, except 128^3), 5 the warp-owned two-phase
+ * kernel (64^3, 128^3).  Mixed plans:
  * 0 one launch of the mixed-edge kernel, 1 one launch per distinct edge.
  * At create the variant comes from FFT3D_VARIANT / FFT3D_MIXED_VARIANT if
  * set, else from the tuning cache named by FFT3D_TUNE_CACHE (tuned on the

@@ -4,14 +4,17 @@
 // warp-specialised TMA-fed kernel (variant 2) and the cluster-fused
 // single-pass kernel (variant 3).
 // Variant 4: the double-buffered (cp.async prefetch) persistent kernel.
+// Variant 5: warp-owned rows/columns inside the two-phase items.
 #include "cluster.cuh"
 #include "prefetch.cuh"
 #include "pipelined.cuh"
+#include "warpown.cuh"
 
 namespace fft3d {
 
 KernelInfo fused_kernel_info_n64(int dir, int variant) {
   constexpr int T = fused_threads(64);
+  if (variant == 5) return dir < 0 ? wown::info<64, -1>() : wown::info<64, 1>();
   if (variant == 4) return dir < 0 ? pref::info<T, -1, 64>() : pref::info<T, 1, 64>();
   if (variant == 3) return dir < 0 ? clus::info<64, -1>() : clus::info<64, 1>();
   if (variant == 2) return dir < 0 ? piped::info<64, -1>() : piped::info<64, 1>();

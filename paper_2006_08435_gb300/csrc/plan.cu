@@ -114,7 +114,8 @@ static bool fused_size(int n) { return fused_slot(n) >= 0; }
 // Kernel variants of a single-size FP32 plan: 0 plain persistent kernel,
 // 1 the same with twice the threads, 2 the TMA-fed warp-specialised kernel
 // (64^3 and 128^3), 3 the cluster-fused single-pass kernel (16^3, 32^3,
-// 64^3), 4 the double-buffered persistent kernel (32^3 to 96^3).  Mixed plans: 0 one launch of the mixed-edge kernel, 1 one launch
+// 64^3), 4 the double-buffered persistent kernel (32^3 to 96^3), 5 the
+// warp-owned two-phase kernel (64^3, 128^3).  Mixed plans: 0 one launch of the mixed-edge kernel, 1 one launch
 // per distinct edge with that edge's default kernel.
 std::vector<int> variant_candidates(bool mixed, int n, int precision) {
   if (mixed) return {0, 1};
@@ -122,8 +123,8 @@ std::vector<int> variant_candidates(bool mixed, int n, int precision) {
   switch (n) {
     case 16: return {0, 1, 3};
     case 32: return {0, 1, 3, 4};
-    case 64: return {0, 1, 2, 3, 4};
-    case 128: return {0, 1, 2};
+    case 64: return {0, 1, 2, 3, 4, 5};
+    case 128: return {0, 1, 2, 5};
     default: return {0, 1, 4};  // 48, 80, 96
   }
 }

@@ -1,7 +1,8 @@
 """Every kernel variant of every edge it applies to, against the FP64
 oracle: 0 plain persistent, 1 twice the threads, 2 TMA-fed pipelined
 (64^3, 128^3), 3 cluster-fused single pass (16^3, 32^3, 64^3), 4
-double-buffered persistent (32^3 .. 96^3).  Odd batch
+double-buffered persistent (32^3 .. 96^3), 5 warp-owned two-phase
+(64^3, 128^3).  Odd batch
 sizes leave a ragged tail of work items / clusters."""
 import numpy as np
 import pytest
@@ -15,7 +16,7 @@ pytestmark = pytest.mark.gpu
 FP32_TOL = 5e-6
 CASES = [(n, v) for n in (16, 32, 48, 64, 80, 96, 128) for v in (0, 1)]
 CASES += [(64, 2), (128, 2), (16, 3), (32, 3), (64, 3)]
-CASES += [(32, 4), (48, 4), (64, 4), (80, 4), (96, 4)]
+CASES += [(32, 4), (48, 4), (64, 4), (80, 4), (96, 4), (64, 5), (128, 5)]
 
 
 @pytest.mark.parametrize("n,variant", CASES)
