@@ -199,7 +199,11 @@ int fft3d_selftest_wait_timeout(int64_t timeout_ns);
  * block, 2 the TMA-fed warp-specialised kernel (64^3, 128^3), 3 the
  * cluster-fused single-pass kernel (16^3, 32^3, 64^3), 4 the double-buffered
  * persistent kernel (32^3 .. 96^3, except 128^3), 5 the warp-owned two-phase
- * kernel (64^3, 128^3).  Mixed plans:
+ * kernel (64^3, 128^3), 6 the double-buffered TMA-fed kernel with producer
+ * and signaller warps (64^3), 7 the thread-per-pencil kernel (each 1D FFT in
+ * one thread's registers, items loaded by swizzled tensor TMA; 64^3).
+ * Variant 7 needs packed, 16-byte aligned buffers of one batch (it encodes
+ * tensor maps of `in` and `out` at each execute).  Mixed plans:
  * 0 one launch of the mixed-edge kernel, 1 one launch per distinct edge.
  * At create the variant comes from FFT3D_VARIANT / FFT3D_MIXED_VARIANT if
  * set, else from the tuning cache named by FFT3D_TUNE_CACHE (tuned on the

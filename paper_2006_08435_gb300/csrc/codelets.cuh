@@ -136,12 +136,13 @@ FFT3D_HD float2 twc(float2 a) {
 
 // ------------------------------------------------------------------ codelets
 __host__ __device__ constexpr int first_factor(int R) {
-  return R == 16 ? 4 : R == 12 ? 4 : R % 2 == 0 ? 2 : R % 3 == 0 ? 3 : R;
+  return R == 64 ? 8 : R == 32 ? 4 : R == 16 ? 4 : R == 12 ? 4 : R % 2 == 0 ? 2 : R % 3 == 0 ? 3 : R;
 }
 
 template <int R, int DIR>
 struct DFT {
-  static_assert(R == 6 || R == 8 || R == 9 || R == 10 || R == 12 || R == 15 || R == 16,
+  static_assert(R == 6 || R == 8 || R == 9 || R == 10 || R == 12 || R == 15 || R == 16 ||
+                    R == 32 || R == 64,
                 "unsupported codelet radix");
   static constexpr int R1 = first_factor(R);
   static constexpr int R2 = R / R1;

@@ -123,7 +123,7 @@ std::vector<int> variant_candidates(bool mixed, int n, int precision) {
   switch (n) {
     case 16: return {0, 1, 3};
     case 32: return {0, 1, 3, 4};
-    case 64: return {0, 1, 2, 3, 4, 5};
+    case 64: return {0, 1, 2, 3, 4, 5, 6, 7};
     case 128: return {0, 1, 2, 5};
     default: return {0, 1, 4};  // 48, 80, 96
   }

@@ -1,0 +1,371 @@
+// Thread-per-pencil persistent 3D FFT kernel for 64^3 grids, fed by tensor
+// TMA.
+//
+// Same plane and slab items and the same ticket schedule as the persistent
+// kernel; what changes is how little shared-memory traffic an item costs.
+// Each 1D FFT of 64 points runs entirely in one thread's registers (a
+// radix-8 x 8 codelet), so the only shared-memory passes are the ones the
+// data layout forces:
+//
+//   plane item: TMA writes the plane; thread t reads row t, transforms it
+//     along x and writes it back in place; after a barrier of its group,
+//     thread t reads column t, transforms it along y and stores it to
+//     global memory straight from registers (rows of the output plane).
+//   slab item: TMA writes the slab (row z = the 64 points of that z);
+//     thread t reads column x = t, transforms it along z and stores it.
+//
+// That is 4 passes over the tile for a plane and 2 for a slab.  An item is
+// loaded by four 2D tensor copies (cp.async.bulk.tensor, 16 x 64 complex
+// boxes) with 128-byte swizzling: a 128-byte row segment holds 16 complex
+// and its 16-byte chunks are XORed with the row index mod 8, so that both
+// the row reads (16-byte accesses, eight rows per phase) and the column reads
+// (8-byte accesses, sixteen columns of one row per phase) are free of bank
+// conflicts.
+//
+// Block: four compute groups of 64 threads (each group one item at a time,
+// items k = g, g + 4, ...), one producer warp (tickets, slab dependencies,
+// tensor copies into a ring of six tiles) and one signaller warp (frees tiles,
+// publishes finished planes).  One block per SM.  Liveness and bounded waits
+// as in the double-buffered kernel: a block's started items finish without
+// the producer, so its waits for slab dependencies are waits on smaller
+// tickets only.
+#pragma once
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "pipelined.cuh"
+
+namespace fft3d {
+namespace rowk {
+
+using piped::mbar_arrive;
+using piped::mbar_arrive_tx;
+using piped::mbar_init;
+using piped::mbar_wait_bounded;
+using piped::saddr;
+using piped::warp_wait;
+
+template <int N>
+struct Cfg {
+  static_assert(N == 64, "thread-per-pencil kernel covers 64");
+  static constexpr int SEG = 16;                   // complex per 128-byte row segment
+  static constexpr int NSEG = N / SEG;             // tensor boxes per item
+  static constexpr int REGION = N * 128;           // bytes of one box in shared memory
+  static constexpr int TILE = NSEG * REGION;       // bytes of one item
+  static constexpr int NTILE = 6;
+  static constexpr int SCHED = 8192;               // schedule blocks kept in shared memory
+  static constexpr int GROUPS = 4;                 // compute groups of N threads
+  static constexpr int GW = N / 32;                // warps per group
+  static constexpr int NCW = GROUPS * GW;          // compute warps
+  static constexpr int T = 32 * (NCW + 2);         // plus producer and signaller
+  static constexpr size_t smem = 1024 + (size_t)NTILE * TILE +
+                                 (3 * NTILE + GROUPS) * sizeof(unsigned long long) +
+                                 NTILE * sizeof(int4) + SCHED * sizeof(unsigned short);
+};
+
+// Byte offset of complex (row r, column c) in a tile (128-byte swizzle).
+template <int N>
+__device__ __forceinline__ uint32_t eoff(int r, int c) {
+  return (uint32_t)((c >> 4) * Cfg<N>::REGION + r * 128 + ((((c & 15) >> 1) ^ (r & 7)) << 4) +
+                    ((c & 1) << 3));
+}
+
+__device__ __forceinline__ float4 lds128(uint32_t a) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(a));
+  return v;
+}
+__device__ __forceinline__ void sts128(uint32_t a, float4 v) {
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z),
+               "f"(v.w)
+               : "memory");
+}
+__device__ __forceinline__ float2 lds64(uint32_t a) {
+  float2 v;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
+  return v;
+}
+
+// 2D box (16 complex wide) of a 3D tensor map into shared memory.
+__device__ __forceinline__ void tma_box(uint32_t dst, const CUtensorMap* map, int x, int y, int z,
+                                        unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(saddr(bar))
+      : "memory");
+}
+
+struct Desc {
+  int item, grid, phase, idx;
+};
+
+__device__ __forceinline__ Desc bcast(Desc d) {
+  d.item = __shfl_sync(0xffffffffu, d.item, 0);
+  d.grid = __shfl_sync(0xffffffffu, d.grid, 0);
+  d.phase = __shfl_sync(0xffffffffu, d.phase, 0);
+  d.idx = __shfl_sync(0xffffffffu, d.idx, 0);
+  return d;
+}
+
+// Producer warp (lane 0 works): tickets in order into tiles k % NTILE.
+// Tensors are viewed as [N * batch][N][2N] floats (z of all grids, y, x
+// interleaved re/im); planes come from `in`, slabs from `out`.  Schedule
+// block b (tickets b*N .. b*N + N - 1) is read from `sched` (grid * 2 +
+// phase) when the schedule fits there, else from global memory.  A failure
+// elsewhere is seen at the next dependency wait; until then the producer
+// keeps taking tickets without reading the status word.
+template <int N>
+__device__ __forceinline__ void producer(const FusedArgs& a, const CUtensorMap* tin,
+                                         const CUtensorMap* tout, uint32_t tiles,
+                                         unsigned long long* full, unsigned long long* freed,
+                                         Desc* desc, const unsigned short* sched) {
+  using K = Cfg<N>;
+  constexpr int NT = K::NTILE;
+  if ((threadIdx.x & 31) != 0) return;
+  auto take = [&]() -> int { return (int)atomicAdd(a.work, 1u); };
+  const bool local = a.nblocks <= K::SCHED;
+  unsigned live = 0;  // tiles whose copies were issued (bit s)
+  int next = take();
+  int k = 0;
+  for (;; ++k) {
+    const int s = k % NT;
+    if (k >= NT && !mbar_wait_bounded(&freed[s], (k / NT - 1) & 1, a.status, a.timeout_ns)) break;
+    live &= ~(1u << s);
+    const int t = next;
+    next = take();  // one ticket ahead: its round trip overlaps this item
+    Desc d{-1, 0, 0, 0};
+    bool ok = t < a.total_items;
+    if (ok) {
+      const int b = t / N;  // N tickets per block (one edge)
+      int grid, phase;
+      if (local) {
+        grid = sched[b] >> 1;
+        phase = sched[b] & 1;
+      } else {
+        const SchedBlock blk = a.blocks[b];
+        grid = blk.grid;
+        phase = blk.phase;
+      }
+      d = Desc{t, grid, phase, t - b * N};
+      if (phase == 1)
+        ok = bounded_wait_geq(a.work + 1 + grid, (unsigned)N, a.status, a.timeout_ns);
+    }
+    if (!ok) {
+      // a stop for each compute group: items k .. k + GROUPS - 1 (each tile
+      // once the signaller has freed its earlier item)
+      for (int j = 0; j < K::GROUPS; ++j) {
+        const int kk = k + j, sj = kk % NT;
+        if (j > 0 && kk >= NT &&
+            !mbar_wait_bounded(&freed[sj], (kk / NT - 1) & 1, a.status, a.timeout_ns))
+          break;
+        desc[sj] = Desc{-1, 0, 0, 0};
+        mbar_arrive(&full[sj]);
+        live &= ~(1u << sj);
+      }
+      break;
+    }
+    desc[s] = d;
+    // the tile was last written by the compute threads' plain stores, a
+    // slab's rows by other blocks' plain stores
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (d.phase == 1) asm volatile("fence.proxy.async.global;" ::: "memory");
+    mbar_arrive_tx(&full[s], (unsigned)K::TILE);
+    const uint32_t dst = tiles + (uint32_t)(s * K::TILE);
+    for (int b = 0; b < K::NSEG; ++b) {
+      if (d.phase == 0)  // plane z = idx: box {16 x, all y} at z
+        tma_box(dst + b * K::REGION, tin, 2 * K::SEG * b, 0, d.grid * N + d.idx, &full[s]);
+      else  // slab y = idx: box {16 x, all z} at y
+        tma_box(dst + b * K::REGION, tout, 2 * K::SEG * b, d.idx, d.grid * N, &full[s]);
+    }
+    live |= 1u << s;
+  }
+  // no copy may still be writing a tile when the block exits (only after a
+  // failure can one be left unconsumed)
+  for (int j = 1; j <= NT; ++j) {
+    const int kk = k - j;
+    if (kk >= 0 && (live & (1u << (kk % NT))))
+      mbar_wait_bounded(&full[kk % NT], (kk / NT) & 1, a.status, a.timeout_ns);
+  }
+}
+
+// Signaller warp: items in order; once the compute group is done with one,
+// frees its tile and, for a plane, publishes it to the other blocks.
+template <int N>
+__device__ __forceinline__ void signaller(const FusedArgs& a, unsigned long long* full,
+                                          unsigned long long* empty,
+                                          unsigned long long* freed, Desc* desc) {
+  constexpr int NT = Cfg<N>::NTILE;
+  const int lane = threadIdx.x & 31;
+  for (int k = 0;; ++k) {
+    const int s = k % NT;
+    const unsigned par = (k / NT) & 1;
+    if (!warp_wait(&full[s], par, a)) return;
+    const Desc d = desc[s];
+    if (d.item < 0) return;
+    if (!warp_wait(&empty[s], par, a)) return;
+    if (lane == 0) {
+      mbar_arrive(&freed[s]);
+      if (d.phase == 0) {
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        atomicAdd(a.work + 1 + d.grid, 1u);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+template <int N, int DIR>
+__global__ void __launch_bounds__(Cfg<N>::T, 1)
+    rowfft_fft3d_kernel(const FusedArgs a, const __grid_constant__ CUtensorMap tin,
+                        const __grid_constant__ CUtensorMap tout) {
+  using K = Cfg<N>;
+  constexpr int NT = K::NTILE;
+  constexpr long long NN = (long long)N * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // tiles 1024-byte aligned (the swizzle pattern follows address bits 7..9)
+  unsigned char* base = smem_raw + ((1024 - (saddr(smem_raw) & 1023)) & 1023);
+  const uint32_t tiles = saddr(base);
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(base + (size_t)NT * K::TILE);
+  unsigned long long* empty = full + NT;
+  unsigned long long* freed = empty + NT;
+  unsigned long long* tr = freed + NT;  // per group: rows done before columns
+  Desc* desc = reinterpret_cast<Desc*>(tr + K::GROUPS);
+  unsigned short* sched = reinterpret_cast<unsigned short*>(desc + NT);
+  const int w = threadIdx.x >> 5;
+  if (a.nblocks <= K::SCHED)
+    for (int b = threadIdx.x; b < a.nblocks; b += K::T)
+      sched[b] = (unsigned short)(a.blocks[b].grid * 2 + a.blocks[b].phase);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NT; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], K::GW);
+      mbar_init(&freed[s], 1);
+    }
+    for (int g = 0; g < K::GROUPS; ++g) mbar_init(&tr[g], K::GW);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  if (w == K::NCW) {
+    producer<N>(a, &tin, &tout, tiles, full, freed, desc, sched);
+    return;
+  }
+  if (w == K::NCW + 1) {
+    signaller<N>(a, full, empty, freed, desc);
+    return;
+  }
+
+  // compute group g, thread gt of N
+  const int g = w / K::GW, gt = threadIdx.x - g * N, lane = threadIdx.x & 31;
+  unsigned planes = 0;  // plane items of this group (parity of its barrier)
+  for (int k = g;; k += K::GROUPS) {
+    const int s = k % NT;
+    if (!warp_wait(&full[s], (k / NT) & 1, a)) break;
+    const Desc d = desc[s];
+    if (d.item < 0) break;
+    const uint32_t t = tiles + (uint32_t)(s * K::TILE);
+    const float2* gin;
+    float2* gout;
+    grid_ptrs(a, d.grid, N, gin, gout);
+    float2 v[N];
+    if (d.phase == 0) {
+      // x: row y = gt, 16-byte chunks
+#pragma unroll
+      for (int j = 0; j < N / 2; ++j) {
+        const float4 q = lds128(t + eoff<N>(gt, 2 * j));
+        v[2 * j] = make_float2(q.x, q.y);
+        v[2 * j + 1] = make_float2(q.z, q.w);
+      }
+      DFT<N, DIR>::run(v);
+#pragma unroll
+      for (int j = 0; j < N / 2; ++j)
+        sts128(t + eoff<N>(gt, 2 * j), make_float4(v[2 * j].x, v[2 * j].y, v[2 * j + 1].x,
+                                                   v[2 * j + 1].y));
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tr[g]);
+      if (!warp_wait(&tr[g], planes & 1, a)) break;
+      ++planes;
+      // y: column x = gt, output rows straight to global memory
+#pragma unroll
+      for (int r = 0; r < N; ++r) v[r] = lds64(t + eoff<N>(r, gt));
+      DFT<N, DIR>::run(v);
+      float2* dst = gout + (long long)d.idx * NN + gt;
+#pragma unroll
+      for (int k1 = 0; k1 < N; ++k1) dst[(long long)k1 * N] = v[k1];
+    } else {
+      // z: column x = gt of slab y = idx
+#pragma unroll
+      for (int z = 0; z < N; ++z) v[z] = lds64(t + eoff<N>(z, gt));
+      DFT<N, DIR>::run(v);
+      float2* dst = gout + (long long)d.idx * N + gt;
+#pragma unroll
+      for (int k1 = 0; k1 < N; ++k1) {
+        float2 o = v[k1];
+        if (a.do_scale) o = cscale(o, a.scale);
+        st_stream(dst + k1 * NN, o);
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+  }
+}
+
+// cuTensorMapEncodeTiled from the driver, looked up once.
+inline PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
+
+// [N * batch][N][2N] floats, box {32 floats (16 complex), by, bz}, 128-byte swizzle.
+inline bool encode_map(CUtensorMap* m, const void* base, int n, int batch, unsigned by,
+                       unsigned bz) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)2 * n, (cuuint64_t)n, (cuuint64_t)n * batch};
+  const cuuint64_t strides[2] = {(cuuint64_t)n * 8, (cuuint64_t)n * n * 8};
+  const cuuint32_t box[3] = {32, by, bz};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Uniform batches only (packed buffers, grids in plan order).
+template <int N, int DIR>
+cudaError_t launch(const FusedArgs& a, int grid, cudaStream_t stream) {
+  if (a.in_ptrs || a.grid_map || a.grid_off) return cudaErrorInvalidValue;
+  CUtensorMap tin, tout;
+  if (!encode_map(&tin, a.in, N, a.ngrids, N, 1) || !encode_map(&tout, a.out, N, a.ngrids, 1, N))
+    return cudaErrorInvalidValue;
+  rowfft_fft3d_kernel<N, DIR><<<grid, Cfg<N>::T, Cfg<N>::smem, stream>>>(a, tin, tout);
+  return cudaGetLastError();
+}
+
+template <int N, int DIR>
+KernelInfo info() {
+  KernelInfo k;
+  k.launch = &launch<N, DIR>;
+  k.func = (const void*)&rowfft_fft3d_kernel<N, DIR>;
+  k.threads = Cfg<N>::T;
+  k.smem = Cfg<N>::smem;
+  k.twiddle_entries = N;  // (the codelets need no table; one is uploaded anyway)
+  k.sizes[0] = N;
+  k.nsizes = 1;
+  k.items_in_flight = Cfg<N>::NTILE + 1;  // the tiles and one ticket held ahead
+  return k;
+}
+
+}  // namespace rowk
+}  // namespace fft3d

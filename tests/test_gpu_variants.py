@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 FP32_TOL = 5e-6
 CASES = [(n, v) for n in (16, 32, 48, 64, 80, 96, 128) for v in (0, 1)]
 CASES += [(64, 2), (128, 2), (16, 3), (32, 3), (64, 3)]
-CASES += [(32, 4), (48, 4), (64, 4), (80, 4), (96, 4), (64, 5), (128, 5)]
+CASES += [(32, 4), (48, 4), (64, 4), (80, 4), (96, 4), (64, 5), (128, 5), (64, 6), (64, 7)]
 
 
 @pytest.mark.parametrize("n,variant", CASES)
