@@ -55,7 +55,7 @@ struct Cfg {
   static constexpr int TILE = NSEG * REGION;       // bytes of one item
   static constexpr int NTILE = 6;
   static constexpr int SCHED = 8192;               // schedule blocks kept in shared memory
-  static constexpr int GROUPS = 4;                 // compute groups of N threads
+  static constexpr int GROUPS = 3;                 // compute groups of N threads
   static constexpr int GW = N / 32;                // warps per group
   static constexpr int NCW = GROUPS * GW;          // compute warps
   static constexpr int T = 32 * (NCW + 2);         // plus producer and signaller
@@ -69,24 +69,6 @@ template <int N>
 __device__ __forceinline__ uint32_t eoff(int r, int c) {
   return (uint32_t)((c >> 4) * Cfg<N>::REGION + r * 128 + ((((c & 15) >> 1) ^ (r & 7)) << 4) +
                     ((c & 1) << 3));
-}
-
-__device__ __forceinline__ float4 lds128(uint32_t a) {
-  float4 v;
-  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-               : "r"(a));
-  return v;
-}
-__device__ __forceinline__ void sts128(uint32_t a, float4 v) {
-  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z),
-               "f"(v.w)
-               : "memory");
-}
-__device__ __forceinline__ float2 lds64(uint32_t a) {
-  float2 v;
-  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
-  return v;
 }
 
 // 2D box (16 complex wide) of a 3D tensor map into shared memory.
@@ -111,13 +93,16 @@ __device__ __forceinline__ Desc bcast(Desc d) {
   return d;
 }
 
-// Producer warp (lane 0 works): tickets in order into tiles k % NTILE.
+// Producer warp: tickets in order into tiles k % NTILE.  Lane 0 takes and
+// resolves the tickets; lanes 0 .. NSEG-1 issue one tensor box each.
 // Tensors are viewed as [N * batch][N][2N] floats (z of all grids, y, x
 // interleaved re/im); planes come from `in`, slabs from `out`.  Schedule
 // block b (tickets b*N .. b*N + N - 1) is read from `sched` (grid * 2 +
 // phase) when the schedule fits there, else from global memory.  A failure
 // elsewhere is seen at the next dependency wait; until then the producer
-// keeps taking tickets without reading the status word.
+// keeps taking tickets without reading the status word.  The next item is
+// resolved (and a slab's planes waited for) before its tile is free, so
+// those round trips overlap the tile's previous item.
 template <int N>
 __device__ __forceinline__ void producer(const FusedArgs& a, const CUtensorMap* tin,
                                          const CUtensorMap* tout, uint32_t tiles,
@@ -125,71 +110,144 @@ __device__ __forceinline__ void producer(const FusedArgs& a, const CUtensorMap* 
                                          Desc* desc, const unsigned short* sched) {
   using K = Cfg<N>;
   constexpr int NT = K::NTILE;
-  if ((threadIdx.x & 31) != 0) return;
-  auto take = [&]() -> int { return (int)atomicAdd(a.work, 1u); };
+  const int lane = threadIdx.x & 31;
   const bool local = a.nblocks <= K::SCHED;
-  unsigned live = 0;  // tiles whose copies were issued (bit s)
-  int next = take();
+  auto block_of = [&](int b, int& grid, int& phase) {
+    if (local) {
+      grid = sched[b] >> 1;
+      phase = sched[b] & 1;
+    } else {
+      const SchedBlock blk = a.blocks[b];
+      grid = blk.grid;
+      phase = blk.phase;
+    }
+  };
+  // L2 hint for a ticket this warp will load soon: a plane item's input
+  // (one contiguous plane) is fetched from HBM now, so that its tensor copies
+  // later read L2.
+  auto prefetch_item = [&](int t) {
+    if (t >= a.total_items) return;
+    int grid, phase;
+    block_of(t / N, grid, phase);
+    if (phase != 0) return;
+    const float2* gin;
+    float2* gout;
+    grid_ptrs(a, grid, N, gin, gout);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(
+                     gin + (long long)(t % N) * N * N),
+                 "r"((unsigned)(N * N * sizeof(float2)))
+                 : "memory");
+  };
+  // Tickets two at a time (t even; N is even, so a pair never spans two
+  // schedule blocks), requested two pairs ahead.  When the tickets of pair
+  // p are about to be issued, those of pair p + 1 are resolved by lanes 0
+  // and 1 together: schedule lookup, an L2 prefetch of a plane's input, and
+  // a non-blocking probe of a slab's dependencies, so the two round trips
+  // overlap each other and the copies of pair p.
+  auto take2 = [&]() -> int { return (int)atomicAdd(a.work, 2u); };
+  int ahead = 0;  // lane 0: base of the pair after the next
+  // resolved tickets, lanes 0 and 1 (ticket base + lane): current pair, next pair
+  int ct = a.total_items, cg = 0, cph = 0, crd = 1;
+  int nt = a.total_items, ng = 0, nph = 0, nrd = 1;
+  int ready_grid = -1;  // lanes 0, 1: a grid whose planes this lane saw all published
+  auto resolve = [&](int base, int& t, int& grid, int& phase, int& rd) {
+    t = base + lane;
+    grid = 0;
+    phase = 0;
+    rd = 1;
+    if (lane < 2 && t < a.total_items) {
+      block_of(t / N, grid, phase);
+      if (phase == 0) {
+        prefetch_item(t);
+      } else if (grid != ready_grid) {
+        rd = ld_acquire(a.work + 1 + grid) >= (unsigned)N;
+        if (rd) ready_grid = grid;
+      }
+    }
+  };
+  {
+    int b0 = 0, b1 = 0;
+    if (lane == 0) {  // same-address atomics of one thread: b0 < b1 < ahead
+      b0 = take2();
+      b1 = take2();
+      ahead = take2();
+    }
+    b0 = __shfl_sync(0xffffffffu, b0, 0);
+    b1 = __shfl_sync(0xffffffffu, b1, 0);
+    resolve(b0, ct, cg, cph, crd);
+    resolve(b1, nt, ng, nph, nrd);
+  }
+  unsigned live = 0;    // tiles whose copies were issued (bit s)
   int k = 0;
   for (;; ++k) {
     const int s = k % NT;
-    if (k >= NT && !mbar_wait_bounded(&freed[s], (k / NT - 1) & 1, a.status, a.timeout_ns)) break;
-    live &= ~(1u << s);
-    const int t = next;
-    next = take();  // one ticket ahead: its round trip overlaps this item
-    Desc d{-1, 0, 0, 0};
-    bool ok = t < a.total_items;
-    if (ok) {
-      const int b = t / N;  // N tickets per block (one edge)
-      int grid, phase;
-      if (local) {
-        grid = sched[b] >> 1;
-        phase = sched[b] & 1;
-      } else {
-        const SchedBlock blk = a.blocks[b];
-        grid = blk.grid;
-        phase = blk.phase;
+    if (k > 0 && (k & 1) == 0) {  // next pair becomes current; resolve the one after
+      ct = nt, cg = ng, cph = nph, crd = nrd;
+      int bn = 0;
+      if (lane == 0) {
+        bn = ahead;
+        ahead = take2();
       }
-      d = Desc{t, grid, phase, t - b * N};
-      if (phase == 1)
-        ok = bounded_wait_geq(a.work + 1 + grid, (unsigned)N, a.status, a.timeout_ns);
+      bn = __shfl_sync(0xffffffffu, bn, 0);
+      resolve(bn, nt, ng, nph, nrd);
     }
+    const int src = k & 1;  // lane holding this item's ticket
+    const int t = __shfl_sync(0xffffffffu, ct, src);
+    Desc d{t, __shfl_sync(0xffffffffu, cg, src), __shfl_sync(0xffffffffu, cph, src), t % N};
+    const int rd = __shfl_sync(0xffffffffu, crd, src);
+    int ok = t < a.total_items;
+    if (ok && !rd && lane == 0)  // a slab whose planes were not all published yet
+      ok = bounded_wait_geq(a.work + 1 + d.grid, (unsigned)N, a.status, a.timeout_ns);
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    __syncwarp();  // lane 0's (or 1's) acquire before the copies of every lane
     if (!ok) {
       // a stop for each compute group: items k .. k + GROUPS - 1 (each tile
       // once the signaller has freed its earlier item)
-      for (int j = 0; j < K::GROUPS; ++j) {
-        const int kk = k + j, sj = kk % NT;
-        if (j > 0 && kk >= NT &&
-            !mbar_wait_bounded(&freed[sj], (kk / NT - 1) & 1, a.status, a.timeout_ns))
-          break;
-        desc[sj] = Desc{-1, 0, 0, 0};
-        mbar_arrive(&full[sj]);
-        live &= ~(1u << sj);
+      if (lane == 0) {
+        for (int j = 0; j < K::GROUPS; ++j) {
+          const int kk = k + j, sj = kk % NT;
+          if (kk >= NT &&
+              !mbar_wait_bounded(&freed[sj], (kk / NT - 1) & 1, a.status, a.timeout_ns))
+            break;
+          desc[sj] = Desc{-1, 0, 0, 0};
+          mbar_arrive(&full[sj]);
+          live &= ~(1u << sj);
+        }
       }
+      live = __shfl_sync(0xffffffffu, live, 0);
       break;
     }
-    desc[s] = d;
-    // the tile was last written by the compute threads' plain stores, a
-    // slab's rows by other blocks' plain stores
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    if (d.phase == 1) asm volatile("fence.proxy.async.global;" ::: "memory");
-    mbar_arrive_tx(&full[s], (unsigned)K::TILE);
-    const uint32_t dst = tiles + (uint32_t)(s * K::TILE);
-    for (int b = 0; b < K::NSEG; ++b) {
+    if (k >= NT && !__all_sync(0xffffffffu, mbar_wait_bounded(&freed[s], (k / NT - 1) & 1,
+                                                               a.status, a.timeout_ns)))
+      break;
+    live &= ~(1u << s);
+    if (lane == 0) {
+      desc[s] = d;
+      mbar_arrive_tx(&full[s], (unsigned)K::TILE);
+    }
+    __syncwarp();
+    if (lane < K::NSEG) {
+      // the tile was last written by the compute threads' plain stores, a
+      // slab's rows by other blocks' plain stores (seen through lane 0's
+      // acquire)
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      if (d.phase == 1) asm volatile("fence.proxy.async.global;" ::: "memory");
+      const uint32_t dst = tiles + (uint32_t)(s * K::TILE + lane * K::REGION);
       if (d.phase == 0)  // plane z = idx: box {16 x, all y} at z
-        tma_box(dst + b * K::REGION, tin, 2 * K::SEG * b, 0, d.grid * N + d.idx, &full[s]);
+        tma_box(dst, tin, 2 * K::SEG * lane, 0, d.grid * N + d.idx, &full[s]);
       else  // slab y = idx: box {16 x, all z} at y
-        tma_box(dst + b * K::REGION, tout, 2 * K::SEG * b, d.idx, d.grid * N, &full[s]);
+        tma_box(dst, tout, 2 * K::SEG * lane, d.idx, d.grid * N, &full[s]);
     }
     live |= 1u << s;
   }
   // no copy may still be writing a tile when the block exits (only after a
   // failure can one be left unconsumed)
-  for (int j = 1; j <= NT; ++j) {
-    const int kk = k - j;
-    if (kk >= 0 && (live & (1u << (kk % NT))))
-      mbar_wait_bounded(&full[kk % NT], (kk / NT) & 1, a.status, a.timeout_ns);
-  }
+  if (lane == 0)
+    for (int j = 1; j <= NT; ++j) {
+      const int kk = k - j;
+      if (kk >= 0 && (live & (1u << (kk % NT))))
+        mbar_wait_bounded(&full[kk % NT], (kk / NT) & 1, a.status, a.timeout_ns);
+    }
 }
 
 // Signaller warp: items in order; once the compute group is done with one,
@@ -267,7 +325,7 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
     if (!warp_wait(&full[s], (k / NT) & 1, a)) break;
     const Desc d = desc[s];
     if (d.item < 0) break;
-    const uint32_t t = tiles + (uint32_t)(s * K::TILE);
+    unsigned char* t = base + (size_t)s * K::TILE;
     const float2* gin;
     float2* gout;
     grid_ptrs(a, d.grid, N, gin, gout);
@@ -276,22 +334,22 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
       // x: row y = gt, 16-byte chunks
 #pragma unroll
       for (int j = 0; j < N / 2; ++j) {
-        const float4 q = lds128(t + eoff<N>(gt, 2 * j));
+        const float4 q = *reinterpret_cast<const float4*>(t + eoff<N>(gt, 2 * j));
         v[2 * j] = make_float2(q.x, q.y);
         v[2 * j + 1] = make_float2(q.z, q.w);
       }
       DFT<N, DIR>::run(v);
 #pragma unroll
       for (int j = 0; j < N / 2; ++j)
-        sts128(t + eoff<N>(gt, 2 * j), make_float4(v[2 * j].x, v[2 * j].y, v[2 * j + 1].x,
-                                                   v[2 * j + 1].y));
+        *reinterpret_cast<float4*>(t + eoff<N>(gt, 2 * j)) =
+            make_float4(v[2 * j].x, v[2 * j].y, v[2 * j + 1].x, v[2 * j + 1].y);
       __syncwarp();
       if (lane == 0) mbar_arrive(&tr[g]);
       if (!warp_wait(&tr[g], planes & 1, a)) break;
       ++planes;
       // y: column x = gt, output rows straight to global memory
 #pragma unroll
-      for (int r = 0; r < N; ++r) v[r] = lds64(t + eoff<N>(r, gt));
+      for (int r = 0; r < N; ++r) v[r] = *reinterpret_cast<const float2*>(t + eoff<N>(r, gt));
       DFT<N, DIR>::run(v);
       float2* dst = gout + (long long)d.idx * NN + gt;
 #pragma unroll
@@ -299,7 +357,7 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
     } else {
       // z: column x = gt of slab y = idx
 #pragma unroll
-      for (int z = 0; z < N; ++z) v[z] = lds64(t + eoff<N>(z, gt));
+      for (int z = 0; z < N; ++z) v[z] = *reinterpret_cast<const float2*>(t + eoff<N>(z, gt));
       DFT<N, DIR>::run(v);
       float2* dst = gout + (long long)d.idx * N + gt;
 #pragma unroll
@@ -363,7 +421,7 @@ KernelInfo info() {
   k.twiddle_entries = N;  // (the codelets need no table; one is uploaded anyway)
   k.sizes[0] = N;
   k.nsizes = 1;
-  k.items_in_flight = Cfg<N>::NTILE + 1;  // the tiles and one ticket held ahead
+  k.items_in_flight = Cfg<N>::NTILE + 4;  // the tiles and up to four tickets held ahead
   return k;
 }
 
