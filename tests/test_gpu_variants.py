@@ -39,11 +39,12 @@ def test_variant_matches_oracle(cuda, monkeypatch, n, variant):
             assert oracle.rel_l2(yc[b], ref[b]) <= FP32_TOL
 
 
-@pytest.mark.parametrize("n", [16, 32, 64])
-def test_cluster_variant_in_place_and_many_grids(cuda, monkeypatch, n):
-    """More grids than clusters (each cluster loops) and in == out."""
+@pytest.mark.parametrize("n,variant", [(16, 3), (32, 3), (64, 3), (64, 6), (64, 7)])
+def test_variant_in_place_and_many_grids(cuda, monkeypatch, n, variant):
+    """More grids than blocks or clusters (every block goes many times round
+    its tiles or loops over grids) and in == out."""
     from paper_2006_08435_gb300 import Plan
-    monkeypatch.setenv("FFT3D_VARIANT", "3")
+    monkeypatch.setenv("FFT3D_VARIANT", str(variant))
     batch = 200 if n == 64 else 700
     x = torch.from_numpy(synth.uniform_grids(n, 1, seed=n)).cuda().repeat(batch, 1, 1, 1)
     x = (x * torch.arange(1, batch + 1, device="cuda").view(-1, 1, 1, 1)).contiguous()
