@@ -62,6 +62,8 @@ struct KernelInfo {
   int items_in_flight = 1;      // work items a block holds at once (schedule lag)
   int prec = 0;                 // 0 FP32, else fft3d_precision of the tensor-core kinds
   int cluster = 0;              // > 0: cluster kernel of this many blocks per cluster
+  int tw_l1 = 0;                // twiddle table split n = l1 * (n / l1); 0: item_l1(n, prec)
+  int phase_items = 0;          // work items per phase of a grid; 0: the grid's edge
 };
 
 // Defined in the inst_*.cu translation units.

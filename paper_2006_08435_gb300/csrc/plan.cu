@@ -124,7 +124,7 @@ std::vector<int> variant_candidates(bool mixed, int n, int precision) {
     case 16: return {0, 1, 3};
     case 32: return {0, 1, 3, 4};
     case 64: return {0, 1, 2, 3, 4, 5, 6, 7};
-    case 128: return {0, 1, 2, 5};
+    case 128: return {0, 1, 2, 5, 6};
     default: return {0, 1, 4};  // 48, 80, 96
   }
 }
@@ -228,12 +228,13 @@ int check_device() {
 // whose planes are done but whose slabs are not yet scheduled would exceed
 // `l2_budget` bytes (their intermediate must stay in L2).
 std::vector<SchedBlock> build_schedule(const std::vector<int>& dims, const std::vector<int>& order,
-                                       int concurrency, double l2_budget, int* total_items) {
+                                       int concurrency, double l2_budget, int phase_items,
+                                       int* total_items) {
   std::vector<SchedBlock> blocks;
   int start = 0;
   auto push = [&](int g, int phase) {
     blocks.push_back(SchedBlock{g, phase, start, dims[g]});
-    start += dims[g];
+    start += phase_items > 0 ? phase_items : dims[g];
   };
   struct Pending {
     int g;
@@ -330,7 +331,8 @@ int finish_unit(fft3d_plan p, Unit& u, bool identity) {
   const int resident = per_sm * sms;
   int total_items = 0;
   const std::vector<SchedBlock> blocks = build_schedule(
-      ldims, order, resident * u.kernel.items_in_flight, 0.4 * (double)l2_bytes, &total_items);
+      ldims, order, resident * u.kernel.items_in_flight, 0.4 * (double)l2_bytes,
+      u.kernel.phase_items, &total_items);
   u.total_items = total_items;
   u.nblocks = (int)blocks.size();
   u.grid = cluster_blocks > 0 ? cluster_blocks : std::max(1, std::min(total_items, resident));
@@ -340,7 +342,7 @@ int finish_unit(fft3d_plan p, Unit& u, bool identity) {
   size_t off = 0;
   for (int i = 0; i < u.kernel.nsizes; ++i) {
     const int n = u.kernel.sizes[i];
-    twiddle_table(n, item_l1(n, u.kernel.prec), tw.data() + 2 * off);
+    twiddle_table(n, u.kernel.tw_l1 ? u.kernel.tw_l1 : item_l1(n, u.kernel.prec), tw.data() + 2 * off);
     off += n;
   }
   int rc;

@@ -386,15 +386,16 @@ inline PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// [N * batch][N][2N] floats, box {32 floats (16 complex), by, bz}, 128-byte swizzle.
+// [N * batch][N][2N] floats, box {32 floats (16 complex), by, bz}, 128-byte
+// swizzle; along y every `ystep`-th row is taken (by = rows * ystep).
 inline bool encode_map(CUtensorMap* m, const void* base, int n, int batch, unsigned by,
-                       unsigned bz) {
+                       unsigned bz, unsigned ystep = 1) {
   auto fn = encode_fn();
   if (!fn) return false;
   const cuuint64_t dims[3] = {(cuuint64_t)2 * n, (cuuint64_t)n, (cuuint64_t)n * batch};
   const cuuint64_t strides[2] = {(cuuint64_t)n * 8, (cuuint64_t)n * n * 8};
   const cuuint32_t box[3] = {32, by, bz};
-  const cuuint32_t estr[3] = {1, 1, 1};
+  const cuuint32_t estr[3] = {1, ystep, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;

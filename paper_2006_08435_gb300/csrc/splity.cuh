@@ -1,0 +1,413 @@
+// Persistent 3D FFT kernel for 128^3 grids with the y transform split in
+// two, so that every work item is 64 KB and a block can keep three of them in
+// shared memory (a whole 128^3 plane, 128 KB, fits only once).
+//
+// With n = 128 = 2 * 64 and y = n1 + 2 n2 (n1 the parity of the row), the y
+// transform of Eq. 1 is
+//   Y[k2 + 64 k1] = A0[k2] + (-1)^k1 W_128^k2 A1[k2],
+//   A_n1[k2] = sum over n2 of x[n1 + 2 n2] W_64^(n2 k2),
+// a 64-point DFT over the rows of one parity, a twiddle, and a radix-2 step.
+// The items are
+//
+//   half-plane (plane z, parity n1): the 64 rows y = n1 + 2 n2 of plane z
+//     (one tensor copy with a row step of 2): x transform of each row, then
+//     the 64-point y DFT of each column, times W_128^(n1 k2); stored to
+//     rows n1 * 64 + k2 of the output plane.
+//   slab (k2, x quarter q): rows y = k2 and k2 + 64 of every z, columns
+//     32 q .. 32 q + 31: the radix-2 step of y (rows k2 +- W A1 -> k2, k2 +
+//     64), then the z transform of each of the 64 columns, in place.
+//
+// Slabs of a grid wait for all 256 half-planes of that grid, as in the
+// persistent kernel.  Every 128-point FFT (x and z) runs in a pair of
+// threads: thread p holds the points p + 2 m (m < 64), does a 64-point DFT
+// in registers, multiplies by W_128^(p k), and the pair finishes with one
+// radix-2 step after exchanging half of their values with warp shuffles;
+// the 64-point y DFT runs in one thread.  Tiles are tensor copies with
+// 128-byte swizzling, and the lane orders are chosen so that every shared-
+// memory access is free of bank conflicts.
+//
+// Block: two compute groups of 128 threads (items k = g, g + 2, ...), one
+// producer warp (tickets, L2 prefetch of a plane, slab dependencies, tensor
+// copies into a ring of three tiles) and one signaller warp (frees tiles,
+// publishes finished half-planes).  Liveness and bounded waits as in the
+// thread-per-pencil 64^3 kernel.
+#pragma once
+
+#include "rowfft.cuh"
+
+namespace fft3d {
+namespace sy {
+
+using piped::mbar_arrive;
+using piped::mbar_arrive_tx;
+using piped::mbar_init;
+using piped::mbar_wait_bounded;
+using piped::saddr;
+using piped::warp_wait;
+using rowk::bcast;
+using rowk::Desc;
+using rowk::tma_box;
+
+template <int N>
+struct Cfg {
+  static_assert(N == 128, "split-y kernel covers 128");
+  static constexpr int H = N / 2;               // points per thread
+  static constexpr int TILE = 65536;            // bytes of one item
+  static constexpr int NTILE = 3;
+  static constexpr int GT = 128;                // threads per compute group
+  static constexpr int GW = GT / 32;
+  static constexpr int GROUPS = 2;
+  static constexpr int NCW = GROUPS * GW;       // compute warps (warpgroups 1, 2)
+  static constexpr int T = 32 * (NCW + 4);      // plus warpgroup 0: producer, signaller, 2 idle
+  // registers per thread: at launch (T threads fit the register file, three
+  // warps per SM sub-partition), then redistributed with setmaxnreg: the
+  // control warpgroup gives up most of its share, the compute warpgroups take
+  // it (per sub-partition 48 + 2 * 224 <= 3 * 168, and in total
+  // 4 * 32 * 48 + 8 * 32 * 224 <= 12 * 32 * 168, the launch total)
+  static constexpr int REG_LAUNCH = 168, REG_CTRL = 48, REG_COMP = 224;
+  static constexpr int ITEMS = 2 * N;           // items per phase of a grid
+  static constexpr int SCHED = 8192;            // schedule blocks kept in shared memory
+  static constexpr size_t smem = 1024 + (size_t)NTILE * TILE +
+                                 (2 * NTILE + GROUPS) * sizeof(unsigned long long) +
+                                 NTILE * sizeof(int4) + SCHED * sizeof(unsigned short);
+};
+
+// Byte offsets (128-byte swizzle).  Half-plane: row r < 64, column c < 128,
+// boxes of 16 columns, 8 KB each.  Slab: row r in {0, 1} (y = k2, k2 + 64),
+// z < 128, local column x < 32, boxes [r][x / 16] of 16 KB.
+__device__ __forceinline__ uint32_t hoff(int r, int c) {
+  return (uint32_t)((c >> 4) * 8192 + r * 128 + ((((c & 15) >> 1) ^ (r & 7)) << 4) + ((c & 1) << 3));
+}
+__device__ __forceinline__ uint32_t soff(int r, int z, int x) {
+  return (uint32_t)((r * 2 + (x >> 4)) * 16384 + z * 128 + ((((x & 15) >> 1) ^ (z & 7)) << 4) +
+                    ((x & 1) << 3));
+}
+
+// 128-point FFT finished by a thread pair: v holds this thread's 64-point
+// DFT of points p + 2 m.  After the twiddle and the exchange with the
+// partner (lane ^ xm), the outputs are handed over two at a time:
+// store(j, X[j + 32 p], X[j + 1 + 32 p], X[j + 32 p + 64], X[j + 33 + 32 p + 32])
+// for even j < 32, i.e. store(j, a0, a1, b0, b1) with a_u = X[j + u + 32 p]
+// and b_u = X[j + u + 32 p + 64].
+template <int DIR, class Store>
+__device__ __forceinline__ void pair_radix2(float2* v, int p, int xm, Store store) {
+  // times W_128^(p k): compile-time twiddles, selected by the thread's parity
+  static_for<1, 64>([&](auto K) {
+    constexpr int k = decltype(K)::value;
+    const float2 t = twc<k, 128, DIR>(v[k]);
+    v[k] = p ? t : v[k];
+  });
+#pragma unroll
+  for (int j = 0; j < 32; j += 2) {
+    float2 av[2], bv[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const float2 send = p ? v[j + u] : v[32 + j + u];
+      float2 recv;
+      recv.x = __shfl_xor_sync(0xffffffffu, send.x, xm);
+      recv.y = __shfl_xor_sync(0xffffffffu, send.y, xm);
+      const float2 mine = p ? v[32 + j + u] : v[j + u];  // this thread's k2 = j + u + 32 p
+      const float2 e = p ? recv : mine, o = p ? mine : recv;
+      av[u] = cadd(e, o);
+      bv[u] = csub(e, o);
+    }
+    store(j, av[0], av[1], bv[0], bv[1]);
+  }
+}
+
+// ------------------------------------------------------------- producer
+// Lanes 0..7 issue the tensor boxes; lane 0 takes and resolves tickets
+// (pairs, one pair ahead; a pair of half-planes is one plane, prefetched into
+// L2 when the pair is taken).  Tensors are [N * batch][N][2N] floats.
+template <int N>
+__device__ __forceinline__ void producer(const FusedArgs& a, const CUtensorMap* tin,
+                                         const CUtensorMap* tout, uint32_t tiles,
+                                         unsigned long long* full, unsigned long long* freed,
+                                         Desc* desc, const unsigned short* sched) {
+  using K = Cfg<N>;
+  constexpr int NT = K::NTILE, IT = K::ITEMS;
+  const int lane = threadIdx.x & 31;
+  const bool local = a.nblocks <= K::SCHED;
+  auto block_of = [&](int b, int& grid, int& phase) {
+    if (local) {
+      grid = sched[b] >> 1;
+      phase = sched[b] & 1;
+    } else {
+      const SchedBlock blk = a.blocks[b];
+      grid = blk.grid;
+      phase = blk.phase;
+    }
+  };
+  auto prefetch_pair = [&](int t) {  // t even
+    if (t >= a.total_items) return;
+    int grid, phase;
+    block_of(t / IT, grid, phase);
+    if (phase != 0) return;
+    const float2* gin;
+    float2* gout;
+    grid_ptrs(a, grid, N, gin, gout);
+    const char* p = reinterpret_cast<const char*>(gin + (long long)((t % IT) >> 1) * N * N);
+    for (int c = 0; c < 4; ++c)  // the plane, 4 x 32 KB
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p + c * 32768),
+                   "r"(32768u)
+                   : "memory");
+  };
+  auto take2 = [&]() -> int { return (int)atomicAdd(a.work, 2u); };
+  int base = 0, ahead = 0;
+  if (lane == 0) {
+    base = take2();
+    ahead = take2();
+    prefetch_pair(base);
+  }
+  bool second = false;
+  auto next_ticket = [&]() -> int {
+    if (!second) {
+      second = true;
+      return base;
+    }
+    second = false;
+    const int t = base + 1;
+    base = ahead;
+    ahead = take2();
+    prefetch_pair(base);
+    return t;
+  };
+  int ready_grid = -1;
+  unsigned live = 0;
+  int k = 0;
+  for (;; ++k) {
+    const int s = k % NT;
+    Desc d{-1, 0, 0, 0};
+    int ok = 0;
+    if (lane == 0) {
+      const int t = next_ticket();
+      ok = t < a.total_items;
+      if (ok) {
+        const int b = t / IT;
+        int grid, phase;
+        block_of(b, grid, phase);
+        d = Desc{t, grid, phase, t - b * IT};
+        if (phase == 1 && grid != ready_grid) {
+          ok = bounded_wait_geq(a.work + 1 + grid, (unsigned)IT, a.status, a.timeout_ns);
+          if (ok) ready_grid = grid;
+        }
+      }
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (!ok) {
+      // a stop for each compute group: items k .. k + GROUPS - 1
+      if (lane == 0)
+        for (int j = 0; j < K::GROUPS; ++j) {
+          const int kk = k + j, sj = kk % NT;
+          if (kk >= NT &&
+              !mbar_wait_bounded(&freed[sj], (kk / NT - 1) & 1, a.status, a.timeout_ns))
+            break;
+          desc[sj] = Desc{-1, 0, 0, 0};
+          mbar_arrive(&full[sj]);
+          live &= ~(1u << sj);
+        }
+      live = __shfl_sync(0xffffffffu, live, 0);
+      break;
+    }
+    d = bcast(d);
+    if (k >= NT && !__all_sync(0xffffffffu, mbar_wait_bounded(&freed[s], (k / NT - 1) & 1,
+                                                               a.status, a.timeout_ns)))
+      break;
+    live &= ~(1u << s);
+    if (lane == 0) {
+      desc[s] = d;
+      mbar_arrive_tx(&full[s], (unsigned)K::TILE);
+    }
+    __syncwarp();
+    const uint32_t dst = tiles + (uint32_t)(s * K::TILE);
+    if (d.phase == 0 && lane < 8) {
+      // half-plane: plane z = idx / 2, rows y = parity + 2 m, 16 columns per box
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      tma_box(dst + lane * 8192, tin, 32 * lane, d.idx & 1, d.grid * N + (d.idx >> 1), &full[s]);
+    } else if (d.phase == 1 && lane < 4) {
+      // slab: rows y = k2 + 64 r, columns 32 q + 16 h, every z
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+      const int r = lane >> 1, h = lane & 1, k2 = d.idx >> 2, q = d.idx & 3;
+      tma_box(dst + (r * 2 + h) * 16384, tout, 2 * (32 * q + 16 * h), k2 + 64 * r, d.grid * N,
+              &full[s]);
+    }
+    live |= 1u << s;
+  }
+  if (lane == 0)
+    for (int j = 1; j <= NT; ++j) {
+      const int kk = k - j;
+      if (kk >= 0 && (live & (1u << (kk % NT))))
+        mbar_wait_bounded(&full[kk % NT], (kk / NT) & 1, a.status, a.timeout_ns);
+    }
+}
+
+// Signaller warp: items in order; once the compute group is done with one,
+// frees its tile and, for a half-plane, publishes it to the other blocks.
+template <int N>
+__device__ __forceinline__ void signaller(const FusedArgs& a, unsigned long long* full,
+                                          unsigned long long* empty,
+                                          unsigned long long* freed, Desc* desc) {
+  constexpr int NT = Cfg<N>::NTILE;
+  const int lane = threadIdx.x & 31;
+  for (int k = 0;; ++k) {
+    const int s = k % NT;
+    const unsigned par = (k / NT) & 1;
+    if (!warp_wait(&full[s], par, a)) return;
+    const Desc d = desc[s];
+    if (d.item < 0) return;
+    if (!warp_wait(&empty[s], par, a)) return;
+    if (lane == 0) {
+      mbar_arrive(&freed[s]);
+      if (d.phase == 0) {
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        atomicAdd(a.work + 1 + d.grid, 1u);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+template <int N, int DIR>
+__global__ void __launch_bounds__(Cfg<N>::T, 1)
+    splity_fft3d_kernel(const FusedArgs a, const __grid_constant__ CUtensorMap tin,
+                        const __grid_constant__ CUtensorMap tout) {
+  using K = Cfg<N>;
+  constexpr int NT = K::NTILE, H = K::H;
+  constexpr long long NN = (long long)N * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* base = smem_raw + ((1024 - (saddr(smem_raw) & 1023)) & 1023);
+  const uint32_t tiles = saddr(base);
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(base + (size_t)NT * K::TILE);
+  unsigned long long* empty = full + NT;
+  unsigned long long* freed = empty + NT;
+  unsigned long long* tr = freed + NT;  // per group: x done before y
+  Desc* desc = reinterpret_cast<Desc*>(tr + K::GROUPS);
+  unsigned short* sched = reinterpret_cast<unsigned short*>(desc + NT);
+  const int w = threadIdx.x >> 5;
+  if (a.nblocks <= K::SCHED)
+    for (int b = threadIdx.x; b < a.nblocks; b += K::T)
+      sched[b] = (unsigned short)(a.blocks[b].grid * 2 + a.blocks[b].phase);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NT; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], K::GW);
+      mbar_init(&freed[s], 1);
+    }
+    for (int g = 0; g < K::GROUPS; ++g) mbar_init(&tr[g], K::GW);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  if (w < 4) {  // warpgroup 0: control
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(K::REG_CTRL));
+    if (w == 0) sy::producer<N>(a, &tin, &tout, tiles, full, freed, desc, sched);
+    if (w == 1) sy::signaller<N>(a, full, empty, freed, desc);
+    return;
+  }
+  asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(K::REG_COMP));
+
+  // compute group g (warpgroup g + 1), thread gt of 128
+  const int g = (w - 4) / K::GW, gt = threadIdx.x - 128 - g * K::GT, lane = threadIdx.x & 31;
+  unsigned halves = 0;  // half-plane items of this group (parity of its barrier)
+  for (int k = g;; k += K::GROUPS) {
+    const int s = k % NT;
+    if (!warp_wait(&full[s], (k / NT) & 1, a)) break;
+    const Desc d = desc[s];
+    if (d.item < 0) break;
+    unsigned char* t = base + (size_t)s * K::TILE;
+    const float2* gin;
+    float2* gout;
+    grid_ptrs(a, d.grid, N, gin, gout);
+    float2 v[H];
+    if (d.phase == 0) {
+      // x: row r = gt / 2 of the tile, this thread's points p + 2 m
+      const int r = gt >> 1, p = gt & 1;
+#pragma unroll
+      for (int m = 0; m < H; ++m) v[m] = *reinterpret_cast<const float2*>(t + hoff(r, p + 2 * m));
+      DFT<H, DIR>::run(v);
+      __syncwarp();  // both threads of the row have read it
+      // write back X[c]; the odd thread stores the two of a pair in the other
+      // order, so the two threads of a row never hit the same bank
+      pair_radix2<DIR>(v, p, 1, [&](int j, float2 a0, float2 a1, float2 b0, float2 b1) {
+        const int c0 = j + 32 * p;
+        *reinterpret_cast<float2*>(t + hoff(r, c0 + p)) = p ? a1 : a0;
+        *reinterpret_cast<float2*>(t + hoff(r, c0 + 1 - p)) = p ? a0 : a1;
+        *reinterpret_cast<float2*>(t + hoff(r, c0 + 64 + p)) = p ? b1 : b0;
+        *reinterpret_cast<float2*>(t + hoff(r, c0 + 65 - p)) = p ? b0 : b1;
+      });
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tr[g]);
+      if (!warp_wait(&tr[g], halves & 1, a)) break;
+      ++halves;
+      // y: column c = gt, 64-point DFT over the rows of this parity
+      const int par = d.idx & 1, c = gt;
+#pragma unroll
+      for (int m = 0; m < H; ++m) v[m] = *reinterpret_cast<const float2*>(t + hoff(m, c));
+      DFT<H, DIR>::run(v);
+      if (par)  // times W_128^k2 (compile-time twiddles)
+        static_for<1, H>([&](auto K) {
+          constexpr int k2 = decltype(K)::value;
+          v[k2] = twc<k2, 128, DIR>(v[k2]);
+        });
+      float2* dst = gout + (long long)(d.idx >> 1) * NN + (long long)par * H * N + c;
+#pragma unroll
+      for (int k2 = 0; k2 < H; ++k2) dst[(long long)k2 * N] = v[k2];
+    } else {
+      // slab (k2, q): column x = 32 q + xl, output row y = k2 + 64 yr,
+      // this thread's z points p + 2 m
+      const int wl = w - 4 - g * K::GW;  // warp within the group
+      const int p = lane >> 4, xl = (wl & 1) * 16 + (lane & 15), yr = wl >> 1;
+      const int k2 = d.idx >> 2, q = d.idx & 3;
+#pragma unroll
+      for (int m = 0; m < H; ++m) {
+        const int z = p + 2 * m;
+        const float2 e = *reinterpret_cast<const float2*>(t + soff(0, z, xl));
+        const float2 o = *reinterpret_cast<const float2*>(t + soff(1, z, xl));
+        v[m] = yr ? csub(e, o) : cadd(e, o);
+      }
+      DFT<H, DIR>::run(v);
+      float2* dst = gout + (long long)(k2 + H * yr) * N + 32 * q + xl;
+      const float sc = a.do_scale ? a.scale : 1.f;
+      pair_radix2<DIR>(v, p, 16, [&](int j, float2 a0, float2 a1, float2 b0, float2 b1) {
+        float2* d0 = dst + (long long)(j + 32 * p) * NN;
+        st_stream(d0, cscale(a0, sc));
+        st_stream(d0 + NN, cscale(a1, sc));
+        st_stream(d0 + H * NN, cscale(b0, sc));
+        st_stream(d0 + (H + 1) * NN, cscale(b1, sc));
+      });
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+  }
+}
+
+// Uniform batches only (packed buffers, grids in plan order).
+template <int N, int DIR>
+cudaError_t launch(const FusedArgs& a, int grid, cudaStream_t stream) {
+  if (a.in_ptrs || a.grid_map || a.grid_off) return cudaErrorInvalidValue;
+  CUtensorMap tin, tout;
+  if (!rowk::encode_map(&tin, a.in, N, a.ngrids, 2 * (N / 2), 1, 2) ||
+      !rowk::encode_map(&tout, a.out, N, a.ngrids, 1, N))
+    return cudaErrorInvalidValue;
+  splity_fft3d_kernel<N, DIR><<<grid, Cfg<N>::T, Cfg<N>::smem, stream>>>(a, tin, tout);
+  return cudaGetLastError();
+}
+
+template <int N, int DIR>
+KernelInfo info() {
+  KernelInfo k;
+  k.launch = &launch<N, DIR>;
+  k.func = (const void*)&splity_fft3d_kernel<N, DIR>;
+  k.threads = Cfg<N>::T;
+  k.smem = Cfg<N>::smem;
+  k.twiddle_entries = N;  // (the codelets need no table; one is uploaded anyway)
+  k.sizes[0] = N;
+  k.nsizes = 1;
+  k.items_in_flight = Cfg<N>::NTILE + 4;  // the tiles and up to four tickets held ahead
+  k.phase_items = Cfg<N>::ITEMS;
+  return k;
+}
+
+}  // namespace sy
+}  // namespace fft3d
