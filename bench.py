@@ -43,10 +43,11 @@ METRIC = "batched 3D FFT transforms/s and % of HBM roofline at 64^3/128^3 (FP32 
 KERNEL_SOURCES = ["paper_2006_08435_gb300/csrc/persistent.cuh",
                   "paper_2006_08435_gb300/csrc/pipelined.cuh",
                   "paper_2006_08435_gb300/csrc/rowfft.cuh",
+                  "paper_2006_08435_gb300/csrc/splity.cuh",
                   "paper_2006_08435_gb300/csrc/codelets.cuh",
                   "paper_2006_08435_gb300/csrc/tc_stage.cuh",
                   "paper_2006_08435_gb300/csrc/sizes.h"]
-KERNEL_NAMES = {128: "piped_fft3d_kernel<128,-1>", 64: "rowfft_fft3d_kernel<64,-1>"}
+KERNEL_NAMES = {128: "splity_fft3d_kernel<128,-1>", 64: "rowfft_fft3d_kernel<64,-1>"}
 
 
 def dist_env():

@@ -134,7 +134,7 @@ std::vector<int> variant_candidates(bool mixed, int n, int precision) {
 // plain persistent kernel otherwise.
 int builtin_default_variant(bool mixed, int n, int batch, int precision) {
   if (mixed || precision != FFT3D_FP32) return 0;
-  if (n == 128) return 2;
+  if (n == 128) return batch >= 4 ? 6 : 2;  // split-y from 4 grids, measured faster
   if ((n == 16 || n == 32) && batch >= 64) return 3;
   if (n == 64 && batch >= 16) return 7;  // thread-per-pencil, measured faster from 16 grids
   return 0;

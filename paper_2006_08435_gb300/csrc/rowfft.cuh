@@ -71,6 +71,30 @@ __device__ __forceinline__ uint32_t eoff(int r, int c) {
                     ((c & 1) << 3));
 }
 
+// L2 eviction policies (fraction 1.0 of the accessed lines).
+__device__ __forceinline__ unsigned long long policy_evict_first() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ unsigned long long policy_evict_last() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+// As tma_box, with an L2 eviction policy for the lines it reads.
+__device__ __forceinline__ void tma_box_hint(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                             int z, unsigned long long* bar,
+                                             unsigned long long policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      ".L2::cache_hint [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(dst),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(saddr(bar)),
+      "l"(policy)
+      : "memory");
+}
+
 // 2D box (16 complex wide) of a 3D tensor map into shared memory.
 __device__ __forceinline__ void tma_box(uint32_t dst, const CUtensorMap* map, int x, int y, int z,
                                         unsigned long long* bar) {

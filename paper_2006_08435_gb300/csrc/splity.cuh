@@ -27,8 +27,9 @@
 // memory access is free of bank conflicts.
 //
 // Block: two compute groups of 128 threads (items k = g, g + 2, ...), one
-// producer warp (tickets, L2 prefetch of a plane, slab dependencies, tensor
-// copies into a ring of three tiles) and one signaller warp (frees tiles,
+// producer warp (tickets, slab dependencies, tensor copies into a ring of
+// three tiles; every copy marked evict-first in L2, the intermediate's stores
+// evict-last, so the intermediate stays in L2 until its slabs read it) and one signaller warp (frees tiles,
 // publishes finished half-planes).  Liveness and bounded waits as in the
 // thread-per-pencil 64^3 kernel.
 #pragma once
@@ -46,7 +47,9 @@ using piped::saddr;
 using piped::warp_wait;
 using rowk::bcast;
 using rowk::Desc;
-using rowk::tma_box;
+using rowk::policy_evict_first;
+using rowk::policy_evict_last;
+using rowk::tma_box_hint;
 
 template <int N>
 struct Cfg {
@@ -117,8 +120,7 @@ __device__ __forceinline__ void pair_radix2(float2* v, int p, int xm, Store stor
 
 // ------------------------------------------------------------- producer
 // Lanes 0..7 issue the tensor boxes; lane 0 takes and resolves tickets
-// (pairs, one pair ahead; a pair of half-planes is one plane, prefetched into
-// L2 when the pair is taken).  Tensors are [N * batch][N][2N] floats.
+// (pairs, one pair ahead).  Tensors are [N * batch][N][2N] floats.
 template <int N>
 __device__ __forceinline__ void producer(const FusedArgs& a, const CUtensorMap* tin,
                                          const CUtensorMap* tout, uint32_t tiles,
@@ -138,26 +140,11 @@ __device__ __forceinline__ void producer(const FusedArgs& a, const CUtensorMap* 
       phase = blk.phase;
     }
   };
-  auto prefetch_pair = [&](int t) {  // t even
-    if (t >= a.total_items) return;
-    int grid, phase;
-    block_of(t / IT, grid, phase);
-    if (phase != 0) return;
-    const float2* gin;
-    float2* gout;
-    grid_ptrs(a, grid, N, gin, gout);
-    const char* p = reinterpret_cast<const char*>(gin + (long long)((t % IT) >> 1) * N * N);
-    for (int c = 0; c < 4; ++c)  // the plane, 4 x 32 KB
-      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p + c * 32768),
-                   "r"(32768u)
-                   : "memory");
-  };
   auto take2 = [&]() -> int { return (int)atomicAdd(a.work, 2u); };
   int base = 0, ahead = 0;
   if (lane == 0) {
     base = take2();
     ahead = take2();
-    prefetch_pair(base);
   }
   bool second = false;
   auto next_ticket = [&]() -> int {
@@ -169,9 +156,11 @@ __device__ __forceinline__ void producer(const FusedArgs& a, const CUtensorMap* 
     const int t = base + 1;
     base = ahead;
     ahead = take2();
-    prefetch_pair(base);
     return t;
   };
+  // every item is read once: its lines may leave L2 first (the intermediate
+  // still waiting for its slabs stays)
+  const unsigned long long once = policy_evict_first();
   int ready_grid = -1;
   unsigned live = 0;
   int k = 0;
@@ -223,14 +212,15 @@ __device__ __forceinline__ void producer(const FusedArgs& a, const CUtensorMap* 
     if (d.phase == 0 && lane < 8) {
       // half-plane: plane z = idx / 2, rows y = parity + 2 m, 16 columns per box
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      tma_box(dst + lane * 8192, tin, 32 * lane, d.idx & 1, d.grid * N + (d.idx >> 1), &full[s]);
+      tma_box_hint(dst + lane * 8192, tin, 32 * lane, d.idx & 1, d.grid * N + (d.idx >> 1),
+                   &full[s], once);
     } else if (d.phase == 1 && lane < 4) {
       // slab: rows y = k2 + 64 r, columns 32 q + 16 h, every z
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("fence.proxy.async.global;" ::: "memory");
       const int r = lane >> 1, h = lane & 1, k2 = d.idx >> 2, q = d.idx & 3;
-      tma_box(dst + (r * 2 + h) * 16384, tout, 2 * (32 * q + 16 * h), k2 + 64 * r, d.grid * N,
-              &full[s]);
+      tma_box_hint(dst + (r * 2 + h) * 16384, tout, 2 * (32 * q + 16 * h), k2 + 64 * r,
+                   d.grid * N, &full[s], once);
     }
     live |= 1u << s;
   }
@@ -350,9 +340,14 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
           constexpr int k2 = decltype(K)::value;
           v[k2] = twc<k2, 128, DIR>(v[k2]);
         });
+      // the intermediate: kept in L2 until its slabs have read it
+      const unsigned long long keep = policy_evict_last();
       float2* dst = gout + (long long)(d.idx >> 1) * NN + (long long)par * H * N + c;
 #pragma unroll
-      for (int k2 = 0; k2 < H; ++k2) dst[(long long)k2 * N] = v[k2];
+      for (int k2 = 0; k2 < H; ++k2)
+        asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(dst + (long long)k2 * N),
+                     "f"(v[k2].x), "f"(v[k2].y), "l"(keep)
+                     : "memory");
     } else {
       // slab (k2, q): column x = 32 q + xl, output row y = k2 + 64 yr,
       // this thread's z points p + 2 m
