@@ -44,10 +44,11 @@ KERNEL_SOURCES = ["paper_2006_08435_gb300/csrc/persistent.cuh",
                   "paper_2006_08435_gb300/csrc/pipelined.cuh",
                   "paper_2006_08435_gb300/csrc/rowfft.cuh",
                   "paper_2006_08435_gb300/csrc/splity.cuh",
+                  "paper_2006_08435_gb300/csrc/rowfft2.cuh",
                   "paper_2006_08435_gb300/csrc/codelets.cuh",
                   "paper_2006_08435_gb300/csrc/tc_stage.cuh",
                   "paper_2006_08435_gb300/csrc/sizes.h"]
-KERNEL_NAMES = {128: "splity_fft3d_kernel<128,-1>", 64: "rowfft_fft3d_kernel<64,-1>"}
+KERNEL_NAMES = {128: "splity_fft3d_kernel<128,-1>", 64: "rowfft2_fft3d_kernel<64,-1>"}
 
 
 def dist_env():

@@ -201,9 +201,12 @@ int fft3d_selftest_wait_timeout(int64_t timeout_ns);
  * persistent kernel (32^3 .. 96^3, except 128^3), 5 the warp-owned two-phase
  * kernel (64^3, 128^3), 6 the double-buffered TMA-fed kernel with producer
  * and signaller warps (64^3), 7 the thread-per-pencil kernel (each 1D FFT in
- * one thread's registers, items loaded by swizzled tensor TMA; 64^3).
- * Variant 7 needs packed, 16-byte aligned buffers of one batch (it encodes
- * tensor maps of `in` and `out` at each execute).  Mixed plans:
+ * one thread's registers, items loaded by swizzled tensor TMA; 64^3), 8 the
+ * same with two-plane items and a register split (64^3); for 128^3, 6 is the
+ * split-y kernel (64 KB items: half-planes and quarter-slabs, 128-point
+ * FFTs by thread pairs).  The tensor-TMA variants (64^3: 7, 8; 128^3: 6)
+ * need packed, 16-byte aligned buffers of one batch (they encode tensor maps
+ * of `in` and `out` at each execute).  Mixed plans:
  * 0 one launch of the mixed-edge kernel, 1 one launch per distinct edge.
  * At create the variant comes from FFT3D_VARIANT / FFT3D_MIXED_VARIANT if
  * set, else from the tuning cache named by FFT3D_TUNE_CACHE (tuned on the

@@ -7,17 +7,20 @@
 // Variant 5: warp-owned rows/columns inside the two-phase items.
 // Variant 6: double-buffered TMA-fed blocks with producer and signaller warps.
 // Variant 7: thread-per-pencil register FFTs fed by tensor TMA.
+// Variant 8: the same with two-plane items and a register split.
 #include "cluster.cuh"
 #include "dbuf.cuh"
 #include "prefetch.cuh"
 #include "pipelined.cuh"
 #include "rowfft.cuh"
+#include "rowfft2.cuh"
 #include "warpown.cuh"
 
 namespace fft3d {
 
 KernelInfo fused_kernel_info_n64(int dir, int variant) {
   constexpr int T = fused_threads(64);
+  if (variant == 8) return dir < 0 ? rowk2::info<64, -1>() : rowk2::info<64, 1>();
   if (variant == 7) return dir < 0 ? rowk::info<64, -1>() : rowk::info<64, 1>();
   if (variant == 6) return dir < 0 ? dbuf::info<64, -1>() : dbuf::info<64, 1>();
   if (variant == 5) return dir < 0 ? wown::info<64, -1>() : wown::info<64, 1>();

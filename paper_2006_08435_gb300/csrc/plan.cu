@@ -123,7 +123,7 @@ std::vector<int> variant_candidates(bool mixed, int n, int precision) {
   switch (n) {
     case 16: return {0, 1, 3};
     case 32: return {0, 1, 3, 4};
-    case 64: return {0, 1, 2, 3, 4, 5, 6, 7};
+    case 64: return {0, 1, 2, 3, 4, 5, 6, 7, 8};
     case 128: return {0, 1, 2, 5, 6};
     default: return {0, 1, 4};  // 48, 80, 96
   }
@@ -136,7 +136,8 @@ int builtin_default_variant(bool mixed, int n, int batch, int precision) {
   if (mixed || precision != FFT3D_FP32) return 0;
   if (n == 128) return batch >= 4 ? 6 : 2;  // split-y from 4 grids, measured faster
   if ((n == 16 || n == 32) && batch >= 64) return 3;
-  if (n == 64 && batch >= 16) return 7;  // thread-per-pencil, measured faster from 16 grids
+  if (n == 64 && batch >= 128) return 8;  // two-plane items, measured faster from 128 grids
+  if (n == 64 && batch >= 16) return 7;   // thread-per-pencil, measured faster from 16 grids
   return 0;
 }
 

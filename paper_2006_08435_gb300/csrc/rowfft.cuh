@@ -24,8 +24,9 @@
 //
 // Block: four compute groups of 64 threads (each group one item at a time,
 // items k = g, g + 4, ...), one producer warp (tickets, slab dependencies,
-// tensor copies into a ring of six tiles) and one signaller warp (frees tiles,
-// publishes finished planes).  One block per SM.  Liveness and bounded waits
+// tensor copies into a ring of six tiles) and one publisher warp (publishes
+// finished planes; tiles go back to the producer straight from the compute
+// groups).  One block per SM.  Liveness and bounded waits
 // as in the double-buffered kernel: a block's started items finish without
 // the producer, so its waits for slab dependencies are waits on smaller
 // tickets only.
@@ -55,13 +56,15 @@ struct Cfg {
   static constexpr int TILE = NSEG * REGION;       // bytes of one item
   static constexpr int NTILE = 6;
   static constexpr int SCHED = 8192;               // schedule blocks kept in shared memory
+  static constexpr int DQ = 16;                    // finished items queued for the publisher
   static constexpr int GROUPS = 3;                 // compute groups of N threads
   static constexpr int GW = N / 32;                // warps per group
   static constexpr int NCW = GROUPS * GW;          // compute warps
-  static constexpr int T = 32 * (NCW + 2);         // plus producer and signaller
+  static constexpr int T = 32 * (NCW + 2);         // plus producer and publisher
   static constexpr size_t smem = 1024 + (size_t)NTILE * TILE +
-                                 (3 * NTILE + GROUPS) * sizeof(unsigned long long) +
-                                 NTILE * sizeof(int4) + SCHED * sizeof(unsigned short);
+                                 (2 * NTILE + GROUPS + DQ) * sizeof(unsigned long long) +
+                                 NTILE * sizeof(int4) + (DQ + 1) * sizeof(int) +
+                                 SCHED * sizeof(unsigned short);
 };
 
 // Byte offset of complex (row r, column c) in a tile (128-byte swizzle).
@@ -117,6 +120,21 @@ __device__ __forceinline__ Desc bcast(Desc d) {
   return d;
 }
 
+// Spin (sleeping) until *p >= target, bounded in time like the other waits.
+__device__ __forceinline__ int spin_geq(const volatile int* p, int target, const FusedArgs& a) {
+  if (*p >= target) return 1;
+  const unsigned long long t0 = global_timer_ns();
+  for (int it = 0; it < (1 << 22); ++it) {
+    __nanosleep(64);
+    if (*p >= target) return 1;
+    if ((it & 63) == 0 && ((long long)(global_timer_ns() - t0) > a.timeout_ns ||
+                           *(volatile unsigned*)a.status != kStatusOk))
+      break;
+  }
+  atomicCAS(a.status, kStatusOk, kStatusTimeout);
+  return 0;
+}
+
 // Producer warp: tickets in order into tiles k % NTILE.  Lane 0 takes and
 // resolves the tickets; lanes 0 .. NSEG-1 issue one tensor box each.
 // Tensors are viewed as [N * batch][N][2N] floats (z of all grids, y, x
@@ -130,10 +148,12 @@ __device__ __forceinline__ Desc bcast(Desc d) {
 template <int N>
 __device__ __forceinline__ void producer(const FusedArgs& a, const CUtensorMap* tin,
                                          const CUtensorMap* tout, uint32_t tiles,
-                                         unsigned long long* full, unsigned long long* freed,
-                                         Desc* desc, const unsigned short* sched) {
+                                         unsigned long long* full, unsigned long long* empty,
+                                         unsigned long long* done, int* pubq,
+                                         volatile int* pub_done, Desc* desc,
+                                         const unsigned short* sched) {
   using K = Cfg<N>;
-  constexpr int NT = K::NTILE;
+  constexpr int NT = K::NTILE, DQ = K::DQ;
   const int lane = threadIdx.x & 31;
   const bool local = a.nblocks <= K::SCHED;
   auto block_of = [&](int b, int& grid, int& phase) {
@@ -225,28 +245,39 @@ __device__ __forceinline__ void producer(const FusedArgs& a, const CUtensorMap* 
     ok = __shfl_sync(0xffffffffu, ok, 0);
     __syncwarp();  // lane 0's (or 1's) acquire before the copies of every lane
     if (!ok) {
-      // a stop for each compute group: items k .. k + GROUPS - 1 (each tile
-      // once the signaller has freed its earlier item)
       if (lane == 0) {
+        // a stop for each compute group: items k .. k + GROUPS - 1, each tile
+        // once its group is done with its earlier item
         for (int j = 0; j < K::GROUPS; ++j) {
           const int kk = k + j, sj = kk % NT;
           if (kk >= NT &&
-              !mbar_wait_bounded(&freed[sj], (kk / NT - 1) & 1, a.status, a.timeout_ns))
+              !mbar_wait_bounded(&empty[sj], (kk / NT - 1) & 1, a.status, a.timeout_ns))
             break;
           desc[sj] = Desc{-1, 0, 0, 0};
           mbar_arrive(&full[sj]);
           live &= ~(1u << sj);
         }
+        // and one for the publisher, after item k - 1
+        if (spin_geq(pub_done, k - DQ + 1, a)) {
+          pubq[k % DQ] = -2;
+          for (int j = 0; j < K::GW; ++j) mbar_arrive(&done[k % DQ]);
+        }
       }
       live = __shfl_sync(0xffffffffu, live, 0);
       break;
     }
-    if (k >= NT && !__all_sync(0xffffffffu, mbar_wait_bounded(&freed[s], (k / NT - 1) & 1,
-                                                               a.status, a.timeout_ns)))
-      break;
+    // the tile: its group is done with item k - NT; the publisher's slot of
+    // item k: item k - DQ published (rarely waited for)
+    int fr = 1;
+    if (lane == 0) {
+      if (k >= NT) fr = mbar_wait_bounded(&empty[s], (k / NT - 1) & 1, a.status, a.timeout_ns);
+      if (fr) fr = spin_geq(pub_done, k - DQ + 1, a);
+    }
+    if (!__shfl_sync(0xffffffffu, fr, 0)) break;
     live &= ~(1u << s);
     if (lane == 0) {
       desc[s] = d;
+      pubq[k % DQ] = d.phase == 0 ? d.grid : -1;  // read by the publisher after item k
       mbar_arrive_tx(&full[s], (unsigned)K::TILE);
     }
     __syncwarp();
@@ -274,29 +305,27 @@ __device__ __forceinline__ void producer(const FusedArgs& a, const CUtensorMap* 
     }
 }
 
-// Signaller warp: items in order; once the compute group is done with one,
-// frees its tile and, for a plane, publishes it to the other blocks.
+// Publisher warp (lane 0): finished items in order; a plane is published to
+// the other blocks (the GPU-scope release waits for the compute group's
+// stores, so it is kept off the compute and producer warps).  Item k's
+// completion arrives on done[k % DQ] (both warps of its group); its grid was
+// queued by the producer.  Tiles are handed back by the compute groups
+// directly, so publishing never delays a refill.
 template <int N>
-__device__ __forceinline__ void signaller(const FusedArgs& a, unsigned long long* full,
-                                          unsigned long long* empty,
-                                          unsigned long long* freed, Desc* desc) {
-  constexpr int NT = Cfg<N>::NTILE;
-  const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void publisher(const FusedArgs& a, unsigned long long* done,
+                                          const int* pubq, volatile int* pub_done) {
+  constexpr int DQ = Cfg<N>::DQ;
+  if ((threadIdx.x & 31) != 0) return;
   for (int k = 0;; ++k) {
-    const int s = k % NT;
-    const unsigned par = (k / NT) & 1;
-    if (!warp_wait(&full[s], par, a)) return;
-    const Desc d = desc[s];
-    if (d.item < 0) return;
-    if (!warp_wait(&empty[s], par, a)) return;
-    if (lane == 0) {
-      mbar_arrive(&freed[s]);
-      if (d.phase == 0) {
-        asm volatile("fence.acq_rel.gpu;" ::: "memory");
-        atomicAdd(a.work + 1 + d.grid, 1u);
-      }
+    if (!mbar_wait_bounded(&done[k % DQ], (k / DQ) & 1, a.status, a.timeout_ns)) return;
+    const int grid = pubq[k % DQ];
+    if (grid == -2) return;
+    if (grid >= 0) {
+      asm volatile("fence.acq_rel.gpu;" ::: "memory");
+      atomicAdd(a.work + 1 + grid, 1u);
     }
-    __syncwarp();
+    __threadfence_block();  // the slot is read before it is handed back
+    *pub_done = k + 1;
   }
 }
 
@@ -313,10 +342,12 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
   const uint32_t tiles = saddr(base);
   unsigned long long* full = reinterpret_cast<unsigned long long*>(base + (size_t)NT * K::TILE);
   unsigned long long* empty = full + NT;
-  unsigned long long* freed = empty + NT;
-  unsigned long long* tr = freed + NT;  // per group: rows done before columns
-  Desc* desc = reinterpret_cast<Desc*>(tr + K::GROUPS);
-  unsigned short* sched = reinterpret_cast<unsigned short*>(desc + NT);
+  unsigned long long* tr = empty + NT;  // per group: rows done before columns
+  unsigned long long* done = tr + K::GROUPS;  // items finished, for the publisher
+  Desc* desc = reinterpret_cast<Desc*>(done + K::DQ);
+  int* pubq = reinterpret_cast<int*>(desc + NT);
+  volatile int* pub_done = pubq + K::DQ;
+  unsigned short* sched = reinterpret_cast<unsigned short*>(pubq + K::DQ + 1);
   const int w = threadIdx.x >> 5;
   if (a.nblocks <= K::SCHED)
     for (int b = threadIdx.x; b < a.nblocks; b += K::T)
@@ -325,19 +356,20 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
     for (int s = 0; s < NT; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], K::GW);
-      mbar_init(&freed[s], 1);
     }
     for (int g = 0; g < K::GROUPS; ++g) mbar_init(&tr[g], K::GW);
+    for (int q = 0; q < K::DQ; ++q) mbar_init(&done[q], K::GW);
+    *pub_done = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
 
   if (w == K::NCW) {
-    producer<N>(a, &tin, &tout, tiles, full, freed, desc, sched);
+    producer<N>(a, &tin, &tout, tiles, full, empty, done, pubq, pub_done, desc, sched);
     return;
   }
   if (w == K::NCW + 1) {
-    signaller<N>(a, full, empty, freed, desc);
+    publisher<N>(a, done, pubq, pub_done);
     return;
   }
 
@@ -392,7 +424,10 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
       }
     }
     __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[s]);
+    if (lane == 0) {
+      mbar_arrive(&empty[s]);              // the tile is free
+      mbar_arrive(&done[k % K::DQ]);       // and the stores done, for the publisher
+    }
   }
 }
 

@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 FP32_TOL = 5e-6
 CASES = [(n, v) for n in (16, 32, 48, 64, 80, 96, 128) for v in (0, 1)]
 CASES += [(64, 2), (128, 2), (16, 3), (32, 3), (64, 3)]
-CASES += [(32, 4), (48, 4), (64, 4), (80, 4), (96, 4), (64, 5), (128, 5), (64, 6), (64, 7), (128, 6)]
+CASES += [(32, 4), (48, 4), (64, 4), (80, 4), (96, 4), (64, 5), (128, 5), (64, 6), (64, 7), (64, 8), (128, 6)]
 
 
 @pytest.mark.parametrize("n,variant", CASES)
@@ -39,7 +39,7 @@ def test_variant_matches_oracle(cuda, monkeypatch, n, variant):
             assert oracle.rel_l2(yc[b], ref[b]) <= FP32_TOL
 
 
-@pytest.mark.parametrize("n,variant", [(16, 3), (32, 3), (64, 3), (64, 6), (64, 7), (128, 6)])
+@pytest.mark.parametrize("n,variant", [(16, 3), (32, 3), (64, 3), (64, 6), (64, 7), (64, 8), (128, 6)])
 def test_variant_in_place_and_many_grids(cuda, monkeypatch, n, variant):
     """More grids than blocks or clusters (every block goes many times round
     its tiles or loops over grids) and in == out."""
