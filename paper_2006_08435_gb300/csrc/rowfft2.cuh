@@ -34,7 +34,9 @@ using piped::warp_wait;
 using rowk::bcast;
 using rowk::Desc;
 using rowk::spin_geq;
-using rowk::tma_box;
+using rowk::policy_evict_first;
+using rowk::policy_evict_last;
+using rowk::tma_box_hint;
 
 template <int N>
 struct Cfg {
@@ -72,8 +74,10 @@ __device__ __forceinline__ uint32_t boff(int R, int c) {
 
 // Producer warp: tickets (two at a time, two pairs ahead; each ticket one
 // item) in order into tiles k % NTILE; lanes 0 and 1 resolve the pair after
-// the current one (schedule lookup, L2 prefetch of a plane pair, probe of a
-// slab pair's dependencies); lanes 0 .. NSEG-1 issue one tensor box each.
+// the current one (schedule lookup, probe of a slab pair's dependencies);
+// lanes 0 .. NSEG-1 issue one tensor box each.  Every copy is marked
+// evict-first in L2 (each item is read once) and the planes' outputs
+// evict-last, so the intermediate stays in L2 until its slabs read it.
 template <int N>
 __device__ __forceinline__ void producer(const FusedArgs& a, const CUtensorMap* tin,
                                          const CUtensorMap* tout, uint32_t tiles,
@@ -107,15 +111,7 @@ __device__ __forceinline__ void producer(const FusedArgs& a, const CUtensorMap* 
     rd = 1;
     if (lane < 2 && t < a.total_items) {
       block_of(t / IT, grid, phase);
-      if (phase == 0) {  // the item's two planes, contiguous 64 KB
-        const float2* gin;
-        float2* gout;
-        grid_ptrs(a, grid, N, gin, gout);
-        const char* p = reinterpret_cast<const char*>(gin + (long long)(2 * (t % IT)) * N * N);
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(32768u) : "memory");
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p + 32768), "r"(32768u)
-                     : "memory");
-      } else if (grid != ready_grid) {
+      if (phase == 1 && grid != ready_grid) {
         rd = ld_acquire(a.work + 1 + grid) >= (unsigned)IT;
         if (rd) ready_grid = grid;
       }
@@ -134,6 +130,7 @@ __device__ __forceinline__ void producer(const FusedArgs& a, const CUtensorMap* 
     resolve(b1, nt, ng, nph, nrd);
   }
   unsigned live = 0;
+  const unsigned long long once = policy_evict_first();
   int k = 0;
   for (;; ++k) {
     const int s = k % NT;
@@ -193,9 +190,9 @@ __device__ __forceinline__ void producer(const FusedArgs& a, const CUtensorMap* 
       if (d.phase == 1) asm volatile("fence.proxy.async.global;" ::: "memory");
       const uint32_t dst = tiles + (uint32_t)(s * K::TILE + lane * K::REGION);
       if (d.phase == 0)  // planes 2 idx, 2 idx + 1: box {16 x, all y, 2 z}
-        tma_box(dst, tin, 2 * K::SEG * lane, 0, d.grid * N + 2 * d.idx, &full[s]);
+        tma_box_hint(dst, tin, 2 * K::SEG * lane, 0, d.grid * N + 2 * d.idx, &full[s], once);
       else  // slabs 2 idx, 2 idx + 1: box {16 x, 2 y, all z}
-        tma_box(dst, tout, 2 * K::SEG * lane, 2 * d.idx, d.grid * N, &full[s]);
+        tma_box_hint(dst, tout, 2 * K::SEG * lane, 2 * d.idx, d.grid * N, &full[s], once);
     }
     live |= 1u << s;
   }
@@ -287,8 +284,11 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
       for (int r = 0; r < N; ++r) v[r] = *reinterpret_cast<const float2*>(t + boff<N>(64 * j + r, u));
       DFT<N, DIR>::run(v);
       float2* dst = gout + (long long)(2 * d.idx + j) * NN + u;
+      const unsigned long long keep = policy_evict_last();  // until its slabs read it
 #pragma unroll
-      for (int k1 = 0; k1 < N; ++k1) dst[(long long)k1 * N] = v[k1];
+      for (int k1 = 0; k1 < N; ++k1)
+        asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(dst + (long long)k1 * N),
+                     "f"(v[k1].x), "f"(v[k1].y), "l"(keep));
     } else {
       // z: column x = u of slab y = 2 idx + j
 #pragma unroll
