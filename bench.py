@@ -38,6 +38,7 @@ WORKLOADS = {
     # smaller cases of the same kernels for ncu captures (inputs still > L2)
     "128x16": (128, 16),
     "64x64": (64, 64),
+    "64x128": (64, 128),
 }
 METRIC = "batched 3D FFT transforms/s and % of HBM roofline at 64^3/128^3 (FP32 vs split-FP16)"
 KERNEL_SOURCES = ["paper_2006_08435_gb300/csrc/persistent.cuh",
