@@ -54,3 +54,27 @@ def test_variant_in_place_and_many_grids(cuda, monkeypatch, n, variant):
     assert p.device_status() == 0
     for b in (0, batch // 2, batch - 1):
         assert oracle.rel_l2(x[b].cpu().numpy(), (b + 1) * ref0) <= FP32_TOL
+
+
+@pytest.mark.parametrize("variant", [7, 8])
+def test_tensor_kernels_schedule_beyond_shared_table(cuda, monkeypatch, variant):
+    """More schedule blocks (2 per grid) than the tensor-TMA kernels keep in
+    shared memory (8192): the producer reads the schedule from global
+    memory instead.  4100 grids of 64^3 (8.6 GB each way); three of them are
+    checked against the oracle."""
+    from paper_2006_08435_gb300 import Plan
+    monkeypatch.setenv("FFT3D_VARIANT", str(variant))
+    n, batch = 64, 4100
+    base = torch.from_numpy(synth.uniform_grids(n, 1, seed=77)).cuda()
+    x = base.repeat(batch, 1, 1, 1)
+    x.mul_(torch.arange(1, batch + 1, device="cuda", dtype=torch.float32).view(-1, 1, 1, 1))
+    y = torch.empty_like(x)
+    p = Plan(n, n, n, batch)
+    assert p.variant == variant
+    p.execute(x, y)
+    assert p.device_status() == 0
+    ref0 = oracle.dft3d(base[0].cpu().numpy().astype(np.complex128), -1)
+    for b in (0, 2049, batch - 1):
+        assert oracle.rel_l2(y[b].cpu().numpy(), (b + 1) * ref0) <= FP32_TOL
+    del x, y
+    torch.cuda.empty_cache()
