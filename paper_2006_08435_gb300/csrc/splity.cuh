@@ -86,6 +86,17 @@ __device__ __forceinline__ uint32_t soff(int r, int z, int x) {
                     ((x & 1) << 3));
 }
 
+// Shared-memory accesses by 32-bit shared-window address (not volatile, so
+// the compiler may schedule them like plain loads).
+__device__ __forceinline__ float2 lds2(uint32_t a) {
+  float2 v;
+  asm("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ void sts2(uint32_t a, float2 v) {
+  asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
+}
+
 // 128-point FFT finished by a thread pair: v holds this thread's 64-point
 // DFT of points p + 2 m.  After the twiddle and the exchange with the
 // partner (lane ^ xm), the outputs are handed over two at a time:
@@ -305,7 +316,7 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
     if (!warp_wait(&full[s], (k / NT) & 1, a)) break;
     const Desc d = desc[s];
     if (d.item < 0) break;
-    unsigned char* t = base + (size_t)s * K::TILE;
+    const uint32_t t = tiles + (uint32_t)(s * K::TILE);
     const float2* gin;
     float2* gout;
     grid_ptrs(a, d.grid, N, gin, gout);
@@ -314,17 +325,17 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
       // x: row r = gt / 2 of the tile, this thread's points p + 2 m
       const int r = gt >> 1, p = gt & 1;
 #pragma unroll
-      for (int m = 0; m < H; ++m) v[m] = *reinterpret_cast<const float2*>(t + hoff(r, p + 2 * m));
+      for (int m = 0; m < H; ++m) v[m] = lds2(t + hoff(r, p + 2 * m));
       DFT<H, DIR>::run(v);
       __syncwarp();  // both threads of the row have read it
       // write back X[c]; the odd thread stores the two of a pair in the other
       // order, so the two threads of a row never hit the same bank
       pair_radix2<DIR>(v, p, 1, [&](int j, float2 a0, float2 a1, float2 b0, float2 b1) {
         const int c0 = j + 32 * p;
-        *reinterpret_cast<float2*>(t + hoff(r, c0 + p)) = p ? a1 : a0;
-        *reinterpret_cast<float2*>(t + hoff(r, c0 + 1 - p)) = p ? a0 : a1;
-        *reinterpret_cast<float2*>(t + hoff(r, c0 + 64 + p)) = p ? b1 : b0;
-        *reinterpret_cast<float2*>(t + hoff(r, c0 + 65 - p)) = p ? b0 : b1;
+        sts2(t + hoff(r, c0 + p), p ? a1 : a0);
+        sts2(t + hoff(r, c0 + 1 - p), p ? a0 : a1);
+        sts2(t + hoff(r, c0 + 64 + p), p ? b1 : b0);
+        sts2(t + hoff(r, c0 + 65 - p), p ? b0 : b1);
       });
       __syncwarp();
       if (lane == 0) mbar_arrive(&tr[g]);
@@ -333,7 +344,7 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
       // y: column c = gt, 64-point DFT over the rows of this parity
       const int par = d.idx & 1, c = gt;
 #pragma unroll
-      for (int m = 0; m < H; ++m) v[m] = *reinterpret_cast<const float2*>(t + hoff(m, c));
+      for (int m = 0; m < H; ++m) v[m] = lds2(t + hoff(m, c));
       DFT<H, DIR>::run(v);
       if (par)  // times W_128^k2 (compile-time twiddles)
         static_for<1, H>([&](auto K) {
@@ -357,8 +368,8 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
 #pragma unroll
       for (int m = 0; m < H; ++m) {
         const int z = p + 2 * m;
-        const float2 e = *reinterpret_cast<const float2*>(t + soff(0, z, xl));
-        const float2 o = *reinterpret_cast<const float2*>(t + soff(1, z, xl));
+        const float2 e = lds2(t + soff(0, z, xl));
+        const float2 o = lds2(t + soff(1, z, xl));
         v[m] = yr ? csub(e, o) : cadd(e, o);
       }
       DFT<H, DIR>::run(v);
