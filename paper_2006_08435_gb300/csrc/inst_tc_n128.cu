@@ -4,7 +4,7 @@
 
 namespace fft3d {
 
-KernelInfo tc_kernel_info_n128(int dir, int prec) {
+KernelInfo tc_kernel_info_n128(int dir, int prec, int /*variant*/) {
   constexpr int T = fused_threads(128);
   if (dir < 0) {
     if (prec == 1) return make_fused_info_prec<T, -1, 1, 128>();

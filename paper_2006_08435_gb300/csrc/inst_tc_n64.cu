@@ -1,19 +1,26 @@
-// Tensor-core (split FP16, split BF16, FP16) persistent kernels for 64^3
-// grids: the radix-16 first step of each axis runs as mma.sync GEMMs.
+// Tensor-core (split FP16, split BF16, FP16) kernels for 64^3 grids: the
+// radix-16 step of each axis runs as mma.sync products.  Variant 0: the
+// plain persistent kernel; 8: the two-plane tensor-TMA kernel (tcrow.cuh).
 #include "persistent.cuh"
+#include "tcrow.cuh"
 
 namespace fft3d {
 
-KernelInfo tc_kernel_info_n64(int dir, int prec) {
-  constexpr int T = fused_threads(64);
+template <int DIR, int PREC>
+static KernelInfo tc_info_n64(int variant) {
+  if (variant == 8) return tcr::info<64, DIR, PREC>();
+  return make_fused_info_prec<fused_threads(64), DIR, PREC, 64>();
+}
+
+KernelInfo tc_kernel_info_n64(int dir, int prec, int variant) {
   if (dir < 0) {
-    if (prec == 1) return make_fused_info_prec<T, -1, 1, 64>();
-    if (prec == 2) return make_fused_info_prec<T, -1, 2, 64>();
-    return make_fused_info_prec<T, -1, 3, 64>();
+    if (prec == 1) return tc_info_n64<-1, 1>(variant);
+    if (prec == 2) return tc_info_n64<-1, 2>(variant);
+    return tc_info_n64<-1, 3>(variant);
   }
-  if (prec == 1) return make_fused_info_prec<T, 1, 1, 64>();
-  if (prec == 2) return make_fused_info_prec<T, 1, 2, 64>();
-  return make_fused_info_prec<T, 1, 3, 64>();
+  if (prec == 1) return tc_info_n64<1, 1>(variant);
+  if (prec == 2) return tc_info_n64<1, 2>(variant);
+  return tc_info_n64<1, 3>(variant);
 }
 
 }  // namespace fft3d

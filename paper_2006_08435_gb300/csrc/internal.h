@@ -69,7 +69,7 @@ struct KernelInfo {
 // Defined in the inst_*.cu translation units.
 KernelInfo fused_kernel_info(int n, int dir, int variant);   // single-size kernel
 KernelInfo mixed_kernel_info(int dir);          // all fused sizes
-KernelInfo tc_kernel_info(int n, int dir, int prec);  // tensor-core radix-16 kinds
+KernelInfo tc_kernel_info(int n, int dir, int prec, int variant);  // tensor-core kinds
 cudaError_t launch_wait_selftest(unsigned* flag, unsigned* status, long long timeout_ns,
                                  cudaStream_t stream);
 
@@ -86,7 +86,3 @@ int builtin_default_variant(bool mixed, int n, int batch, int precision);
 // A plan with a forced variant (plan.cu), for the autotuner.
 int fft3d_internal_create_variant(bool mixed, int nx, int batch, int precision, int direction,
                                   const int* dims, int count, int variant, fft3d_plan* out);
-
-namespace fft3d {
-
-}  // namespace fft3d

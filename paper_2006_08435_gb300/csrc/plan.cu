@@ -27,13 +27,13 @@ KernelInfo fused_kernel_info_n64(int dir, int variant);
 KernelInfo fused_kernel_info_n80(int dir, int variant);
 KernelInfo fused_kernel_info_n96(int dir, int variant);
 KernelInfo fused_kernel_info_n128(int dir, int variant);
-KernelInfo tc_kernel_info_n64(int dir, int prec);
-KernelInfo tc_kernel_info_n128(int dir, int prec);
+KernelInfo tc_kernel_info_n64(int dir, int prec, int variant);
+KernelInfo tc_kernel_info_n128(int dir, int prec, int variant);
 
-KernelInfo tc_kernel_info(int n, int dir, int prec) {
+KernelInfo tc_kernel_info(int n, int dir, int prec, int variant) {
   switch (n) {
-    case 64: return tc_kernel_info_n64(dir, prec);
-    case 128: return tc_kernel_info_n128(dir, prec);
+    case 64: return tc_kernel_info_n64(dir, prec, variant);
+    case 128: return tc_kernel_info_n128(dir, prec, variant);
     default: return KernelInfo{};
   }
 }
@@ -115,11 +115,14 @@ static bool fused_size(int n) { return fused_slot(n) >= 0; }
 // 1 the same with twice the threads, 2 the TMA-fed warp-specialised kernel
 // (64^3 and 128^3), 3 the cluster-fused single-pass kernel (16^3, 32^3,
 // 64^3), 4 the double-buffered persistent kernel (32^3 to 96^3), 5 the
-// warp-owned two-phase kernel (64^3, 128^3).  Mixed plans: 0 one launch of the mixed-edge kernel, 1 one launch
-// per distinct edge with that edge's default kernel.
+// warp-owned two-phase kernel (64^3, 128^3), 6 to 8 the tensor-TMA
+// thread-per-pencil kernels.  Tensor-core precisions: 0 the plain persistent
+// kernel, 8 (64^3) the two-plane tensor-TMA kernel.  Mixed plans: 0 one
+// launch of the mixed-edge kernel, 1 one launch per distinct edge with that
+// edge's default kernel.
 std::vector<int> variant_candidates(bool mixed, int n, int precision) {
   if (mixed) return {0, 1};
-  if (precision != FFT3D_FP32) return {0};
+  if (precision != FFT3D_FP32) return n == 64 ? std::vector<int>{0, 8} : std::vector<int>{0};
   switch (n) {
     case 16: return {0, 1, 3};
     case 32: return {0, 1, 3, 4};
@@ -133,7 +136,8 @@ std::vector<int> variant_candidates(bool mixed, int n, int precision) {
 // cluster-fused kernel for 16^3 and 32^3 batches of 64 grids or more, the
 // plain persistent kernel otherwise.
 int builtin_default_variant(bool mixed, int n, int batch, int precision) {
-  if (mixed || precision != FFT3D_FP32) return 0;
+  if (mixed) return 0;
+  if (precision != FFT3D_FP32) return n == 64 && batch >= 16 ? 8 : 0;
   if (n == 128) return batch >= 4 ? 6 : 2;  // split-y from 4 grids, measured faster
   if ((n == 16 || n == 32) && batch >= 64) return 3;
   if (n == 64 && batch >= 128) return 8;  // two-plane items, measured faster from 128 grids
@@ -454,7 +458,7 @@ int create_uniform(int nx, int ny, int nz, int batch, int precision, int directi
   set_scale(p, (double)pts);
   Unit u;
   u.kernel = precision == FFT3D_FP32 ? fused_kernel_info(nx, direction, variant)
-                                     : tc_kernel_info(nx, direction, precision);
+                                     : tc_kernel_info(nx, direction, precision, variant);
   u.grids.resize(batch);
   for (int g = 0; g < batch; ++g) u.grids[g] = g;
   p->units.push_back(u);
@@ -614,11 +618,11 @@ int fft3d_plan_host_io(fft3d_plan plan, int chunk_grids) {
   h->grids = chunk_grids;
   h->grid_bytes = sizeof(float2) * (size_t)n * n * n;
   int rc = create_uniform(n, n, n, chunk_grids, plan->precision, plan->direction, plan->norm,
-                          plan->precision == FFT3D_FP32 ? plan->variant : 0, &h->chunk);
+                          plan->variant, &h->chunk);
   const int rem = plan->batch % chunk_grids;
   if (!rc && rem)
     rc = create_uniform(n, n, n, rem, plan->precision, plan->direction, plan->norm,
-                        plan->precision == FFT3D_FP32 ? plan->variant : 0, &h->tail);
+                        plan->variant, &h->tail);
   const size_t bytes = h->grid_bytes * (size_t)chunk_grids;
   for (int b = 0; b < 2 && !rc; ++b)
     if (cudaMalloc(&h->in_buf[b], bytes) != cudaSuccess ||

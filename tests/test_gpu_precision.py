@@ -74,3 +74,69 @@ def test_precision_unsupported_size_is_refused(cuda):
     from paper_2006_08435_gb300 import Plan, FFT3DError
     with pytest.raises(FFT3DError):
         Plan(48, 48, 48, 1, precision="split_fp16")
+
+
+@pytest.mark.parametrize("variant", [0, 8])
+@pytest.mark.parametrize("inverse", [False, True])
+def test_precision_kinds_per_variant_64(cuda, monkeypatch, variant, inverse):
+    """Each 64^3 tensor-core kernel (0 plain persistent, 8 two-plane
+    tensor-TMA) for every precision kind, three grids (a ragged tail of
+    plane-pair items), forward and normalised inverse."""
+    from paper_2006_08435_gb300 import Plan
+    monkeypatch.setenv("FFT3D_VARIANT", str(variant))
+    n, batch = 64, 3
+    x = torch.from_numpy(synth.gaussian_sum_grids(n, batch, seed=11 + variant)).cuda()
+    ref = oracle.dft3d(x.cpu().numpy().astype(np.complex128), 1 if inverse else -1)
+    norm = "by_n" if inverse else "none"
+    if inverse:
+        ref /= float(n) ** 3
+    for prec, tol in (("split_fp16", SPLIT_FP16_TOL), ("split_bf16", 1e-3), ("fp16", 1e-2)):
+        p = Plan(n, n, n, batch, precision=prec, inverse=inverse, norm=norm)
+        assert p.variant == variant
+        y = torch.empty_like(x)
+        p.execute(x, y)
+        assert p.device_status() == 0
+        err = max(oracle.rel_l2(y[b].cpu().numpy(), ref[b]) for b in range(batch))
+        print(f"\nvariant {variant} {prec} inverse={inverse}: rel-L2 {err:.2e}")
+        assert err <= tol
+
+
+def test_split_fp16_two_plane_in_place_many_grids(cuda, monkeypatch):
+    """40 grids in place (every block goes several times round its tiles),
+    each a multiple of the first, so one oracle transform checks three."""
+    from paper_2006_08435_gb300 import Plan
+    monkeypatch.setenv("FFT3D_VARIANT", "8")
+    n, batch = 64, 40
+    base = torch.from_numpy(synth.gaussian_sum_grids(n, 1, seed=5)).cuda()
+    x = (base.repeat(batch, 1, 1, 1) *
+         torch.arange(1, batch + 1, device="cuda", dtype=torch.float32).view(-1, 1, 1, 1)).contiguous()
+    p = Plan(n, n, n, batch, precision="split_fp16")
+    assert p.variant == 8
+    p.execute(x, x)
+    assert p.device_status() == 0
+    ref0 = oracle.dft3d(base[0].cpu().numpy().astype(np.complex128), -1)
+    for b in (0, batch // 2, batch - 1):
+        assert oracle.rel_l2(x[b].cpu().numpy(), (b + 1) * ref0) <= SPLIT_FP16_TOL
+
+
+def test_split_fp16_two_plane_closed_forms_and_range(cuda, monkeypatch):
+    """The two-plane tensor-core kernel on a delta (all-ones result), a
+    constant (one bin), zero planes, and a round trip through values far
+    above the FP16 range."""
+    from paper_2006_08435_gb300 import fft3d
+    monkeypatch.setenv("FFT3D_VARIANT", "8")
+    n = 64
+    d = torch.zeros((1, n, n, n), dtype=torch.complex64, device="cuda")
+    d[0, 0, 0, 0] = 1.0
+    y = fft3d(d, precision="split_fp16").cpu().numpy()
+    assert np.abs(y - 1.0).max() < 1e-6
+    c = torch.full((1, n, n, n), 3.0 - 1.0j, dtype=torch.complex64, device="cuda")
+    y = fft3d(c, precision="split_fp16").cpu().numpy()
+    expect = np.zeros((1, n, n, n), np.complex128)
+    expect[0, 0, 0, 0] = (3.0 - 1.0j) * n ** 3
+    assert oracle.rel_l2(y, expect) <= SPLIT_FP16_TOL
+    x = torch.from_numpy(synth.uniform_grids(n, 1, seed=9) * 1e6 + 3e6).cuda()
+    f = fft3d(x, precision="split_fp16")
+    assert float(f.abs().max()) > 1e11
+    back = fft3d(f, inverse=True, norm="by_n", precision="split_fp16")
+    assert oracle.rel_l2(back.cpu().numpy(), x.cpu().numpy()) <= 2 * SPLIT_FP16_TOL
