@@ -109,6 +109,41 @@ static void mma_fragments(int prec, uint32_t* out /* tc::kFragWords */) {
         }
 }
 
+// B operands of the tcgen05 64^3 kernel (tcgen.cuh): for k1 = 0..3 the
+// 32 x 32 real form of M_k1[n2][k2] = W_64^(n2 (k1 + 4 k2)) (forward root;
+// the radix-16 DFT with the twiddles of the radix-4 x 16 split folded in),
+// rows and columns interleaved re/im as for mma_fragments, stored K-major
+// (row = output column 2 k2 + d, 32 input entries 2 n2 + c per row) in
+// 8 x 16-byte core matrices: byte ((row / 8) * 4 + kk / 8) * 128 +
+// (row % 8) * 16 + (kk % 8) * 2 of block (term * 4 + k1) * 2048, term 0 the
+// hi halves, 1 the lo halves (FP16, or BF16 for prec 2).
+static void umma_b_table(int prec, uint16_t* out /* 8192 */) {
+  for (int k1 = 0; k1 < 4; ++k1)
+    for (int row = 0; row < 32; ++row)
+      for (int kk = 0; kk < 32; ++kk) {
+        const int k2 = row / 2, d = row % 2, n2 = kk / 2, c = kk % 2;
+        const int m = (n2 * (k1 + 4 * k2)) % 64;
+        const double a = -2.0 * 3.14159265358979323846 * (double)m / 64.0;
+        const double wr = std::cos(a), wi = std::sin(a);
+        const double v = c == 0 ? (d == 0 ? wr : wi) : (d == 0 ? -wi : wr);
+        uint16_t hi, lo;
+        if (prec == 2) {
+          const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+          const __nv_bfloat16 l = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
+          hi = __bfloat16_as_ushort(h);
+          lo = __bfloat16_as_ushort(l);
+        } else {
+          const __half h = __float2half_rn((float)v);
+          const __half l = __float2half_rn((float)(v - (double)__half2float(h)));
+          hi = __half_as_ushort(h);
+          lo = __half_as_ushort(l);
+        }
+        const int byte = ((row / 8) * 4 + kk / 8) * 128 + (row % 8) * 16 + (kk % 8) * 2;
+        out[(0 * 4 + k1) * 1024 + byte / 2] = hi;
+        out[(1 * 4 + k1) * 1024 + byte / 2] = lo;
+      }
+}
+
 static bool fused_size(int n) { return fused_slot(n) >= 0; }
 
 // Kernel variants of a single-size FP32 plan: 0 plain persistent kernel,
@@ -117,12 +152,13 @@ static bool fused_size(int n) { return fused_slot(n) >= 0; }
 // 64^3), 4 the double-buffered persistent kernel (32^3 to 96^3), 5 the
 // warp-owned two-phase kernel (64^3, 128^3), 6 to 8 the tensor-TMA
 // thread-per-pencil kernels.  Tensor-core precisions: 0 the plain persistent
-// kernel, 8 (64^3) the two-plane tensor-TMA kernel.  Mixed plans: 0 one
+// kernel, 8 (64^3) the two-plane tensor-TMA kernel with mma.sync, 9 (64^3)
+// the same items with tcgen05 products.  Mixed plans: 0 one
 // launch of the mixed-edge kernel, 1 one launch per distinct edge with that
 // edge's default kernel.
 std::vector<int> variant_candidates(bool mixed, int n, int precision) {
   if (mixed) return {0, 1};
-  if (precision != FFT3D_FP32) return n == 64 ? std::vector<int>{0, 8} : std::vector<int>{0};
+  if (precision != FFT3D_FP32) return n == 64 ? std::vector<int>{0, 8, 9} : std::vector<int>{0};
   switch (n) {
     case 16: return {0, 1, 3};
     case 32: return {0, 1, 3, 4};
@@ -352,7 +388,13 @@ int finish_unit(fft3d_plan p, Unit& u, bool identity) {
   }
   int rc;
   if ((rc = upload(&u.d_tw, reinterpret_cast<const float2*>(tw.data()), tw.size() / 2))) return rc;
-  if (u.kernel.prec) {
+  if (u.kernel.prec && u.kernel.umma_b) {
+    std::vector<uint16_t> b(8192);
+    umma_b_table(u.kernel.prec, b.data());
+    std::vector<uint32_t> words(4096);
+    std::memcpy(words.data(), b.data(), sizeof(uint16_t) * b.size());
+    if ((rc = upload(&u.d_frag, words.data(), words.size()))) return rc;
+  } else if (u.kernel.prec) {
     std::vector<uint32_t> frag(tc::kFragWords);
     mma_fragments(u.kernel.prec, frag.data());
     if ((rc = upload(&u.d_frag, frag.data(), frag.size()))) return rc;

@@ -1,0 +1,414 @@
+// Split-precision two-plane kernel for 64^3 grids on the fifth-generation
+// tensor cores (tcgen05): the tiles, work items, producer and publisher of
+// rowfft2.cuh, one pencil per thread as in the FP32 kernel, and the
+// radix-16 stage of every axis as tcgen05.mma products with the
+// accumulators in tensor memory.
+//
+// Each 64-point transform is split as n = 16 n1 + n2, k = k1 + 4 k2:
+//     R[k1][n2] = DFT_4 over n1 (registers, the transform's direction),
+//     X[k1 + 4 k2] = sum_n2 R[k1][n2] W_64^(n2 (k1 + 4 k2))   (tensor cores),
+// the second step a 16 x 16 complex product per k1 whose matrix carries the
+// twiddles of the split (host table, FP64 rounded to hi + lo halves).  A
+// pass over the 128 pencils of an item:
+//   1. each thread loads its pencil, scales it by one power of two (its
+//      largest component to [2^12, 2^13), so |R| < 2^15), and runs the
+//      radix-4 stage;
+//   2. each thread writes its four rows (k1) of the A operands into tensor
+//      memory (lane = pencil, one 32-bit column per two K entries): hi = R
+//      rounded to a multiple of 16 by adding and subtracting 1.5 * 2^27
+//      (exact in FP16; 128 and BF16 for split BF16), lo = the exact
+//      remainder rounded once;
+//   3. after one group barrier, one thread issues, per k1, D_k1 = A_hi B_hi
+//      + A_hi B_lo + A_lo B_hi (M = 128 pencils, N = 32, K = 32: six
+//      kind::f16 products, A from tensor memory, B from shared memory, FP32
+//      accumulation in 32 tensor-memory columns) and commits them to an
+//      mbarrier;
+//   4. each thread reads its own row of D, undoes the scale and stores X
+//      (x: back into its row of the tile, 16-byte chunks; y, z: to global
+//      memory, coalesced across the warp).
+// Plain FP16 keeps only A_hi B_hi with A rounded to nearest.  The inverse
+// feeds conj(R) to the forward matrices and conjugates the result.  The
+// shared-memory traffic is the FP32 kernel's plus the small B operands; a
+// tile goes back to the producer as soon as its y or z pencils are loaded.
+//
+// Tensor memory (512 columns): group g owns columns 256 g .. 256 g + 255,
+// A_(term, k1) at + (4 term + k1) * 16 and D_k1 at + 128 + 32 k1.
+// B operands (16 KB, shared memory for the kernel's life), K-major with no
+// swizzle: 8-row x 16-byte core matrices, row r at byte r * 16, core
+// matrices 128 bytes apart along K (the leading byte offset) and 512 bytes
+// apart along N (the stride byte offset).
+#pragma once
+
+#include "tcrow.cuh"
+
+namespace fft3d {
+namespace tg {
+
+using piped::mbar_arrive;
+using piped::mbar_init;
+using piped::saddr;
+using piped::warp_wait;
+using rowk::Desc;
+using rowk::policy_evict_last;
+using rowk2::boff;
+using rowk2::Cfg;
+using tcr::lds2;
+using tcr::max3;
+using tcr::mul2;
+using tcr::sts4;
+
+constexpr int kBBytes = 2 * 4 * 2048;  // B operands: term (hi, lo) x k1 x 32 x 32 halves
+constexpr int kTmemCols = 512;         // 2 groups x (A: 8 x 16, D: 4 x 32 columns)
+
+// Shared-memory matrix descriptor: start address, leading byte offset 128
+// (next core matrix along K), stride byte offset 512 (next eight rows),
+// descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(128u >> 4) << 16) |
+         ((uint64_t)(512u >> 4) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, A and B FP16 (or
+// BF16 for PREC 2), both K-major, N = 32, M = 128.
+template <int PREC>
+constexpr uint32_t idesc() {
+  constexpr uint32_t ab = PREC == 2 ? 1u : 0u;
+  return (1u << 4) | (ab << 7) | (ab << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+// D (tensor memory) (+)= A (tensor memory) B (shared memory descriptor).
+__device__ __forceinline__ void umma(uint32_t d, uint32_t a, uint64_t b, uint32_t id, int acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+      "r"(a), "l"(b), "r"(id), "r"(acc));
+}
+
+// 8 consecutive 32-bit columns of this thread's tensor-memory lane.
+__device__ __forceinline__ void tmem_st8(uint32_t addr, const uint32_t (&r)[8]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(addr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(unsigned long long* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          saddr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void named_bar(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// Barrier over `count` threads that also ANDs their `ok`: every thread of a
+// compute group takes the same decision after a bounded wait, so none is
+// left at a later barrier that the others never reach.
+__device__ __forceinline__ int group_and(int id, int count, int ok) {
+  int r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.b32 p, %1, 0;\n bar.red.and.pred q, %2, %3, p;\n"
+      " selp.b32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"(ok), "r"(id), "r"(count)
+      : "memory");
+  return r;
+}
+
+// 32 consecutive FP32 columns of this thread's tensor-memory lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t addr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(addr));
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Largest |component| of the 64 points.
+__device__ __forceinline__ float absmax64(const float2 (&v)[64]) {
+  float m[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+  for (int i = 0; i < 64; i += 4)
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+      m[p * 2] = max3(m[p * 2], fabsf(v[i + 2 * p].x), fabsf(v[i + 2 * p].y)),
+      m[p * 2 + 1] = max3(m[p * 2 + 1], fabsf(v[i + 2 * p + 1].x), fabsf(v[i + 2 * p + 1].y));
+  return fmaxf(max3(m[0], m[1], m[2]), m[3]);
+}
+
+// Group state of the tensor-core passes.
+struct Pass {
+  uint32_t bsm;            // shared address of the B operands
+  uint32_t col;            // tensor-memory address of the group's first column
+  uint32_t lanes;          // this warp's lane quarter (in the address's high half)
+  unsigned long long* bar; // the group's product-completion mbarrier
+  int g, gt;
+};
+
+// One tensor-core pass over the pencils of the group's tile: v holds this
+// thread's pencil (natural order); store(kp, k2, y0, y1) receives output
+// points 2 kp + 4 k2 and 2 kp + 1 + 4 k2, multiplied by out_scale.
+// Returns false if a wait gave up (the status word is set).
+template <int DIR, int PREC, class Store>
+__device__ __forceinline__ bool pass(float2 (&v)[64], const Pass& P, unsigned& phase,
+                                     const FusedArgs& a, float out_scale, Store store) {
+  const float m = absmax64(v);
+  const int ex = m > 0.0f ? tc::exponent_of(m) : 0;
+  const float sc = tc::pow2(12 - ex);
+  const float cj = DIR > 0 ? -1.0f : 1.0f;
+  // radix-4 over n1: v[16 k1 + n2] = R[k1][n2]
+#pragma unroll
+  for (int n2 = 0; n2 < 16; ++n2) {
+    float2 q[4] = {v[n2], v[16 + n2], v[32 + n2], v[48 + n2]};
+    tcr::dft4<DIR>(q);
+    v[n2] = q[0];
+    v[16 + n2] = q[1];
+    v[32 + n2] = q[2];
+    v[48 + n2] = q[3];
+  }
+  // A rows: lane gt of matrix (term, k1), column n2 = (re, im) of point n2
+  const float2 s2 = make_float2(sc, cj * sc);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      uint32_t h[8], l[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) tcr::split<PREC>(v[16 * k1 + 8 * e + i], s2, h[i], l[i]);
+      tmem_st8(P.col + P.lanes + 16 * k1 + 8 * e, h);
+      if constexpr (PREC != 3) tmem_st8(P.col + P.lanes + 16 * (4 + k1) + 8 * e, l);
+    }
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+  tc_fence_before();
+  named_bar(1 + P.g, Cfg<64>::GT);  // every A row is written, every D row read
+  if (P.gt == 0) {
+    tc_fence_after();
+    constexpr uint32_t id = idesc<PREC>();
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      const uint32_t d = P.col + 128 + 32 * k1;
+      const uint32_t ahi = P.col + 16 * k1, alo = P.col + 16 * (4 + k1);
+      const uint32_t bhi = P.bsm + k1 * 2048, blo = P.bsm + (4 + k1) * 2048;
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks) umma(d, ahi + 8 * ks, sdesc(bhi + 256 * ks), id, ks);
+      if constexpr (PREC != 3) {
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) umma(d, ahi + 8 * ks, sdesc(blo + 256 * ks), id, 1);
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) umma(d, alo + 8 * ks, sdesc(bhi + 256 * ks), id, 1);
+      }
+    }
+    umma_commit(P.bar);
+  }
+  if (!group_and(1 + P.g, Cfg<64>::GT, warp_wait(P.bar, phase & 1, a))) return false;
+  ++phase;
+  tc_fence_after();
+  const float inv = tc::pow2(ex - 12) * out_scale;
+  const float2 o = make_float2(inv, cj * inv);
+#pragma unroll
+  for (int kp = 0; kp < 2; ++kp) {
+    float d0[32], d1[32];
+    tmem_ld32(P.col + P.lanes + 128 + 32 * (2 * kp), d0);
+    tmem_ld32(P.col + P.lanes + 128 + 32 * (2 * kp + 1), d1);
+    tmem_wait_ld();
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2)
+      store(kp, k2, mul2(make_float2(d0[2 * k2], d0[2 * k2 + 1]), o),
+            mul2(make_float2(d1[2 * k2], d1[2 * k2 + 1]), o));
+  }
+  tc_fence_before();  // these reads precede the group's next products
+  return true;
+}
+
+template <int N>
+constexpr size_t kSmem = Cfg<N>::smem + 128 + kBBytes + 2 * sizeof(unsigned long long) + 16;
+
+template <int N, int DIR, int PREC>
+__global__ void __launch_bounds__(Cfg<N>::T, 1)
+    tcgen_fft3d_kernel(const FusedArgs a, const __grid_constant__ CUtensorMap tin,
+                       const __grid_constant__ CUtensorMap tout) {
+  using K = Cfg<N>;
+  static_assert(N == 64 && K::GT == 128, "one pencil per thread of a 128-thread group");
+  constexpr int NT = K::NTILE;
+  constexpr long long NN = (long long)N * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* base = smem_raw + ((1024 - (saddr(smem_raw) & 1023)) & 1023);
+  const uint32_t tiles = saddr(base);
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(base + (size_t)NT * K::TILE);
+  unsigned long long* empty = full + NT;
+  unsigned long long* tr = empty + NT;
+  unsigned long long* done = tr + K::GROUPS;
+  Desc* desc = reinterpret_cast<Desc*>(done + K::DQ);
+  int* pubq = reinterpret_cast<int*>(desc + NT);
+  volatile int* pub_done = pubq + K::DQ;
+  unsigned short* sched = reinterpret_cast<unsigned short*>(pubq + K::DQ + 1);
+  unsigned char* bsm_p = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(sched + K::SCHED) + 127) & ~(uintptr_t)127);
+  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(bsm_p + kBBytes);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+  const int w = threadIdx.x >> 5;
+  if (a.nblocks <= K::SCHED)
+    for (int b = threadIdx.x; b < a.nblocks; b += K::T)
+      sched[b] = (unsigned short)(a.blocks[b].grid * 2 + a.blocks[b].phase);
+  for (int i = threadIdx.x; i < kBBytes / 16; i += K::T)
+    reinterpret_cast<uint4*>(bsm_p)[i] = reinterpret_cast<const uint4*>(a.mma_frag)[i];
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NT; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], K::GW);
+    }
+    for (int g = 0; g < K::GROUPS; ++g) mbar_init(&tr[g], K::GW);
+    for (int q = 0; q < K::DQ; ++q) mbar_init(&done[q], K::GW);
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    *pub_done = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (w == 4) {  // the first compute warp owns the tensor-memory allocation
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     saddr(tslot)),
+                 "n"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // B operands, for the tensor cores
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+
+  if (w < 4) {  // control warpgroup
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(K::REG_CTRL));
+    if (w == 0)
+      rowk2::producer<N>(a, &tin, &tout, tiles, full, empty, done, pubq, pub_done, desc, sched);
+    if (w == 1) rowk::publisher<N>(a, done, pubq, pub_done);
+    return;
+  }
+  asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(K::REG_COMP));
+
+  // compute group g (warpgroup g + 1), thread gt of 128: pencil gt of a pass
+  const int g = (w - 4) / K::GW, gt = threadIdx.x - 128 - g * K::GT, lane = threadIdx.x & 31;
+  const int j = gt >> 6, u = gt & (N - 1);
+  Pass P;
+  P.bsm = saddr(bsm_p);
+  P.col = *tslot + (uint32_t)(256 * g);
+  P.lanes = (uint32_t)(32 * (gt >> 5)) << 16;
+  P.bar = &mbar[g];
+  P.g = g;
+  P.gt = gt;
+  unsigned phase = 0;  // completed product batches of this group
+  for (int k = g;; k += K::GROUPS) {
+    const int s = k % NT;
+    if (!group_and(1 + g, K::GT, warp_wait(&full[s], (k / NT) & 1, a))) break;
+    const Desc d = desc[s];
+    if (d.item < 0) break;
+    const uint32_t tl = tiles + (uint32_t)(s * K::TILE);
+    const float2* gin;
+    float2* gout;
+    grid_ptrs(a, d.grid, N, gin, gout);
+    float2 v[N];
+    if (d.phase == 0) {
+      // x: row gt of the pair (row y = u of plane j), 16-byte chunks
+#pragma unroll
+      for (int i = 0; i < N / 2; ++i) {
+        const float4 q = *reinterpret_cast<const float4*>(base + (size_t)s * K::TILE + boff<N>(gt, 2 * i));
+        v[2 * i] = make_float2(q.x, q.y);
+        v[2 * i + 1] = make_float2(q.z, q.w);
+      }
+      if (!pass<DIR, PREC>(v, P, phase, a, 1.0f, [&](int kp, int k2, float2 y0, float2 y1) {
+            sts4(tl + boff<N>(gt, 2 * kp + 4 * k2), y0, y1);
+          }))
+        break;
+      named_bar(1 + g, K::GT);  // the x results are in the tile
+      // y: column x = u of plane j, output rows straight to global memory
+#pragma unroll
+      for (int r = 0; r < N; ++r) v[r] = lds2(tl + boff<N>(64 * j + r, u));
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);  // the tile is read: back to the producer
+      float2* dst = gout + (long long)(2 * d.idx + j) * NN + u;
+      const unsigned long long keep = policy_evict_last();  // until its slabs read it
+      if (!pass<DIR, PREC>(v, P, phase, a, 1.0f, [&](int kp, int k2, float2 y0, float2 y1) {
+            float2* p = dst + (long long)(2 * kp + 4 * k2) * N;
+            asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p),
+                         "f"(y0.x), "f"(y0.y), "l"(keep));
+            asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p + N),
+                         "f"(y1.x), "f"(y1.y), "l"(keep));
+          }))
+        break;
+    } else {
+      // z: column x = u of slab y = 2 idx + j
+#pragma unroll
+      for (int z = 0; z < N; ++z) v[z] = lds2(tl + boff<N>(2 * z + j, u));
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);  // the tile is read: back to the producer
+      float2* dst = gout + (long long)(2 * d.idx + j) * N + u;
+      if (!pass<DIR, PREC>(v, P, phase, a, a.do_scale ? a.scale : 1.0f,
+                           [&](int kp, int k2, float2 y0, float2 y1) {
+                             float2* p = dst + (long long)(2 * kp + 4 * k2) * NN;
+                             st_stream(p, y0);
+                             st_stream(p + NN, y1);
+                           }))
+        break;
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&done[k % K::DQ]);  // the stores are done, for the publisher
+  }
+  // every compute warp is out of its loop: no product or tensor-memory read
+  // is in flight
+  tc_fence_before();
+  named_bar(3, 2 * K::GT);
+  tc_fence_after();
+  if (w == 4)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tslot),
+                 "n"(kTmemCols));
+}
+
+// Uniform batches only (packed buffers, grids in plan order).
+template <int N, int DIR, int PREC>
+cudaError_t launch(const FusedArgs& a, int grid, cudaStream_t stream) {
+  if (a.in_ptrs || a.grid_map || a.grid_off || !a.mma_frag) return cudaErrorInvalidValue;
+  CUtensorMap tin, tout;
+  if (!rowk::encode_map(&tin, a.in, N, a.ngrids, N, 2) ||
+      !rowk::encode_map(&tout, a.out, N, a.ngrids, 2, N))
+    return cudaErrorInvalidValue;
+  tcgen_fft3d_kernel<N, DIR, PREC><<<grid, Cfg<N>::T, kSmem<N>, stream>>>(a, tin, tout);
+  return cudaGetLastError();
+}
+
+template <int N, int DIR, int PREC>
+KernelInfo info() {
+  KernelInfo k;
+  k.launch = &launch<N, DIR, PREC>;
+  k.func = (const void*)&tcgen_fft3d_kernel<N, DIR, PREC>;
+  k.threads = Cfg<N>::T;
+  k.smem = kSmem<N>;
+  k.twiddle_entries = N;  // (the B operands carry the twiddles; a table is uploaded anyway)
+  k.tw_l1 = 4;
+  k.sizes[0] = N;
+  k.nsizes = 1;
+  k.items_in_flight = Cfg<N>::NTILE + 4;
+  k.phase_items = Cfg<N>::ITEMS;
+  k.prec = PREC;
+  k.umma_b = 1;
+  return k;
+}
+
+}  // namespace tg
+}  // namespace fft3d

@@ -5,21 +5,25 @@
 // One warp transforms 16 pencils at a time.  Lane (g, t) = (lane / 4,
 // lane % 4) holds pencils g and g + 8 of the set, points t + 4 q (q < 4) of
 // each length-16 vector, as the mma.m16n8k16 A fragment wants them
-// (tc_stage.cuh).  The four vectors of a pencil (n1 = 0..3) go through four
-// products with the same DFT_16 matrix, so the radix-4 stage over n1 stays
-// inside the thread and the twiddles are per-lane registers:
+// (tc_stage.cuh).  Each pencil is split as n = 16 n1 + n2, k = k1 + 4 k2
+// (decimation in frequency):
+//     Z[k1][n2] = DFT_4 over n1 (registers),  Z *= W_64^(n2 k1),
+//     X[k1 + 4 k2] = DFT_16 over n2 (tensor cores),
+// so the radix-4 stage stays inside the thread, and the four vectors of a
+// pencil (k1 = 0..3) go through four products with the same DFT_16 matrix,
+// whose B fragments stay in registers.
 //
-//   DIT (x and y):  n = n1 + 4 n2, k = k2 + 16 k1
-//     Y[n1][k2] = DFT_16 over n2 (tensor cores),  Y *= W_64^(n1 k2),
-//     X[k2 + 16 k1] = DFT_4 over n1.
-//   DIF (z):        n = 16 n1 + n2, k = k1 + 4 k2
-//     Z[k1][n2] = DFT_4 over n1,  Z *= W_64^(n2 k1),
-//     X[k1 + 4 k2] = DFT_16 over n2 (tensor cores).
-//
-// The two orders are chosen for shared-memory banks: with the tile's
-// 128-byte swizzle, DIT rows, DIT columns of a plane pair and DIF columns of
-// a slab pair are read (and DIT rows written) at the minimum number of
-// wavefronts.
+// The pencil-to-lane maps are chosen for shared-memory banks.  With the
+// tile's 128-byte swizzle an 8-byte access of a half-warp (16-byte access
+// of a quarter-warp) meets no conflict when its lanes hit distinct
+// (16-byte slot, half) pairs of the 128-byte row pattern:
+//   x rows: lane group gl takes row rho(gl) of each eight, rho =
+//     0 3 4 7 1 2 5 6, so that the rows of a half-warp differ in the slot
+//     bits that the points' 8-byte loads and the k1-pairs' 16-byte stores
+//     leave free;
+//   y columns: columns whose bits 3 and 0 differ within a half-warp (the
+//     points t of a lane quad fill the slot's low bits);
+//   z columns of a slab: consecutive columns.
 //
 // Operands: each pencil is scaled by one power of two so that its largest
 // component (after the radix-4 stage for DIF) stays below 2^15, then split
@@ -70,13 +74,10 @@ __device__ __forceinline__ float2 lds2(uint32_t a) {
   asm("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
   return v;
 }
-__device__ __forceinline__ float4 lds4(uint32_t a) {
-  float4 v;
-  asm("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
-  return v;
-}
-__device__ __forceinline__ void sts2(uint32_t a, float2 v) {
-  asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
+__device__ __forceinline__ void sts4(uint32_t a, float2 v, float2 w) {
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(w.x),
+               "f"(w.y)
+               : "memory");
 }
 
 __device__ __forceinline__ float max3(float a, float b, float c) {
@@ -156,21 +157,27 @@ __device__ __forceinline__ void split(float2 x, float2 s, uint32_t& hi, uint32_t
 }
 
 // acc[u] = 16 vectors x DFT_16, output points 4 u + t (tc_stage.cuh layout).
+// The four n-tiles are innermost, so consecutive products are independent.
 template <int PREC>
 __device__ __forceinline__ void dft16_mma(const Frag& b, const uint32_t (&ah)[2][4],
                                           const uint32_t (&al)[2][4], float (&acc)[4][4]) {
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
+  for (int u = 0; u < 4; ++u)
 #pragma unroll
     for (int i = 0; i < 4; ++i) acc[u][i] = 0.0f;
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      tc::mma<PREC>(acc[u], ah[s], b.h[s][u][0], b.h[s][u][1]);
-      if constexpr (PREC != 3) {
-        tc::mma<PREC>(acc[u], ah[s], b.l[s][u][0], b.l[s][u][1]);
-        tc::mma<PREC>(acc[u], al[s], b.h[s][u][0], b.h[s][u][1]);
-      }
-    }
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) tc::mma<PREC>(acc[u], ah[s], b.h[s][u][0], b.h[s][u][1]);
+  if constexpr (PREC != 3) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) tc::mma<PREC>(acc[u], ah[s], b.l[s][u][0], b.l[s][u][1]);
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) tc::mma<PREC>(acc[u], al[s], b.h[s][u][0], b.h[s][u][1]);
   }
 }
 
@@ -185,70 +192,26 @@ __device__ __forceinline__ void dft4(float2 (&v)[4]) {
   v[3] = csub(b, d);
 }
 
-// The per-lane twiddles W_64^(a (4 b + t)), a = 1..3, b = 0..3 (forward).
+// The per-lane twiddles W_64^(a (4 b + t)), a = 1..3, b = 0..3 (forward),
+// read from the shared copy of the table tw[k2 * 4 + n1] = W_64^(n1 k2)
+// at the start of each set.
 struct Tw {
   float2 w[3][4];
 };
 
-__device__ __forceinline__ void load_tw(const float2* __restrict__ table, Tw& tw) {
+__device__ __forceinline__ void load_tw(uint32_t table, Tw& tw) {
   const int t = threadIdx.x & 3;
 #pragma unroll
   for (int a = 1; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) tw.w[a - 1][b] = table[(4 * b + t) * 4 + a];
+    for (int b = 0; b < 4; ++b) tw.w[a - 1][b] = lds2(table + (uint32_t)((4 * b + t) * 4 + a) * 8u);
 }
 
-// DIT set: load(r, q, v) fills v[n1] = point n1 + 4 (t + 4 q) of pencil r;
-// store(r, u, k1, y) takes output point 4 u + t + 16 k1.
+// One set of 16 pencils: load(r, q, n1) returns point 16 n1 + t + 4 q of
+// pencil r; store(r, u, kp, y0, y1) takes output points k1 + 4 (4 u + t)
+// for k1 = 2 kp, 2 kp + 1, already multiplied by `out_scale`.
 template <int DIR, int PREC, class Load, class Store>
-__device__ __forceinline__ void dit_set(const Frag& b, const Tw& tw, Load load, Store store) {
-  float2 x[2][4][4];  // [r][q][n1]
-#pragma unroll
-  for (int r = 0; r < 2; ++r)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) load(r, q, x[r][q]);
-  float sc[2], inv[2];
-#pragma unroll
-  for (int r = 0; r < 2; ++r) pencil_scale<14>(absmax16(x[r]), sc[r], inv[r]);
-  const float cj = DIR > 0 ? -1.0f : 1.0f;  // the inverse runs on the conjugate
-  float2 y[2][4][4];  // [r][u][n1]: point k2 = 4 u + t of vector n1
-#pragma unroll
-  for (int n1 = 0; n1 < 4; ++n1) {
-    uint32_t ah[2][4], al[2][4];
-#pragma unroll
-    for (int s = 0; s < 2; ++s)
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int r = i & 1, q = 2 * s + (i >> 1);
-        split<PREC>(x[r][q][n1], make_float2(sc[r], cj * sc[r]), ah[s][i], al[s][i]);
-      }
-    float acc[4][4];
-    dft16_mma<PREC>(b, ah, al, acc);
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      y[0][u][n1] = make_float2(acc[u][0], acc[u][1]);
-      y[1][u][n1] = make_float2(acc[u][2], acc[u][3]);
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < 2; ++r) {
-    const float2 o = make_float2(inv[r], cj * inv[r]);
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-#pragma unroll
-      for (int n1 = 1; n1 < 4; ++n1) y[r][u][n1] = cmul_tw<-1>(y[r][u][n1], tw.w[n1 - 1][u]);
-      dft4<-1>(y[r][u]);
-#pragma unroll
-      for (int k1 = 0; k1 < 4; ++k1) store(r, u, k1, mul2(y[r][u][k1], o));
-    }
-  }
-}
-
-// DIF set: load(r, q, n1) returns point 16 n1 + t + 4 q of pencil r;
-// store(r, u, k1, y) takes output point k1 + 4 (4 u + t), y already
-// multiplied by `out_scale`.
-template <int DIR, int PREC, class Load, class Store>
-__device__ __forceinline__ void dif_set(const Frag& b, const Tw& tw, float out_scale, Load load,
+__device__ __forceinline__ void dif_set(const Frag& b, uint32_t twtab, float out_scale, Load load,
                                         Store store) {
   float2 x[2][4][4];  // [r][q][n1], then [r][q][k1]
 #pragma unroll
@@ -262,6 +225,8 @@ __device__ __forceinline__ void dif_set(const Frag& b, const Tw& tw, float out_s
   for (int r = 0; r < 2; ++r) pencil_scale<11>(absmax16(x[r]), sc[r], inv[r]);
   // radix-4 in the transform's own direction and twiddles W^(DIR n2 k1);
   // the tensor-core stage then runs forward on the conjugate (inverse)
+  Tw tw;
+  load_tw(twtab, tw);
 #pragma unroll
   for (int r = 0; r < 2; ++r)
 #pragma unroll
@@ -272,26 +237,34 @@ __device__ __forceinline__ void dif_set(const Frag& b, const Tw& tw, float out_s
     }
   const float cj = DIR > 0 ? -1.0f : 1.0f;
 #pragma unroll
-  for (int k1 = 0; k1 < 4; ++k1) {
-    uint32_t ah[2][4], al[2][4];
+  for (int kp = 0; kp < 2; ++kp) {
+    float acc[2][4][4];
 #pragma unroll
-    for (int s = 0; s < 2; ++s)
+    for (int e = 0; e < 2; ++e) {
+      uint32_t ah[2][4], al[2][4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int r = i & 1, q = 2 * s + (i >> 1);
-        split<PREC>(x[r][q][k1], make_float2(sc[r], cj * sc[r]), ah[s][i], al[s][i]);
-      }
-    float acc[4][4];
-    dft16_mma<PREC>(b, ah, al, acc);
+      for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int r = i & 1, q = 2 * s + (i >> 1);
+          split<PREC>(x[r][q][2 * kp + e], make_float2(sc[r], cj * sc[r]), ah[s][i], al[s][i]);
+        }
+      dft16_mma<PREC>(b, ah, al, acc[e]);
+    }
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
       const float2 o = make_float2(inv[r] * out_scale, cj * inv[r] * out_scale);
 #pragma unroll
       for (int u = 0; u < 4; ++u)
-        store(r, u, k1, mul2(make_float2(acc[u][2 * r], acc[u][2 * r + 1]), o));
+        store(r, u, kp, mul2(make_float2(acc[0][u][2 * r], acc[0][u][2 * r + 1]), o),
+              mul2(make_float2(acc[1][u][2 * r], acc[1][u][2 * r + 1]), o));
     }
   }
 }
+
+// The two-plane kernel's shared memory plus the twiddle table.
+template <int N>
+constexpr size_t kSmem = Cfg<N>::smem + 16 + N * sizeof(float2);
 
 template <int N, int DIR, int PREC>
 __global__ void __launch_bounds__(Cfg<N>::T, 1)
@@ -311,10 +284,13 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
   int* pubq = reinterpret_cast<int*>(desc + NT);
   volatile int* pub_done = pubq + K::DQ;
   unsigned short* sched = reinterpret_cast<unsigned short*>(pubq + K::DQ + 1);
+  float2* twt = reinterpret_cast<float2*>(
+      (reinterpret_cast<uintptr_t>(sched + K::SCHED) + 15) & ~(uintptr_t)15);
   const int w = threadIdx.x >> 5;
   if (a.nblocks <= K::SCHED)
     for (int b = threadIdx.x; b < a.nblocks; b += K::T)
       sched[b] = (unsigned short)(a.blocks[b].grid * 2 + a.blocks[b].phase);
+  if (threadIdx.x < N) twt[threadIdx.x] = a.twiddles[threadIdx.x];
   if (threadIdx.x == 0) {
     for (int s = 0; s < NT; ++s) {
       mbar_init(&full[s], 1);
@@ -341,8 +317,7 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
   const int gl = lane >> 2, t = lane & 3;
   Frag fb;
   load_frag<PREC>(a.mma_frag, fb);
-  Tw tw;
-  load_tw(a.twiddles, tw);
+  const uint32_t tw = saddr(twt);
   unsigned pairs = 0;  // plane-pair items of this group (parity of its barrier)
   for (int k = g;; k += K::GROUPS) {
     const int s = k % NT;
@@ -354,47 +329,42 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
     float2* gout;
     grid_ptrs(a, d.grid, N, gin, gout);
     if (d.phase == 0) {
-      // x: rows R = 32 wl + 16 h + gl + 8 r of the pair (R = 64 j + y)
+      // x: rows R = 32 wl + 16 h + rho(gl) + 8 r of the pair (R = 64 j + y)
+      const int rho = (4 * ((gl >> 1) & 1) + 3 * (gl & 1)) ^ (gl >> 2);
 #pragma unroll 1
       for (int h = 0; h < 2; ++h) {
-        const int R0 = 32 * wl + 16 * h + gl;
-        dit_set<DIR, PREC>(
-            fb, tw,
-            [&](int r, int q, float2(&v)[4]) {
-              const int R = R0 + 8 * r, c = 4 * t + 16 * q;
-              const float4 p0 = lds4(tl + boff<N>(R, c));
-              const float4 p1 = lds4(tl + boff<N>(R, c + 2));
-              v[0] = make_float2(p0.x, p0.y);
-              v[1] = make_float2(p0.z, p0.w);
-              v[2] = make_float2(p1.x, p1.y);
-              v[3] = make_float2(p1.z, p1.w);
-            },
-            [&](int r, int u, int k1, float2 y) {
-              sts2(tl + boff<N>(R0 + 8 * r, 4 * u + t + 16 * k1), y);
+        const int R0 = 32 * wl + 16 * h + rho;
+        dif_set<DIR, PREC>(
+            fb, tw, 1.0f,
+            [&](int r, int q, int n1) { return lds2(tl + boff<N>(R0 + 8 * r, 16 * n1 + t + 4 * q)); },
+            [&](int r, int u, int kp, float2 y0, float2 y1) {
+              sts4(tl + boff<N>(R0 + 8 * r, 2 * kp + 16 * u + 4 * t), y0, y1);
             });
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&tr[g]);
       if (!warp_wait(&tr[g], pairs & 1, a)) break;
       ++pairs;
-      // y: columns c of plane j = wl / 2, c = 32 (wl % 2) + 16 h + gl + 8 r
+      // y: columns c of plane j = wl / 2, c = 32 (wl % 2) + 16 h + gamma(gl)
+      // + 2 r, gamma = 0 1 8 9 4 5 12 13
       const int j = wl >> 1;
       float2* dst = gout + (long long)(2 * d.idx + j) * NN;
       const unsigned long long keep = policy_evict_last();  // until its slabs read it
+      const int gamma = (gl & 1) + 8 * ((gl >> 1) & 1) + 4 * (gl >> 2);
 #pragma unroll 1
       for (int h = 0; h < 2; ++h) {
-        const int c0 = 32 * (wl & 1) + 16 * h + gl;
-        dit_set<DIR, PREC>(
-            fb, tw,
-            [&](int r, int q, float2(&v)[4]) {
-#pragma unroll
-              for (int n1 = 0; n1 < 4; ++n1)
-                v[n1] = lds2(tl + boff<N>(64 * j + n1 + 4 * t + 16 * q, c0 + 8 * r));
+        const int c0 = 32 * (wl & 1) + 16 * h + gamma;
+        dif_set<DIR, PREC>(
+            fb, tw, 1.0f,
+            [&](int r, int q, int n1) {
+              return lds2(tl + boff<N>(64 * j + 16 * n1 + t + 4 * q, c0 + 2 * r));
             },
-            [&](int r, int u, int k1, float2 y) {
-              float2* p = dst + (long long)(4 * u + t + 16 * k1) * N + c0 + 8 * r;
+            [&](int r, int u, int kp, float2 y0, float2 y1) {
+              float2* p = dst + (long long)(2 * kp + 16 * u + 4 * t) * N + c0 + 2 * r;
               asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p),
-                           "f"(y.x), "f"(y.y), "l"(keep));
+                           "f"(y0.x), "f"(y0.y), "l"(keep));
+              asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p + N),
+                           "f"(y1.x), "f"(y1.y), "l"(keep));
             });
       }
     } else {
@@ -410,8 +380,10 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
             [&](int r, int q, int n1) {
               return lds2(tl + boff<N>(2 * (16 * n1 + t + 4 * q) + j, c0 + 8 * r));
             },
-            [&](int r, int u, int k1, float2 y) {
-              st_stream(dst + (long long)(k1 + 16 * u + 4 * t) * NN + c0 + 8 * r, y);
+            [&](int r, int u, int kp, float2 y0, float2 y1) {
+              float2* p = dst + (long long)(2 * kp + 16 * u + 4 * t) * NN + c0 + 8 * r;
+              st_stream(p, y0);
+              st_stream(p + NN, y1);
             });
       }
     }
@@ -431,7 +403,7 @@ cudaError_t launch(const FusedArgs& a, int grid, cudaStream_t stream) {
   if (!rowk::encode_map(&tin, a.in, N, a.ngrids, N, 2) ||
       !rowk::encode_map(&tout, a.out, N, a.ngrids, 2, N))
     return cudaErrorInvalidValue;
-  tcrow_fft3d_kernel<N, DIR, PREC><<<grid, Cfg<N>::T, Cfg<N>::smem, stream>>>(a, tin, tout);
+  tcrow_fft3d_kernel<N, DIR, PREC><<<grid, Cfg<N>::T, kSmem<N>, stream>>>(a, tin, tout);
   return cudaGetLastError();
 }
 
@@ -441,7 +413,7 @@ KernelInfo info() {
   k.launch = &launch<N, DIR, PREC>;
   k.func = (const void*)&tcrow_fft3d_kernel<N, DIR, PREC>;
   k.threads = Cfg<N>::T;
-  k.smem = Cfg<N>::smem;
+  k.smem = kSmem<N>;
   k.twiddle_entries = N;  // W_64^(n1 k2), n1 < 4, k2 < 16
   k.tw_l1 = 4;
   k.sizes[0] = N;
