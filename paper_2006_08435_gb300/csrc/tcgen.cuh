@@ -18,11 +18,11 @@
 //      rounded to a multiple of 16 by adding and subtracting 1.5 * 2^27
 //      (exact in FP16; 128 and BF16 for split BF16), lo = the exact
 //      remainder rounded once;
-//   3. after one group barrier, one thread issues, per k1, D_k1 = A_hi B_hi
-//      + A_hi B_lo + A_lo B_hi (M = 128 pencils, N = 32, K = 32: six
+//   3. after one group barrier, one thread of warp k1 issues D_k1 = A_hi
+//      B_hi + A_hi B_lo + A_lo B_hi (M = 128 pencils, N = 32, K = 32: six
 //      kind::f16 products, A from tensor memory, B from shared memory, FP32
-//      accumulation in 32 tensor-memory columns) and commits them to an
-//      mbarrier;
+//      accumulation in 32 tensor-memory columns) and commits them to the
+//      group's mbarrier (four arrivals);
 //   4. each thread reads its own row of D, undoes the scale and stores X
 //      (x: back into its row of the tile, 16-byte chunks; y, z: to global
 //      memory, coalesced across the warp).
@@ -200,11 +200,14 @@ __device__ __forceinline__ bool pass(float2 (&v)[64], const Pass& P, unsigned& p
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
   tc_fence_before();
   named_bar(1 + P.g, Cfg<64>::GT);  // every A row is written, every D row read
-  if (P.gt == 0) {
+  if ((P.gt & 31) == 0) {
+    // warp k1 of the group issues the products of k1: four issuing threads
+    // keep the tensor cores busier than one (each instruction costs its
+    // issuing thread some tens of cycles)
     tc_fence_after();
     constexpr uint32_t id = idesc<PREC>();
-#pragma unroll
-    for (int k1 = 0; k1 < 4; ++k1) {
+    {
+      const int k1 = P.gt >> 5;
       const uint32_t d = P.col + 128 + 32 * k1;
       const uint32_t ahi = P.col + 16 * k1, alo = P.col + 16 * (4 + k1);
       const uint32_t bhi = P.bsm + k1 * 2048, blo = P.bsm + (4 + k1) * 2048;
@@ -278,8 +281,8 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
     }
     for (int g = 0; g < K::GROUPS; ++g) mbar_init(&tr[g], K::GW);
     for (int q = 0; q < K::DQ; ++q) mbar_init(&done[q], K::GW);
-    mbar_init(&mbar[0], 1);
-    mbar_init(&mbar[1], 1);
+    mbar_init(&mbar[0], 4);  // one commit per issuing warp of the group
+    mbar_init(&mbar[1], 4);
     *pub_done = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
