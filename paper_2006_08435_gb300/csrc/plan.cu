@@ -173,7 +173,10 @@ std::vector<int> variant_candidates(bool mixed, int n, int precision) {
 // plain persistent kernel otherwise.
 int builtin_default_variant(bool mixed, int n, int batch, int precision) {
   if (mixed) return 0;
-  if (precision != FFT3D_FP32) return n == 64 && batch >= 16 ? 8 : 0;
+  // tensor-core precisions: the tcgen05 two-plane kernel at 64^3 (measured
+  // 0.50 of the HBM roofline at 256 grids against 0.40 for mma.sync and
+  // 0.24 for the plain persistent kernel)
+  if (precision != FFT3D_FP32) return n == 64 && batch >= 16 ? 9 : 0;
   if (n == 128) return batch >= 4 ? 6 : 2;  // split-y from 4 grids, measured faster
   if ((n == 16 || n == 32) && batch >= 64) return 3;
   if (n == 64 && batch >= 128) return 8;  // two-plane items, measured faster from 128 grids

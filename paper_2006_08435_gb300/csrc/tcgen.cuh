@@ -227,17 +227,16 @@ __device__ __forceinline__ bool pass(float2 (&v)[64], const Pass& P, unsigned& p
   tc_fence_after();
   const float inv = tc::pow2(ex - 12) * out_scale;
   const float2 o = make_float2(inv, cj * inv);
+  float dk[4][32];  // the four D rows of this pencil, read before one wait
 #pragma unroll
-  for (int kp = 0; kp < 2; ++kp) {
-    float d0[32], d1[32];
-    tmem_ld32(P.col + P.lanes + 128 + 32 * (2 * kp), d0);
-    tmem_ld32(P.col + P.lanes + 128 + 32 * (2 * kp + 1), d1);
-    tmem_wait_ld();
+  for (int k1 = 0; k1 < 4; ++k1) tmem_ld32(P.col + P.lanes + 128 + 32 * k1, dk[k1]);
+  tmem_wait_ld();
+#pragma unroll
+  for (int kp = 0; kp < 2; ++kp)
 #pragma unroll
     for (int k2 = 0; k2 < 16; ++k2)
-      store(kp, k2, mul2(make_float2(d0[2 * k2], d0[2 * k2 + 1]), o),
-            mul2(make_float2(d1[2 * k2], d1[2 * k2 + 1]), o));
-  }
+      store(kp, k2, mul2(make_float2(dk[2 * kp][2 * k2], dk[2 * kp][2 * k2 + 1]), o),
+            mul2(make_float2(dk[2 * kp + 1][2 * k2], dk[2 * kp + 1][2 * k2 + 1]), o));
   tc_fence_before();  // these reads precede the group's next products
   return true;
 }
