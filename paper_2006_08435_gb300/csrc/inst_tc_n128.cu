@@ -1,19 +1,27 @@
-// Tensor-core (split FP16, split BF16, FP16) persistent kernels for 128^3
-// grids: the radix-16 first step of each axis runs as mma.sync GEMMs.
+// Tensor-core (split FP16, split BF16, FP16) kernels for 128^3 grids: the
+// radix-16 step of each 64-point DFT runs on the tensor cores.  Variant 0:
+// the plain persistent kernel (mma.sync); 9: the split-y items with tcgen05
+// products (tcsplity.cuh).
 #include "persistent.cuh"
+#include "tcsplity.cuh"
 
 namespace fft3d {
 
-KernelInfo tc_kernel_info_n128(int dir, int prec, int /*variant*/) {
-  constexpr int T = fused_threads(128);
+template <int DIR, int PREC>
+static KernelInfo tc_info_n128(int variant) {
+  if (variant == 9) return tsy::info<128, DIR, PREC>();
+  return make_fused_info_prec<fused_threads(128), DIR, PREC, 128>();
+}
+
+KernelInfo tc_kernel_info_n128(int dir, int prec, int variant) {
   if (dir < 0) {
-    if (prec == 1) return make_fused_info_prec<T, -1, 1, 128>();
-    if (prec == 2) return make_fused_info_prec<T, -1, 2, 128>();
-    return make_fused_info_prec<T, -1, 3, 128>();
+    if (prec == 1) return tc_info_n128<-1, 1>(variant);
+    if (prec == 2) return tc_info_n128<-1, 2>(variant);
+    return tc_info_n128<-1, 3>(variant);
   }
-  if (prec == 1) return make_fused_info_prec<T, 1, 1, 128>();
-  if (prec == 2) return make_fused_info_prec<T, 1, 2, 128>();
-  return make_fused_info_prec<T, 1, 3, 128>();
+  if (prec == 1) return tc_info_n128<1, 1>(variant);
+  if (prec == 2) return tc_info_n128<1, 2>(variant);
+  return tc_info_n128<1, 3>(variant);
 }
 
 }  // namespace fft3d

@@ -152,13 +152,13 @@ static bool fused_size(int n) { return fused_slot(n) >= 0; }
 // 64^3), 4 the double-buffered persistent kernel (32^3 to 96^3), 5 the
 // warp-owned two-phase kernel (64^3, 128^3), 6 to 8 the tensor-TMA
 // thread-per-pencil kernels.  Tensor-core precisions: 0 the plain persistent
-// kernel, 8 (64^3) the two-plane tensor-TMA kernel with mma.sync, 9 (64^3)
-// the same items with tcgen05 products.  Mixed plans: 0 one
+// kernel, 8 (64^3) the two-plane tensor-TMA kernel with mma.sync, 9 the
+// tensor-TMA items with tcgen05 products (64^3 two-plane, 128^3 split-y).  Mixed plans: 0 one
 // launch of the mixed-edge kernel, 1 one launch per distinct edge with that
 // edge's default kernel.
 std::vector<int> variant_candidates(bool mixed, int n, int precision) {
   if (mixed) return {0, 1};
-  if (precision != FFT3D_FP32) return n == 64 ? std::vector<int>{0, 8, 9} : std::vector<int>{0};
+  if (precision != FFT3D_FP32) return n == 64 ? std::vector<int>{0, 8, 9} : std::vector<int>{0, 9};
   switch (n) {
     case 16: return {0, 1, 3};
     case 32: return {0, 1, 3, 4};
@@ -173,10 +173,10 @@ std::vector<int> variant_candidates(bool mixed, int n, int precision) {
 // plain persistent kernel otherwise.
 int builtin_default_variant(bool mixed, int n, int batch, int precision) {
   if (mixed) return 0;
-  // tensor-core precisions: the tcgen05 two-plane kernel at 64^3 (measured
-  // 0.50 of the HBM roofline at 256 grids against 0.40 for mma.sync and
-  // 0.24 for the plain persistent kernel)
-  if (precision != FFT3D_FP32) return n == 64 && batch >= 16 ? 9 : 0;
+  // tensor-core precisions: the tcgen05 kernels (measured 0.50 of the HBM
+  // roofline at 64^3 x 256 against 0.40 for mma.sync and 0.24 for the plain
+  // persistent kernel; 0.37 at 128^3 x 32 against 0.20)
+  if (precision != FFT3D_FP32) return (n == 64 && batch >= 16) || (n == 128 && batch >= 4) ? 9 : 0;
   if (n == 128) return batch >= 4 ? 6 : 2;  // split-y from 4 grids, measured faster
   if ((n == 16 || n == 32) && batch >= 64) return 3;
   if (n == 64 && batch >= 128) return 8;  // two-plane items, measured faster from 128 grids

@@ -168,3 +168,30 @@ def test_tcgen05_kernel_all_kinds(cuda, monkeypatch, n_grids):
             err = max(oracle.rel_l2(y[b].cpu().numpy(), (b + 1) * ref) for b in check)
             print(f"\ntcgen05 {prec} grids={n_grids} inverse={inverse}: rel-L2 {err:.2e}")
             assert err <= tol
+
+
+@pytest.mark.parametrize("n_grids", [1, 5])
+def test_tcgen05_128_kernel_all_kinds(cuda, monkeypatch, n_grids):
+    """The tcgen05 split-y 128^3 kernel (variant 9) for every precision kind,
+    forward and normalised inverse, in place; grids are multiples of the
+    first, so one oracle transform checks them."""
+    from paper_2006_08435_gb300 import Plan
+    monkeypatch.setenv("FFT3D_VARIANT", "9")
+    n = 128
+    base = torch.from_numpy(synth.gaussian_sum_grids(n, 1, seed=23)).cuda()
+    x = (base.repeat(n_grids, 1, 1, 1) *
+         torch.arange(1, n_grids + 1, device="cuda", dtype=torch.float32).view(-1, 1, 1, 1)).contiguous()
+    ref0 = {s: oracle.dft3d(base[0].cpu().numpy().astype(np.complex128), s) for s in (-1, 1)}
+    check = sorted({0, n_grids - 1})
+    for prec, tol in (("split_fp16", SPLIT_FP16_TOL), ("split_bf16", 1e-3), ("fp16", 1e-2)):
+        for inverse in (False, True):
+            p = Plan(n, n, n, n_grids, precision=prec, inverse=inverse,
+                     norm="by_n" if inverse else "none")
+            assert p.variant == 9
+            y = x.clone()
+            p.execute(y, y)
+            assert p.device_status() == 0
+            ref = ref0[1] / float(n) ** 3 if inverse else ref0[-1]
+            err = max(oracle.rel_l2(y[b].cpu().numpy(), (b + 1) * ref) for b in check)
+            print(f"\ntcgen05 128^3 {prec} grids={n_grids} inverse={inverse}: rel-L2 {err:.2e}")
+            assert err <= tol
