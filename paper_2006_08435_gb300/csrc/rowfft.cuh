@@ -74,6 +74,23 @@ __device__ __forceinline__ uint32_t eoff(int r, int c) {
                     ((c & 1) << 3));
 }
 
+// Full barriers of a ring of NT tiles that G compute groups take in turn
+// (item k: tile k % NT, group k % G; NT and G coprime).  One barrier per
+// (group, tile): the consecutive phases of each are the uses by one group.
+// With one barrier per tile the uses alternate between the groups, and a
+// group that reaches its next use of a tile while the other group's load
+// into it is still pending would match its own previous phase (same parity)
+// and take a stale tile.
+template <int NT, int G>
+__device__ __forceinline__ int full_idx(int k) {
+  static_assert(G == 2 && NT % 2 == 1, "coprime ring and group counts");
+  return (k % G) * NT + k % NT;
+}
+template <int NT, int G>
+__device__ __forceinline__ unsigned full_par(int k) {
+  return (unsigned)(k / (NT * G)) & 1u;
+}
+
 // L2 eviction policies (fraction 1.0 of the accessed lines).
 __device__ __forceinline__ unsigned long long policy_evict_first() {
   unsigned long long p;

@@ -58,8 +58,9 @@ struct Cfg {
   static constexpr int ITEMS = N / 2;           // items per phase of a grid
   static constexpr int SCHED = 8192;
   static constexpr int DQ = 16;                 // finished items queued for the publisher
+  static constexpr int NFULL = NTILE * GROUPS;  // full barriers, one per (group, tile)
   static constexpr size_t smem = 1024 + (size_t)NTILE * TILE +
-                                 (2 * NTILE + GROUPS + DQ) * sizeof(unsigned long long) +
+                                 (NFULL + NTILE + GROUPS + DQ) * sizeof(unsigned long long) +
                                  NTILE * sizeof(int4) + (DQ + 1) * sizeof(int) +
                                  SCHED * sizeof(unsigned short);
 };
@@ -161,7 +162,7 @@ __device__ __forceinline__ void producer(const FusedArgs& a, const CUtensorMap* 
               !mbar_wait_bounded(&empty[sj], (kk / NT - 1) & 1, a.status, a.timeout_ns))
             break;
           desc[sj] = Desc{-1, 0, 0, 0};
-          mbar_arrive(&full[sj]);
+          mbar_arrive(&full[rowk::full_idx<NT, K::GROUPS>(kk)]);
           live &= ~(1u << sj);
         }
         if (spin_geq(pub_done, k - DQ + 1, a)) {
@@ -179,10 +180,11 @@ __device__ __forceinline__ void producer(const FusedArgs& a, const CUtensorMap* 
     }
     if (!__shfl_sync(0xffffffffu, fr, 0)) break;
     live &= ~(1u << s);
+    unsigned long long* fb = &full[rowk::full_idx<NT, K::GROUPS>(k)];
     if (lane == 0) {
       desc[s] = d;
       pubq[k % DQ] = d.phase == 0 ? d.grid : -1;
-      mbar_arrive_tx(&full[s], (unsigned)K::TILE);
+      mbar_arrive_tx(fb, (unsigned)K::TILE);
     }
     __syncwarp();
     if (lane < K::NSEG) {
@@ -190,9 +192,9 @@ __device__ __forceinline__ void producer(const FusedArgs& a, const CUtensorMap* 
       if (d.phase == 1) asm volatile("fence.proxy.async.global;" ::: "memory");
       const uint32_t dst = tiles + (uint32_t)(s * K::TILE + lane * K::REGION);
       if (d.phase == 0)  // planes 2 idx, 2 idx + 1: box {16 x, all y, 2 z}
-        tma_box_hint(dst, tin, 2 * K::SEG * lane, 0, d.grid * N + 2 * d.idx, &full[s], once);
+        tma_box_hint(dst, tin, 2 * K::SEG * lane, 0, d.grid * N + 2 * d.idx, fb, once);
       else  // slabs 2 idx, 2 idx + 1: box {16 x, 2 y, all z}
-        tma_box_hint(dst, tout, 2 * K::SEG * lane, 2 * d.idx, d.grid * N, &full[s], once);
+        tma_box_hint(dst, tout, 2 * K::SEG * lane, 2 * d.idx, d.grid * N, fb, once);
     }
     live |= 1u << s;
   }
@@ -200,7 +202,8 @@ __device__ __forceinline__ void producer(const FusedArgs& a, const CUtensorMap* 
     for (int j = 1; j <= NT; ++j) {
       const int kk = k - j;
       if (kk >= 0 && (live & (1u << (kk % NT))))
-        mbar_wait_bounded(&full[kk % NT], (kk / NT) & 1, a.status, a.timeout_ns);
+        mbar_wait_bounded(&full[rowk::full_idx<NT, K::GROUPS>(kk)],
+                          rowk::full_par<NT, K::GROUPS>(kk), a.status, a.timeout_ns);
     }
 }
 
@@ -215,7 +218,7 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
   unsigned char* base = smem_raw + ((1024 - (saddr(smem_raw) & 1023)) & 1023);
   const uint32_t tiles = saddr(base);
   unsigned long long* full = reinterpret_cast<unsigned long long*>(base + (size_t)NT * K::TILE);
-  unsigned long long* empty = full + NT;
+  unsigned long long* empty = full + K::NFULL;
   unsigned long long* tr = empty + NT;
   unsigned long long* done = tr + K::GROUPS;
   Desc* desc = reinterpret_cast<Desc*>(done + K::DQ);
@@ -227,10 +230,8 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
     for (int b = threadIdx.x; b < a.nblocks; b += K::T)
       sched[b] = (unsigned short)(a.blocks[b].grid * 2 + a.blocks[b].phase);
   if (threadIdx.x == 0) {
-    for (int s = 0; s < NT; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], K::GW);
-    }
+    for (int i = 0; i < K::NFULL; ++i) mbar_init(&full[i], 1);
+    for (int s = 0; s < NT; ++s) mbar_init(&empty[s], K::GW);
     for (int g = 0; g < K::GROUPS; ++g) mbar_init(&tr[g], K::GW);
     for (int q = 0; q < K::DQ; ++q) mbar_init(&done[q], K::GW);
     *pub_done = 0;
@@ -253,7 +254,8 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
   unsigned pairs = 0;  // plane-pair items of this group (parity of its barrier)
   for (int k = g;; k += K::GROUPS) {
     const int s = k % NT;
-    if (!warp_wait(&full[s], (k / NT) & 1, a)) break;
+    if (!warp_wait(&full[rowk::full_idx<NT, K::GROUPS>(k)], rowk::full_par<NT, K::GROUPS>(k), a))
+      break;
     const Desc d = desc[s];
     if (d.item < 0) break;
     unsigned char* t = base + (size_t)s * K::TILE;

@@ -70,8 +70,10 @@ struct Cfg {
   static constexpr int REG_LAUNCH = 168, REG_CTRL = 48, REG_COMP = 224;
   static constexpr int ITEMS = 2 * N;           // items per phase of a grid
   static constexpr int SCHED = 8192;            // schedule blocks kept in shared memory
+  static constexpr int NFULL = NTILE * GROUPS;  // full barriers, one per (group, tile)
+  // barriers: full (NFULL), empty, freed (NTILE each), tr (GROUPS)
   static constexpr size_t smem = 1024 + (size_t)NTILE * TILE +
-                                 (2 * NTILE + GROUPS) * sizeof(unsigned long long) +
+                                 (NFULL + 2 * NTILE + GROUPS) * sizeof(unsigned long long) +
                                  NTILE * sizeof(int4) + SCHED * sizeof(unsigned short);
 };
 
@@ -203,7 +205,7 @@ __device__ __forceinline__ void producer(const FusedArgs& a, const CUtensorMap* 
               !mbar_wait_bounded(&freed[sj], (kk / NT - 1) & 1, a.status, a.timeout_ns))
             break;
           desc[sj] = Desc{-1, 0, 0, 0};
-          mbar_arrive(&full[sj]);
+          mbar_arrive(&full[rowk::full_idx<NT, K::GROUPS>(kk)]);
           live &= ~(1u << sj);
         }
       live = __shfl_sync(0xffffffffu, live, 0);
@@ -214,24 +216,25 @@ __device__ __forceinline__ void producer(const FusedArgs& a, const CUtensorMap* 
                                                                a.status, a.timeout_ns)))
       break;
     live &= ~(1u << s);
+    unsigned long long* fb = &full[rowk::full_idx<NT, K::GROUPS>(k)];
     if (lane == 0) {
       desc[s] = d;
-      mbar_arrive_tx(&full[s], (unsigned)K::TILE);
+      mbar_arrive_tx(fb, (unsigned)K::TILE);
     }
     __syncwarp();
     const uint32_t dst = tiles + (uint32_t)(s * K::TILE);
     if (d.phase == 0 && lane < 8) {
       // half-plane: plane z = idx / 2, rows y = parity + 2 m, 16 columns per box
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      tma_box_hint(dst + lane * 8192, tin, 32 * lane, d.idx & 1, d.grid * N + (d.idx >> 1),
-                   &full[s], once);
+      tma_box_hint(dst + lane * 8192, tin, 32 * lane, d.idx & 1, d.grid * N + (d.idx >> 1), fb,
+                   once);
     } else if (d.phase == 1 && lane < 4) {
       // slab: rows y = k2 + 64 r, columns 32 q + 16 h, every z
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("fence.proxy.async.global;" ::: "memory");
       const int r = lane >> 1, h = lane & 1, k2 = d.idx >> 2, q = d.idx & 3;
       tma_box_hint(dst + (r * 2 + h) * 16384, tout, 2 * (32 * q + 16 * h), k2 + 64 * r,
-                   d.grid * N, &full[s], once);
+                   d.grid * N, fb, once);
     }
     live |= 1u << s;
   }
@@ -239,7 +242,8 @@ __device__ __forceinline__ void producer(const FusedArgs& a, const CUtensorMap* 
     for (int j = 1; j <= NT; ++j) {
       const int kk = k - j;
       if (kk >= 0 && (live & (1u << (kk % NT))))
-        mbar_wait_bounded(&full[kk % NT], (kk / NT) & 1, a.status, a.timeout_ns);
+        mbar_wait_bounded(&full[rowk::full_idx<NT, Cfg<N>::GROUPS>(kk)],
+                          rowk::full_par<NT, Cfg<N>::GROUPS>(kk), a.status, a.timeout_ns);
     }
 }
 
@@ -254,7 +258,9 @@ __device__ __forceinline__ void signaller(const FusedArgs& a, unsigned long long
   for (int k = 0;; ++k) {
     const int s = k % NT;
     const unsigned par = (k / NT) & 1;
-    if (!warp_wait(&full[s], par, a)) return;
+    if (!warp_wait(&full[rowk::full_idx<NT, Cfg<N>::GROUPS>(k)],
+                   rowk::full_par<NT, Cfg<N>::GROUPS>(k), a))
+      return;
     const Desc d = desc[s];
     if (d.item < 0) return;
     if (!warp_wait(&empty[s], par, a)) return;
@@ -280,7 +286,7 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
   unsigned char* base = smem_raw + ((1024 - (saddr(smem_raw) & 1023)) & 1023);
   const uint32_t tiles = saddr(base);
   unsigned long long* full = reinterpret_cast<unsigned long long*>(base + (size_t)NT * K::TILE);
-  unsigned long long* empty = full + NT;
+  unsigned long long* empty = full + K::NFULL;
   unsigned long long* freed = empty + NT;
   unsigned long long* tr = freed + NT;  // per group: x done before y
   Desc* desc = reinterpret_cast<Desc*>(tr + K::GROUPS);
@@ -290,8 +296,8 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
     for (int b = threadIdx.x; b < a.nblocks; b += K::T)
       sched[b] = (unsigned short)(a.blocks[b].grid * 2 + a.blocks[b].phase);
   if (threadIdx.x == 0) {
+    for (int i = 0; i < K::NFULL; ++i) mbar_init(&full[i], 1);
     for (int s = 0; s < NT; ++s) {
-      mbar_init(&full[s], 1);
       mbar_init(&empty[s], K::GW);
       mbar_init(&freed[s], 1);
     }
@@ -313,7 +319,8 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
   unsigned halves = 0;  // half-plane items of this group (parity of its barrier)
   for (int k = g;; k += K::GROUPS) {
     const int s = k % NT;
-    if (!warp_wait(&full[s], (k / NT) & 1, a)) break;
+    if (!warp_wait(&full[rowk::full_idx<NT, K::GROUPS>(k)], rowk::full_par<NT, K::GROUPS>(k), a))
+      break;
     const Desc d = desc[s];
     if (d.item < 0) break;
     const uint32_t t = tiles + (uint32_t)(s * K::TILE);

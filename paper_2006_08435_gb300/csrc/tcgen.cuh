@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
   unsigned char* base = smem_raw + ((1024 - (saddr(smem_raw) & 1023)) & 1023);
   const uint32_t tiles = saddr(base);
   unsigned long long* full = reinterpret_cast<unsigned long long*>(base + (size_t)NT * K::TILE);
-  unsigned long long* empty = full + NT;
+  unsigned long long* empty = full + K::NFULL;
   unsigned long long* tr = empty + NT;
   unsigned long long* done = tr + K::GROUPS;
   Desc* desc = reinterpret_cast<Desc*>(done + K::DQ);
@@ -274,10 +274,8 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
   for (int i = threadIdx.x; i < kBBytes / 16; i += K::T)
     reinterpret_cast<uint4*>(bsm_p)[i] = reinterpret_cast<const uint4*>(a.mma_frag)[i];
   if (threadIdx.x == 0) {
-    for (int s = 0; s < NT; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], K::GW);
-    }
+    for (int i = 0; i < K::NFULL; ++i) mbar_init(&full[i], 1);
+    for (int s = 0; s < NT; ++s) mbar_init(&empty[s], K::GW);
     for (int g = 0; g < K::GROUPS; ++g) mbar_init(&tr[g], K::GW);
     for (int q = 0; q < K::DQ; ++q) mbar_init(&done[q], K::GW);
     mbar_init(&mbar[0], 4);  // one commit per issuing warp of the group
@@ -318,7 +316,10 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
   unsigned phase = 0;  // completed product batches of this group
   for (int k = g;; k += K::GROUPS) {
     const int s = k % NT;
-    if (!group_and(1 + g, K::GT, warp_wait(&full[s], (k / NT) & 1, a))) break;
+    if (!group_and(1 + g, K::GT,
+                   warp_wait(&full[rowk::full_idx<NT, K::GROUPS>(k)],
+                             rowk::full_par<NT, K::GROUPS>(k), a)))
+      break;
     const Desc d = desc[s];
     if (d.item < 0) break;
     const uint32_t tl = tiles + (uint32_t)(s * K::TILE);
