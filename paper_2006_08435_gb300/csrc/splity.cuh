@@ -100,35 +100,34 @@ __device__ __forceinline__ void sts2(uint32_t a, float2 v) {
 }
 
 // 128-point FFT finished by a thread pair: v holds this thread's 64-point
-// DFT of points p + 2 m.  After the twiddle and the exchange with the
-// partner (lane ^ xm), the outputs are handed over two at a time:
-// store(j, X[j + 32 p], X[j + 1 + 32 p], X[j + 32 p + 64], X[j + 33 + 32 p + 32])
-// for even j < 32, i.e. store(j, a0, a1, b0, b1) with a_u = X[j + u + 32 p]
-// and b_u = X[j + u + 32 p + 64].
+// DFT (E for p = 0, O for p = 1) of points p + 2 m.  Thread p produces
+// X[k] = E[k] + W_128^k O[k] and X[k + 64] = E[k] - W_128^k O[k] for
+// k = j + 32 p, j < 32: it keeps its own half k in [32 p, 32 p + 32) and
+// receives the partner's values of that half (lane ^ xm), so that both
+// threads multiply by the same compile-time W_128^j; the odd thread then
+// applies W_128^32 = DIR i.  The outputs are handed over two at a time:
+// store(j, a0, a1, b0, b1) with a_u = X[j + u + 32 p] and
+// b_u = X[j + u + 32 p + 64], for even j < 32.
 template <int DIR, class Store>
 __device__ __forceinline__ void pair_radix2(float2* v, int p, int xm, Store store) {
-  // times W_128^(p k): compile-time twiddles, selected by the thread's parity
-  static_for<1, 64>([&](auto K) {
-    constexpr int k = decltype(K)::value;
-    const float2 t = twc<k, 128, DIR>(v[k]);
-    v[k] = p ? t : v[k];
-  });
-#pragma unroll
-  for (int j = 0; j < 32; j += 2) {
+  static_for<0, 16>([&](auto J) {
+    constexpr int j = 2 * decltype(J)::value;
     float2 av[2], bv[2];
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const float2 send = p ? v[j + u] : v[32 + j + u];
+    static_for<0, 2>([&](auto U) {
+      constexpr int jj = j + decltype(U)::value;
+      const float2 send = p ? v[jj] : v[32 + jj];
       float2 recv;
       recv.x = __shfl_xor_sync(0xffffffffu, send.x, xm);
       recv.y = __shfl_xor_sync(0xffffffffu, send.y, xm);
-      const float2 mine = p ? v[32 + j + u] : v[j + u];  // this thread's k2 = j + u + 32 p
-      const float2 e = p ? recv : mine, o = p ? mine : recv;
-      av[u] = cadd(e, o);
-      bv[u] = csub(e, o);
-    }
+      const float2 mine = p ? v[32 + jj] : v[jj];  // this thread's k = jj + 32 p
+      const float2 e = p ? recv : mine;
+      const float2 t = twc<jj, 128, DIR>(p ? mine : recv);  // W_128^jj O[k]
+      const float2 o = p ? mul_i<DIR>(t) : t;              // times W_128^(32 p)
+      av[decltype(U)::value] = cadd(e, o);
+      bv[decltype(U)::value] = csub(e, o);
+    });
     store(j, av[0], av[1], bv[0], bv[1]);
-  }
+  });
 }
 
 // ------------------------------------------------------------- producer
