@@ -371,12 +371,13 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
       const int wl = w - 4 - g * K::GW;  // warp within the group
       const int p = lane >> 4, xl = (wl & 1) * 16 + (lane & 15), yr = wl >> 1;
       const int k2 = d.idx >> 2, q = d.idx & 3;
+      const float sg = yr ? -1.0f : 1.0f;  // the y radix-2: E + O or E - O
 #pragma unroll
       for (int m = 0; m < H; ++m) {
         const int z = p + 2 * m;
         const float2 e = lds2(t + soff(0, z, xl));
         const float2 o = lds2(t + soff(1, z, xl));
-        v[m] = yr ? csub(e, o) : cadd(e, o);
+        v[m] = fma2(o, make_float2(sg, sg), e);
       }
       DFT<H, DIR>::run(v);
       float2* dst = gout + (long long)(k2 + H * yr) * N + 32 * q + xl;

@@ -54,7 +54,6 @@ using rowk2::boff;
 using rowk2::Cfg;
 using tcr::lds2;
 using tcr::max3;
-using tcr::mul2;
 using tcr::sts4;
 
 constexpr int kBBytes = 2 * 4 * 2048;  // B operands: term (hi, lo) x k1 x 32 x 32 halves

@@ -50,24 +50,6 @@ using rowk::policy_evict_last;
 using rowk2::boff;
 using rowk2::Cfg;
 
-#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000) && !defined(FFT3D_NO_F32X2)
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
-  unsigned long long r;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(pack2(a)), "l"(pack2(b)), "l"(pack2(c)));
-  return unpack2(r);
-}
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
-  unsigned long long r;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pack2(a)), "l"(pack2(b)));
-  return unpack2(r);
-}
-#else
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
-  return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
-}
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return make_float2(a.x * b.x, a.y * b.y); }
-#endif
-
 // Shared-memory accesses by 32-bit shared-window address.
 __device__ __forceinline__ float2 lds2(uint32_t a) {
   float2 v;
