@@ -206,7 +206,13 @@ int fft3d_selftest_wait_timeout(int64_t timeout_ns);
  * split-y kernel (64 KB items: half-planes and quarter-slabs, 128-point
  * FFTs by thread pairs).  The tensor-TMA variants (64^3: 7, 8; 128^3: 6)
  * need packed, 16-byte aligned buffers of one batch (they encode tensor maps
- * of `in` and `out` at each execute).  Mixed plans:
+ * of `in` and `out` at each execute).  Tensor-core precision plans (64^3,
+ * 128^3): 0 the plain persistent kernel (mma.sync radix-16 stage), 8 the
+ * two-plane tensor-TMA kernel with mma.sync products (64^3), 9 the
+ * tensor-TMA items with tcgen05 products, operands and accumulators in
+ * tensor memory (64^3 two-plane, 128^3 split-y; all of a multiprocessor's
+ * tensor memory, one block per multiprocessor); 8 and 9 have the same buffer
+ * requirements as the tensor-TMA FP32 variants.  Mixed plans:
  * 0 one launch of the mixed-edge kernel, 1 one launch per distinct edge.
  * At create the variant comes from FFT3D_VARIANT / FFT3D_MIXED_VARIANT if
  * set, else from the tuning cache named by FFT3D_TUNE_CACHE (tuned on the
