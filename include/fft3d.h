@@ -97,6 +97,23 @@ int fft3d_size_supported(int n);
 int fft3d_twiddle_table(int n, float* out, int* l1, int* l2);
 
 /*
+ * Host-only view of the B operands of the tcgen05 tensor-core kernels
+ * (variant 9; needs no GPU).  For k1 = 0..3, the 32 x 32 real form of the
+ * complex 16 x 16 matrix M_k1[n2][k2] = W_64^(n2 (k1 + 4 k2)) (forward root,
+ * the radix-16 stage of a 64-point DFT split n = 16 n1 + n2, k = k1 + 4 k2,
+ * with the split's twiddles folded in): entry (kk = 2 n2 + c, nn = 2 k2 + d)
+ * is Re w for (c, d) = (0, 0) and (1, 1), Im w for (0, 1), -Im w for (1, 0),
+ * w = M_k1[n2][k2].  Halfword ((term * 4 + k1) * 2048 + ((nn / 8) * 4 +
+ * kk / 8) * 128 + (nn % 8) * 16 + (kk % 8) * 2) / 2 of `out` holds term 0
+ * hi = rn(b) and term 1 lo = rn(b - hi) of entry b, each rounded once from
+ * its FP64 value to FP16 (precision FFT3D_SPLIT_FP16 or FFT3D_FP16) or BF16
+ * (FFT3D_SPLIT_BF16).  `out` holds 8192 halfwords.  Errors:
+ * FFT3D_ERR_NULL_PTR, FFT3D_ERR_INVALID_ARG (precision FFT3D_FP32 or out of
+ * range).
+ */
+int fft3d_tc_operand_table(int precision, uint16_t* out);
+
+/*
  * Plan `batch` grids of nx*ny*nz points (Eq. 1 per grid).
  *   nx, ny, nz : edge lengths, each fft3d_size_supported.
  *   batch      : number of grids, >= 1, packed back to back.

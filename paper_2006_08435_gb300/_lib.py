@@ -34,6 +34,7 @@ _I = ctypes.c_int
 _SIGS = {
     "fft3d_size_supported": (_I, [_I]),
     "fft3d_twiddle_table": (_I, [_I, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "fft3d_tc_operand_table": (_I, [_I, ctypes.POINTER(ctypes.c_uint16)]),
     "fft3d_plan_create": (_I, [_I, _I, _I, _I, _I, _I, _I, ctypes.POINTER(_VP)]),
     "fft3d_plan_create_mixed": (_I, [_I, ctypes.POINTER(_I), _I, _I, _I, ctypes.POINTER(_VP)]),
     "fft3d_plan_grid_offset": (_I, [_VP, _I, ctypes.POINTER(ctypes.c_int64)]),

@@ -116,7 +116,8 @@ static void mma_fragments(int prec, uint32_t* out /* tc::kFragWords */) {
 // (row = output column 2 k2 + d, 32 input entries 2 n2 + c per row) in
 // 8 x 16-byte core matrices: byte ((row / 8) * 4 + kk / 8) * 128 +
 // (row % 8) * 16 + (kk % 8) * 2 of block (term * 4 + k1) * 2048, term 0 the
-// hi halves, 1 the lo halves (FP16, or BF16 for prec 2).
+// hi halves, 1 the lo halves (FP16, or BF16 for prec 2): hi = rn(b),
+// lo = rn(b - hi), each rounded once from the FP64 value.
 static void umma_b_table(int prec, uint16_t* out /* 8192 */) {
   for (int k1 = 0; k1 < 4; ++k1)
     for (int row = 0; row < 32; ++row)
@@ -128,13 +129,13 @@ static void umma_b_table(int prec, uint16_t* out /* 8192 */) {
         const double v = c == 0 ? (d == 0 ? wr : wi) : (d == 0 ? -wi : wr);
         uint16_t hi, lo;
         if (prec == 2) {
-          const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
-          const __nv_bfloat16 l = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
+          const __nv_bfloat16 h = __double2bfloat16(v);
+          const __nv_bfloat16 l = __double2bfloat16(v - (double)__bfloat162float(h));
           hi = __bfloat16_as_ushort(h);
           lo = __bfloat16_as_ushort(l);
         } else {
-          const __half h = __float2half_rn((float)v);
-          const __half l = __float2half_rn((float)(v - (double)__half2float(h)));
+          const __half h = __double2half(v);
+          const __half l = __double2half(v - (double)__half2float(h));
           hi = __half_as_ushort(h);
           lo = __half_as_ushort(l);
         }
@@ -742,6 +743,13 @@ int fft3d_execute_host(fft3d_plan plan, const void* host_in, void* host_out, voi
 extern "C" {
 
 int fft3d_size_supported(int n) { return fused_size(n) ? 1 : 0; }
+
+int fft3d_tc_operand_table(int precision, uint16_t* out) {
+  if (!out) return FFT3D_ERR_NULL_PTR;
+  if (precision < FFT3D_SPLIT_FP16 || precision > FFT3D_FP16) return FFT3D_ERR_INVALID_ARG;
+  umma_b_table(precision, out);
+  return FFT3D_SUCCESS;
+}
 
 int fft3d_twiddle_table(int n, float* out, int* l1, int* l2) {
   if (!out || !l1 || !l2) return FFT3D_ERR_NULL_PTR;

@@ -106,3 +106,63 @@ def test_twiddle_tables_are_rounded_fp64(fft3d_lib, n):
             a = 2 * math.pi * ((n1 * k2) % n) / n
             assert got[k2, n1, 0] == np.float32(math.cos(a))
             assert got[k2, n1, 1] == np.float32(-math.sin(a))
+
+
+def _rn_bits(x: float, bits: int, min_normal_exp: int) -> float:
+    """x rounded to nearest (ties to even) with `bits` significant bits and
+    a subnormal quantum below 2**min_normal_exp (FP16: 11, -14; BF16: 8,
+    -126), written from the definition with frexp."""
+    if x == 0.0:
+        return 0.0
+    m, e = math.frexp(x)  # x = m 2^e, 0.5 <= |m| < 1
+    if e - 1 < min_normal_exp:
+        q = 2.0 ** (min_normal_exp - bits + 1)
+        return round(x / q) * q
+    return round(m * 2.0 ** bits) * 2.0 ** (e - bits)
+
+
+@pytest.mark.parametrize("prec", [1, 2, 3])
+def test_tc_operand_table_is_the_twiddled_dft16(fft3d_lib, prec):
+    """The tcgen05 B operands: for k1 < 4 the real 2 x 2 form of
+    W_64^(n2 (k1 + 4 k2)) at the documented core-matrix positions, hi =
+    rn(b) and lo = rn(b - hi) of the FP64 entry b (FP16; BF16 for split
+    BF16), and hi + lo reproducing the complex matrix."""
+    buf = (ctypes.c_uint16 * 8192)()
+    assert fft3d_lib.fft3d_tc_operand_table(prec, buf) == 0
+    raw = np.frombuffer(buf, dtype=np.uint16)
+    bf16 = prec == 2
+    bits, emin = (8, -126) if bf16 else (11, -14)
+
+    def dec(u):
+        if bf16:
+            return float(np.array([int(u) << 16], dtype=np.uint32).view(np.float32)[0])
+        return float(np.array([u], dtype=np.uint16).view(np.float16)[0])
+
+    for k1 in range(4):
+        m_rec = np.zeros((16, 16), np.complex128)
+        for nn in range(32):
+            for kk in range(32):
+                k2, d, n2, c = nn // 2, nn % 2, kk // 2, kk % 2
+                a = -2.0 * math.pi * ((n2 * (k1 + 4 * k2)) % 64) / 64.0
+                wr, wi = math.cos(a), math.sin(a)
+                b = (wr if d == 0 else wi) if c == 0 else (-wi if d == 0 else wr)
+                off = ((nn // 8) * 4 + kk // 8) * 128 + (nn % 8) * 16 + (kk % 8) * 2
+                hi = dec(raw[(0 * 4 + k1) * 1024 + off // 2])
+                lo = dec(raw[(1 * 4 + k1) * 1024 + off // 2])
+                assert hi == _rn_bits(b, bits, emin)
+                assert lo == _rn_bits(b - hi, bits, emin)
+                if c == 0:
+                    if d == 0:
+                        m_rec[n2, k2] += hi + lo
+                    else:
+                        m_rec[n2, k2] += 1j * (hi + lo)
+        n2g, k2g = np.meshgrid(np.arange(16), np.arange(16), indexing="ij")
+        expect = np.exp(-2j * np.pi * n2g * (k1 + 4 * k2g) / 64)
+        assert np.abs(m_rec - expect).max() < (2.0 ** -15 if bf16 else 2.0 ** -20)
+
+
+def test_tc_operand_table_errors(fft3d_lib):
+    buf = (ctypes.c_uint16 * 8192)()
+    assert fft3d_lib.fft3d_tc_operand_table(1, None) == L.FFT3D_ERR_NULL_PTR
+    for bad in (0, 4, -1):
+        assert fft3d_lib.fft3d_tc_operand_table(bad, buf) == L.FFT3D_ERR_INVALID_ARG
