@@ -118,65 +118,87 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
     float2* gout;
     grid_ptrs(a, d.grid, N, gin, gout);
     float2 v[H];
-    if (d.phase == 0) {
-      // x: row r = gt / 2 of the half-plane, this thread's points p + 2 m
-      const int r = gt >> 1, p = gt & 1;
+    // The passes of the item (half-plane: x, then y; slab: z) share one copy
+    // of the tensor-core pass (for the instruction cache); loads and stores
+    // of each pass are chosen once per pass.
+    //   x: row r = gt / 2 of the tile, this thread's points p + 2 m, then
+    //      the pair radix-2 back into the tile;
+    //   y: column c = gt, 64-point DFT over the rows of this parity, times
+    //      W_128^(parity k2), to global memory;
+    //   z: slab (k2, q): column x = 32 q + xl, output row y = k2 + 64 yr,
+    //      the y radix-2 (E + O or E - O), this thread's z points p + 2 m,
+    //      then the pair radix-2 to global memory.
+    const int npass = d.phase == 0 ? 2 : 1;
+    bool fail = false;
+#pragma unroll 1
+    for (int ps = 0; ps < npass; ++ps) {
+      const int kind = d.phase == 0 ? ps : 2;  // 0 x, 1 y, 2 z
+      if (kind == 0) {
+        const int r = gt >> 1, p = gt & 1;
 #pragma unroll
-      for (int m = 0; m < H; ++m) v[m] = lds2(t + hoff(r, p + 2 * m));
-      if (!dft64(v)) break;
-      // write back X[c]; the odd thread stores the two of a pair in the other
-      // order, so the two threads of a row never hit the same bank
-      sy::pair_radix2<DIR>(v, p, 1, [&](int j, float2 a0, float2 a1, float2 b0, float2 b1) {
-        const int c0 = j + 32 * p;
-        sts2(t + hoff(r, c0 + p), p ? a1 : a0);
-        sts2(t + hoff(r, c0 + 1 - p), p ? a0 : a1);
-        sts2(t + hoff(r, c0 + 64 + p), p ? b1 : b0);
-        sts2(t + hoff(r, c0 + 65 - p), p ? b0 : b1);
-      });
-      named_bar(1 + g, K::GT);  // the x results are in the tile
-      // y: column c = gt, 64-point DFT over the rows of this parity
-      const int par = d.idx & 1, c = gt;
+        for (int m = 0; m < H; ++m) v[m] = lds2(t + hoff(r, p + 2 * m));
+      } else if (kind == 1) {
 #pragma unroll
-      for (int m = 0; m < H; ++m) v[m] = lds2(t + hoff(m, c));
-      if (!dft64(v)) break;
-      if (par)  // times W_128^k2 (compile-time twiddles)
-        static_for<1, H>([&](auto K2) {
-          constexpr int k2 = decltype(K2)::value;
-          v[k2] = twc<k2, 128, DIR>(v[k2]);
-        });
-      // the intermediate: kept in L2 until its slabs have read it
-      const unsigned long long keep = policy_evict_last();
-      float2* dst = gout + (long long)(d.idx >> 1) * NN + (long long)par * H * N + c;
+        for (int m = 0; m < H; ++m) v[m] = lds2(t + hoff(m, gt));
+      } else {
+        const int wl = w - 4 - g * K::GW;
+        const int p = lane >> 4, xl = (wl & 1) * 16 + (lane & 15), yr = wl >> 1;
+        const float sg = yr ? -1.0f : 1.0f;  // the y radix-2: E + O or E - O
 #pragma unroll
-      for (int k2 = 0; k2 < H; ++k2)
-        asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(dst + (long long)k2 * N),
-                     "f"(v[k2].x), "f"(v[k2].y), "l"(keep)
-                     : "memory");
-    } else {
-      // slab (k2, q): column x = 32 q + xl, output row y = k2 + 64 yr,
-      // this thread's z points p + 2 m
-      const int wl = w - 4 - g * K::GW;  // warp within the group
-      const int p = lane >> 4, xl = (wl & 1) * 16 + (lane & 15), yr = wl >> 1;
-      const int k2 = d.idx >> 2, q = d.idx & 3;
-      const float sg = yr ? -1.0f : 1.0f;  // the y radix-2: E + O or E - O
-#pragma unroll
-      for (int m = 0; m < H; ++m) {
-        const int z = p + 2 * m;
-        const float2 e = lds2(t + soff(0, z, xl));
-        const float2 o = lds2(t + soff(1, z, xl));
-        v[m] = fma2(o, make_float2(sg, sg), e);
+        for (int m = 0; m < H; ++m) {
+          const int z = p + 2 * m;
+          const float2 e = lds2(t + soff(0, z, xl));
+          const float2 o = lds2(t + soff(1, z, xl));
+          v[m] = fma2(o, make_float2(sg, sg), e);
+        }
       }
-      if (!dft64(v)) break;
-      float2* dst = gout + (long long)(k2 + H * yr) * N + 32 * q + xl;
-      const float sc = a.do_scale ? a.scale : 1.f;
-      sy::pair_radix2<DIR>(v, p, 16, [&](int j, float2 a0, float2 a1, float2 b0, float2 b1) {
-        float2* d0 = dst + (long long)(j + 32 * p) * NN;
-        st_stream(d0, cscale(a0, sc));
-        st_stream(d0 + NN, cscale(a1, sc));
-        st_stream(d0 + H * NN, cscale(b0, sc));
-        st_stream(d0 + (H + 1) * NN, cscale(b1, sc));
-      });
+      if (!dft64(v)) {
+        fail = true;
+        break;
+      }
+      if (kind == 0) {
+        const int r = gt >> 1, p = gt & 1;
+        // write back X[c]; the odd thread stores the two of a pair in the
+        // other order, so the two threads of a row never hit the same bank
+        sy::pair_radix2<DIR>(v, p, 1, [&](int j, float2 a0, float2 a1, float2 b0, float2 b1) {
+          const int c0 = j + 32 * p;
+          sts2(t + hoff(r, c0 + p), p ? a1 : a0);
+          sts2(t + hoff(r, c0 + 1 - p), p ? a0 : a1);
+          sts2(t + hoff(r, c0 + 64 + p), p ? b1 : b0);
+          sts2(t + hoff(r, c0 + 65 - p), p ? b0 : b1);
+        });
+        named_bar(1 + g, K::GT);  // the x results are in the tile
+      } else if (kind == 1) {
+        const int par = d.idx & 1;
+        if (par)  // times W_128^k2 (compile-time twiddles)
+          static_for<1, H>([&](auto K2) {
+            constexpr int k2 = decltype(K2)::value;
+            v[k2] = twc<k2, 128, DIR>(v[k2]);
+          });
+        // the intermediate: kept in L2 until its slabs have read it
+        const unsigned long long keep = policy_evict_last();
+        float2* dst = gout + (long long)(d.idx >> 1) * NN + (long long)par * H * N + gt;
+#pragma unroll
+        for (int k2 = 0; k2 < H; ++k2)
+          asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(dst + (long long)k2 * N),
+                       "f"(v[k2].x), "f"(v[k2].y), "l"(keep)
+                       : "memory");
+      } else {
+        const int wl = w - 4 - g * K::GW;
+        const int p = lane >> 4, xl = (wl & 1) * 16 + (lane & 15), yr = wl >> 1;
+        const int k2 = d.idx >> 2, q = d.idx & 3;
+        float2* dst = gout + (long long)(k2 + H * yr) * N + 32 * q + xl;
+        const float sc = a.do_scale ? a.scale : 1.f;
+        sy::pair_radix2<DIR>(v, p, 16, [&](int j, float2 a0, float2 a1, float2 b0, float2 b1) {
+          float2* d0 = dst + (long long)(j + 32 * p) * NN;
+          st_stream(d0, cscale(a0, sc));
+          st_stream(d0 + NN, cscale(a1, sc));
+          st_stream(d0 + H * NN, cscale(b0, sc));
+          st_stream(d0 + (H + 1) * NN, cscale(b1, sc));
+        });
+      }
     }
+    if (fail) break;
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
   }
