@@ -98,6 +98,11 @@ __device__ __forceinline__ float2 lds2(uint32_t a) {
 __device__ __forceinline__ void sts2(uint32_t a, float2 v) {
   asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
 }
+__device__ __forceinline__ void sts4(uint32_t a, float2 v, float2 w) {
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(w.x),
+               "f"(w.y)
+               : "memory");
+}
 
 // 128-point FFT finished by a thread pair: v holds this thread's 64-point
 // DFT (E for p = 0, O for p = 1) of points p + 2 m.  Thread p produces
@@ -376,15 +381,12 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
       if (kind == 0) {
         const int r = gt >> 1, p = gt & 1;
         __syncwarp();  // both threads of the row have read it
-        // write back X[c]; the odd thread stores the two of a pair in the
-        // other order, so the two threads of a row never hit the same bank
+        // write back X[c], two adjacent columns per 16-byte store
 #pragma unroll
         for (int j = 0; j < 32; j += 2) {
           const int c0 = j + 32 * p;
-          sts2(t + hoff(r, c0 + p), p ? v[j + 1] : v[j]);
-          sts2(t + hoff(r, c0 + 1 - p), p ? v[j] : v[j + 1]);
-          sts2(t + hoff(r, c0 + 64 + p), p ? v[33 + j] : v[32 + j]);
-          sts2(t + hoff(r, c0 + 65 - p), p ? v[32 + j] : v[33 + j]);
+          sy::sts4(t + hoff(r, c0), v[j], v[j + 1]);
+          sy::sts4(t + hoff(r, c0 + 64), v[32 + j], v[33 + j]);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&tr[g]);

@@ -156,17 +156,27 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
         fail = true;
         break;
       }
+      if (kind != 1) {
+        // the pair radix-2 of x and z (one copy), in place: v[j] = X[j + 32 p],
+        // v[32 + j] = X[j + 32 p + 64]
+        const int p = kind == 0 ? (gt & 1) : (lane >> 4);
+        sy::pair_radix2<DIR>(v, p, kind == 0 ? 1 : 16,
+                             [&](int j, float2 a0, float2 a1, float2 b0, float2 b1) {
+                               v[j] = a0;
+                               v[j + 1] = a1;
+                               v[32 + j] = b0;
+                               v[33 + j] = b1;
+                             });
+      }
       if (kind == 0) {
         const int r = gt >> 1, p = gt & 1;
-        // write back X[c]; the odd thread stores the two of a pair in the
-        // other order, so the two threads of a row never hit the same bank
-        sy::pair_radix2<DIR>(v, p, 1, [&](int j, float2 a0, float2 a1, float2 b0, float2 b1) {
+        // write back X[c], two adjacent columns per 16-byte store
+#pragma unroll
+        for (int j = 0; j < 32; j += 2) {
           const int c0 = j + 32 * p;
-          sts2(t + hoff(r, c0 + p), p ? a1 : a0);
-          sts2(t + hoff(r, c0 + 1 - p), p ? a0 : a1);
-          sts2(t + hoff(r, c0 + 64 + p), p ? b1 : b0);
-          sts2(t + hoff(r, c0 + 65 - p), p ? b0 : b1);
-        });
+          sy::sts4(t + hoff(r, c0), v[j], v[j + 1]);
+          sy::sts4(t + hoff(r, c0 + 64), v[32 + j], v[33 + j]);
+        }
         named_bar(1 + g, K::GT);  // the x results are in the tile
       } else if (kind == 1) {
         const int par = d.idx & 1;
@@ -187,15 +197,13 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
         const int wl = w - 4 - g * K::GW;
         const int p = lane >> 4, xl = (wl & 1) * 16 + (lane & 15), yr = wl >> 1;
         const int k2 = d.idx >> 2, q = d.idx & 3;
-        float2* dst = gout + (long long)(k2 + H * yr) * N + 32 * q + xl;
+        float2* dst = gout + (long long)(k2 + H * yr) * N + 32 * q + xl + (long long)(32 * p) * NN;
         const float sc = a.do_scale ? a.scale : 1.f;
-        sy::pair_radix2<DIR>(v, p, 16, [&](int j, float2 a0, float2 a1, float2 b0, float2 b1) {
-          float2* d0 = dst + (long long)(j + 32 * p) * NN;
-          st_stream(d0, cscale(a0, sc));
-          st_stream(d0 + NN, cscale(a1, sc));
-          st_stream(d0 + H * NN, cscale(b0, sc));
-          st_stream(d0 + (H + 1) * NN, cscale(b1, sc));
-        });
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          st_stream(dst + (long long)j * NN, cscale(v[j], sc));
+          st_stream(dst + (long long)(j + H) * NN, cscale(v[32 + j], sc));
+        }
       }
     }
     if (fail) break;
