@@ -352,8 +352,9 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
 #pragma unroll
         for (int m = 0; m < H; ++m) v[m] = lds2(t + hoff(r, p + 2 * m));
       } else if (kind == 1) {
+        const int cs = gt ^ (((gt >> 5) & 1) << 3);  // the slot of column gt
 #pragma unroll
-        for (int m = 0; m < H; ++m) v[m] = lds2(t + hoff(m, gt));
+        for (int m = 0; m < H; ++m) v[m] = lds2(t + hoff(m, cs));
       } else {
         const int wl = w - 4 - g * K::GW;
         const int p = lane >> 4, xl = (wl & 1) * 16 + (lane & 15), yr = wl >> 1;
@@ -381,12 +382,15 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
       if (kind == 0) {
         const int r = gt >> 1, p = gt & 1;
         __syncwarp();  // both threads of the row have read it
-        // write back X[c], two adjacent columns per 16-byte store
+        // write back X[c], two adjacent columns per 16-byte store, at slot
+        // c ^ 8 for the odd thread's columns (bit 5 of c set), so that the
+        // two threads of a row hit different banks; the y pass reads there
+        const int cx = 8 * p;
 #pragma unroll
         for (int j = 0; j < 32; j += 2) {
           const int c0 = j + 32 * p;
-          sy::sts4(t + hoff(r, c0), v[j], v[j + 1]);
-          sy::sts4(t + hoff(r, c0 + 64), v[32 + j], v[33 + j]);
+          sy::sts4(t + hoff(r, c0 ^ cx), v[j], v[j + 1]);
+          sy::sts4(t + hoff(r, (c0 + 64) ^ cx), v[32 + j], v[33 + j]);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&tr[g]);
