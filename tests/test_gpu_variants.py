@@ -78,3 +78,24 @@ def test_tensor_kernels_schedule_beyond_shared_table(cuda, monkeypatch, variant)
         assert oracle.rel_l2(y[b].cpu().numpy(), (b + 1) * ref0) <= FP32_TOL
     del x, y
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("n,variant,precision,batch",
+                         [(64, 8, "fp32", 64), (128, 6, "fp32", 8),
+                          (64, 9, "split_fp16", 64), (128, 9, "split_fp16", 8)])
+def test_back_to_back_launches_stay_live(cuda, monkeypatch, n, variant, precision, batch):
+    """Thousands of launches in a row of the kernels whose three tiles serve
+    two compute groups in turn (a tile barrier per group and tile): no
+    bounded wait may time out, and the last result equals the first."""
+    from paper_2006_08435_gb300 import Plan
+    monkeypatch.setenv("FFT3D_VARIANT", str(variant))
+    x = torch.from_numpy(synth.uniform_grids(n, batch, seed=41)).cuda()
+    y = torch.empty_like(x)
+    p = Plan(n, n, n, batch, precision=precision)
+    assert p.variant == variant
+    p.execute(x, y)
+    first = y.clone()
+    for _ in range(2000):
+        p.execute(x, y)
+    assert p.device_status() == 0
+    assert torch.equal(y, first)
