@@ -16,8 +16,8 @@
 //   2. each thread writes its four rows (k1) of the A operands into tensor
 //      memory (lane = pencil, one 32-bit column per two K entries): hi = R
 //      rounded to a multiple of 16 by adding and subtracting 1.5 * 2^27
-//      (exact in FP16; 128 and BF16 for split BF16), lo = the exact
-//      remainder rounded once;
+//      (exact in FP16; 128 and BF16 for split BF16), stored as -hi (the
+//      products with it negate A), lo = the exact remainder rounded once;
 //   3. after one group barrier, one thread of warp k1 issues D_k1 = A_hi
 //      B_hi + A_hi B_lo + A_lo B_hi (M = 128 pencils, N = 32, K = 32: six
 //      kind::f16 products, A from tensor memory, B from shared memory, FP32
@@ -68,11 +68,40 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
 }
 
 // Instruction descriptor of kind::f16: FP32 accumulator, A and B FP16 (or
-// BF16 for PREC 2), both K-major, N = 32, M = 128.
-template <int PREC>
+// BF16 for PREC 2), A negated if NEG, both K-major, N = 32, M = 128.
+template <int PREC, bool NEG = false>
 constexpr uint32_t idesc() {
   constexpr uint32_t ab = PREC == 2 ? 1u : 0u;
-  return (1u << 4) | (ab << 7) | (ab << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+  return (1u << 4) | (ab << 7) | (ab << 10) | ((NEG ? 1u : 0u) << 13) | ((32u >> 3) << 17) |
+         ((128u >> 4) << 24);
+}
+
+// y = x s split as hi + lo for the split kinds, returning -hi: the adding
+// and subtracting of 1.5 * 2^27 (2^30 for BF16) yields -hi and the exact
+// remainder with one subtraction, and the products with hi negate A.  Plain
+// FP16 returns hi = rn(y) itself.
+template <int PREC>
+__device__ __forceinline__ void split_nhi(float2 x, float2 s, uint32_t& nhi, uint32_t& lo) {
+  if constexpr (PREC == 3) {
+    tcr::split<3>(x, s, nhi, lo);
+  } else {
+    constexpr float C = PREC == 2 ? 1610612736.0f : 201326592.0f;
+    const float2 c = make_float2(C, C);
+    const float2 t = fma2(x, s, c);
+    const float2 hn = csub(c, t);       // -(x s rounded to the hi quantum)
+    const float2 lf = fma2(x, s, hn);   // x s - hi, exact
+    if constexpr (PREC == 2) {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(hn.x, hn.y);
+      const __nv_bfloat162 l = __floats2bfloat162_rn(lf.x, lf.y);
+      nhi = *reinterpret_cast<const uint32_t*>(&h);
+      lo = *reinterpret_cast<const uint32_t*>(&l);
+    } else {
+      const __half2 h = __floats2half2_rn(hn.x, hn.y);
+      const __half2 l = __floats2half2_rn(lf.x, lf.y);
+      nhi = *reinterpret_cast<const uint32_t*>(&h);
+      lo = *reinterpret_cast<const uint32_t*>(&l);
+    }
+  }
 }
 
 // D (tensor memory) (+)= A (tensor memory) B (shared memory descriptor).
@@ -192,7 +221,7 @@ __device__ __forceinline__ bool pass(float2 (&v)[64], const Pass& P, unsigned& p
     for (int e = 0; e < 2; ++e) {
       uint32_t h[8], l[8];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) tcr::split<PREC>(v[16 * k1 + 8 * e + i], s2, h[i], l[i]);
+      for (int i = 0; i < 8; ++i) split_nhi<PREC>(v[16 * k1 + 8 * e + i], s2, h[i], l[i]);
       tmem_st8(P.col + P.lanes + 16 * k1 + 8 * e, h);
       if constexpr (PREC != 3) tmem_st8(P.col + P.lanes + 16 * (4 + k1) + 8 * e, l);
     }
@@ -204,19 +233,20 @@ __device__ __forceinline__ bool pass(float2 (&v)[64], const Pass& P, unsigned& p
     // keep the tensor cores busier than one (each instruction costs its
     // issuing thread some tens of cycles)
     tc_fence_after();
-    constexpr uint32_t id = idesc<PREC>();
+    // the A_hi columns hold -hi for the split kinds: those products negate A
+    constexpr uint32_t idh = idesc<PREC, PREC != 3>(), idl = idesc<PREC>();
     {
       const int k1 = P.gt >> 5;
       const uint32_t d = P.col + 128 + 32 * k1;
       const uint32_t ahi = P.col + 16 * k1, alo = P.col + 16 * (4 + k1);
       const uint32_t bhi = P.bsm + k1 * 2048, blo = P.bsm + (4 + k1) * 2048;
 #pragma unroll
-      for (int ks = 0; ks < 2; ++ks) umma(d, ahi + 8 * ks, sdesc(bhi + 256 * ks), id, ks);
+      for (int ks = 0; ks < 2; ++ks) umma(d, ahi + 8 * ks, sdesc(bhi + 256 * ks), idh, ks);
       if constexpr (PREC != 3) {
 #pragma unroll
-        for (int ks = 0; ks < 2; ++ks) umma(d, ahi + 8 * ks, sdesc(blo + 256 * ks), id, 1);
+        for (int ks = 0; ks < 2; ++ks) umma(d, ahi + 8 * ks, sdesc(blo + 256 * ks), idh, 1);
 #pragma unroll
-        for (int ks = 0; ks < 2; ++ks) umma(d, alo + 8 * ks, sdesc(bhi + 256 * ks), id, 1);
+        for (int ks = 0; ks < 2; ++ks) umma(d, alo + 8 * ks, sdesc(bhi + 256 * ks), idl, 1);
       }
     }
     umma_commit(P.bar);
