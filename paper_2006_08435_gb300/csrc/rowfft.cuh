@@ -22,9 +22,10 @@
 // (8-byte accesses, sixteen columns of one row per phase) are free of bank
 // conflicts.
 //
-// Block: four compute groups of 64 threads (each group one item at a time,
-// items k = g, g + 4, ...), one producer warp (tickets, slab dependencies,
-// tensor copies into a ring of six tiles) and one publisher warp (publishes
+// Block: three compute groups of 64 threads (each group one item at a time,
+// items k = g, g + 3, ...; tile k % 6, so each tile always serves the same
+// group), one producer warp (tickets, slab dependencies, tensor copies into
+// a ring of six tiles) and one publisher warp (publishes
 // finished planes; tiles go back to the producer straight from the compute
 // groups).  One block per SM.  Liveness and bounded waits
 // as in the double-buffered kernel: a block's started items finish without
