@@ -284,6 +284,8 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
       // y: column x = u of plane j, output rows straight to global memory
 #pragma unroll
       for (int r = 0; r < N; ++r) v[r] = *reinterpret_cast<const float2*>(t + boff<N>(64 * j + r, u));
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);  // the tile is read: back to the producer
       DFT<N, DIR>::run(v);
       float2* dst = gout + (long long)(2 * d.idx + j) * NN + u;
       const unsigned long long keep = policy_evict_last();  // until its slabs read it
@@ -295,6 +297,8 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
       // z: column x = u of slab y = 2 idx + j
 #pragma unroll
       for (int z = 0; z < N; ++z) v[z] = *reinterpret_cast<const float2*>(t + boff<N>(2 * z + j, u));
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);  // the tile is read: back to the producer
       DFT<N, DIR>::run(v);
       float2* dst = gout + (long long)(2 * d.idx + j) * N + u;
 #pragma unroll
@@ -305,10 +309,7 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
       }
     }
     __syncwarp();
-    if (lane == 0) {
-      mbar_arrive(&empty[s]);         // the tile is free
-      mbar_arrive(&done[k % K::DQ]);  // and the stores done, for the publisher
-    }
+    if (lane == 0) mbar_arrive(&done[k % K::DQ]);  // the stores are done, for the publisher
   }
 }
 
