@@ -202,11 +202,18 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
         const int p = lane >> 4, xl = (wl & 1) * 16 + (lane & 15), yr = wl >> 1;
         const int k2 = d.idx >> 2, q = d.idx & 3;
         float2* dst = gout + (long long)(k2 + H * yr) * N + 32 * q + xl + (long long)(32 * p) * NN;
-        const float sc = a.do_scale ? a.scale : 1.f;
+        if (a.do_scale) {  // (uniform) the output scale only when one is asked for
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          st_stream(dst + (long long)j * NN, cscale(v[j], sc));
-          st_stream(dst + (long long)(j + H) * NN, cscale(v[32 + j], sc));
+          for (int j = 0; j < 32; ++j) {
+            st_stream(dst + (long long)j * NN, cscale(v[j], a.scale));
+            st_stream(dst + (long long)(j + H) * NN, cscale(v[32 + j], a.scale));
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            st_stream(dst + (long long)j * NN, v[j]);
+            st_stream(dst + (long long)(j + H) * NN, v[32 + j]);
+          }
         }
       }
     }
