@@ -88,11 +88,14 @@ __device__ __forceinline__ uint32_t soff(int r, int z, int x) {
                     ((x & 1) << 3));
 }
 
-// Shared-memory accesses by 32-bit shared-window address (not volatile, so
-// the compiler may schedule them like plain loads).
+// Shared-memory accesses by 32-bit shared-window address.  The load is not
+// volatile (an unused one may be dropped) but declares that it reads memory,
+// so that it stays ordered after the barrier waits and the stores that fill
+// the tile (an asm without the clobber would count as reading no memory at
+// all, free to move across them or to merge with an earlier load).
 __device__ __forceinline__ float2 lds2(uint32_t a) {
   float2 v;
-  asm("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
+  asm("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
   return v;
 }
 __device__ __forceinline__ void sts2(uint32_t a, float2 v) {

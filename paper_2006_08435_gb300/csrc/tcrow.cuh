@@ -50,10 +50,12 @@ using rowk::policy_evict_last;
 using rowk2::boff;
 using rowk2::Cfg;
 
-// Shared-memory accesses by 32-bit shared-window address.
+// Shared-memory accesses by 32-bit shared-window address; the load declares
+// that it reads memory, so it stays ordered after the barrier waits and the
+// stores that fill the tile.
 __device__ __forceinline__ float2 lds2(uint32_t a) {
   float2 v;
-  asm("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
+  asm("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
   return v;
 }
 __device__ __forceinline__ void sts4(uint32_t a, float2 v, float2 w) {
