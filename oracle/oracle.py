@@ -14,6 +14,12 @@ Contents
   lines.  O(n^4) for an n^3 grid.
 * ``dft3d_brute``  -- the literal triple sum of Eq. 1, O(n^6); pins the
   separable form on tiny grids.
+* ``rdft3d`` / ``irdft3d`` -- Eq. 1 for real grids (a real density, the
+  paper's plane-wave DFT setting): the forward transform of a real grid
+  keeps the half spectrum kx <= nx/2 (the rest is its complex conjugate
+  mirrored); the inverse extends a half spectrum by that symmetry and keeps
+  the real part of the inverse transform.  Both are the complex ``dft3d``
+  plus that bookkeeping.
 * ``hartree_*``    -- the plane-wave Hartree energy of a periodic density and
   its gradient, written from the standard Gaussian-and-plane-wave definition
   (the paper's motivating application, section "Introduction" and
@@ -116,6 +122,50 @@ def dft3d_brute(x, sign: int = -1) -> np.ndarray:
     if rc != 0:
         raise RuntimeError(f"oracle_dft3d_brute failed ({rc})")
     return out
+
+
+def rdft3d(r) -> np.ndarray:
+    """Forward transform (Eq. 1, exponent sign -1, unnormalised) of REAL
+    grids over the last three axes (nz, ny, nx), returned as the half
+    spectrum kx = 0 .. nx // 2: shape (..., nz, ny, nx // 2 + 1), complex128.
+    For real input F(-k) = conj(F(k)), so the dropped bins carry nothing
+    new.  FP64 throughout."""
+    a = np.asarray(r)
+    if np.iscomplexobj(a):
+        raise TypeError("rdft3d takes real grids")
+    if a.ndim < 3:
+        raise ValueError("need at least 3 dims (nz, ny, nx)")
+    nx = a.shape[-1]
+    return dft3d(a.astype(np.float64), sign=-1)[..., : nx // 2 + 1]
+
+
+def hermitian_extend(half, nx: int) -> np.ndarray:
+    """Full spectrum E(X) of a half spectrum X (..., nz, ny, nx // 2 + 1):
+    E(X)(k) = X(k) for kx <= nx // 2 and conj(X(-k)) for kx > nx // 2, with
+    -k taken modulo (nz, ny, nx)."""
+    h = _as_c128(half)
+    if h.ndim < 3 or h.shape[-1] != nx // 2 + 1:
+        raise ValueError("need (..., nz, ny, nx // 2 + 1)")
+    nz, ny = h.shape[-3], h.shape[-2]
+    full = np.empty(h.shape[:-1] + (nx,), dtype=np.complex128)
+    full[..., : nx // 2 + 1] = h
+    for kx in range(nx // 2 + 1, nx):
+        # conj(X(-kz, -ky, nx - kx)) for every (kz, ky)
+        mz = (-np.arange(nz)) % nz
+        my = (-np.arange(ny)) % ny
+        col = h[..., nx - kx]                      # (..., nz, ny)
+        full[..., kx] = np.conj(col[..., mz, :][..., :, my])
+    return full
+
+
+def irdft3d(half, nx: int) -> np.ndarray:
+    """Inverse transform (exponent sign +1, unnormalised) of half spectra
+    (..., nz, ny, nx // 2 + 1) to REAL grids (..., nz, ny, nx): the real part
+    of the inverse transform of the Hermitian extension E(X).  For a half
+    spectrum of a real grid this is nz ny nx times that grid; for any other
+    input it equals the inverse of the Hermitian part of E(X) (the imaginary
+    parts of the self-mirrored bins drop out).  FP64 throughout."""
+    return dft3d(hermitian_extend(half, nx), sign=+1).real
 
 
 def rel_l2(y, y_ref) -> float:
