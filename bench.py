@@ -9,7 +9,7 @@ transform = 16 * N^3 (one read and one write of the grid).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload 128x32|64x256|128x16|64x64] [--no-cpu-baseline] [--no-e2e]
-                  [--no-split]
+                  [--no-split] [--no-real]
 
 The two small workloads exist for profiler captures of the same kernels.
 
@@ -319,6 +319,32 @@ def run_ours(args, ws, rank, local):
         split = {"value": ws * batch / (ms16 / 1e3), "unit": "transforms/s", "steps": k16,
                  "ms_per_step": ms16}
 
+    # real grids (the real parts of the same batch): forward R2C to half
+    # spectra, two grids per complex transform (pack, transform, separate)
+    real = None
+    if not args.no_real:
+        from paper_2006_08435_gb300 import RealPlan
+        xr = x.real.contiguous()
+        yr = torch.empty((batch, n, n, n // 2 + 1), dtype=torch.complex64, device=dev)
+        rplan = RealPlan(n, batch)
+        for _ in range(3):
+            rplan.execute(xr, yr, stream)
+        barrier()
+        kr = max(1, args.steps // 8)
+        r0 = torch.cuda.Event(enable_timing=True)
+        r1 = torch.cuda.Event(enable_timing=True)
+        r0.record(stream)
+        for _ in range(kr):
+            rplan.execute(xr, yr, stream)
+        r1.record(stream)
+        barrier()
+        msr = r0.elapsed_time(r1) / kr
+        assert rplan.device_status() == 0
+        real = {"value": ws * batch / (msr / 1e3), "unit": "transforms/s", "steps": kr,
+                "ms_per_step": msr, "launches_per_step": 3,
+                "bytes_per_transform": 4 * n ** 3 + 8 * n * n * (n // 2 + 1)}
+        del xr, yr, rplan
+
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -350,6 +376,10 @@ def run_ours(args, ws, rank, local):
     if split is not None:
         split["roofline_frac"] = 16.0 * n ** 3 * batch / (split["ms_per_step"] / 1e3) / 1e9 / peak
         line["split_fp16"] = split
+    if real is not None:
+        real["roofline_frac"] = (real["bytes_per_transform"] * batch / (real["ms_per_step"] / 1e3)
+                                 / 1e9 / peak)
+        line["real_r2c_fp32"] = real
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(n)
     print(json.dumps(line), flush=True)
@@ -368,6 +398,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-split", action="store_true")
+    ap.add_argument("--no-real", action="store_true")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":

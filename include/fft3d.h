@@ -311,6 +311,63 @@ int fft3d_real_to_complex(const float* re, void* out, int64_t count, void* strea
 /* re[i] = Re in[i] for i < count (device complex64 -> float). */
 int fft3d_complex_to_real(const void* in, float* re, int64_t count, void* stream);
 
+/*
+ * ---------------------------------------------------------------------------
+ * Real grids (a real density, the setting of the paper's plane-wave DFT
+ * application, section "Introduction").  For a real grid f, Eq. 1 gives
+ * F(-k) = conj(F(k)) (indices modulo n), so the forward transform returns the
+ * HALF spectrum kx = 0 .. n/2 and the inverse takes one.
+ *
+ * Layouts: a real grid is n^3 floats, index (z*n + y)*n + x; a half spectrum
+ * is n*n*(n/2 + 1) complex64 points, index (kz*n + ky)*(n/2 + 1) + kx; grids
+ * of a batch are packed back to back.
+ *
+ * Forward: out = the half spectrum of F(in) (unnormalised, or scaled per
+ * norm).  Inverse: out = Re of the inverse transform of the Hermitian
+ * extension of the half spectrum `in` (bins above n/2 taken as conj(X(-k)));
+ * for a half spectrum of a real grid that is n^3 times the grid (norm NONE),
+ * and for any other input the imaginary parts of the self-mirrored bins
+ * (kx, ky, kz each 0 or n/2) drop out.  `in` is not modified.
+ *
+ * Two grids of the batch share one complex transform (c = a + i b; the pair
+ * is separated with the symmetry above), so a grid's rounding error is
+ * relative to the larger of its pair.  Cost per pair: a packing pass, one
+ * complex transform of the plan's precision, a separating pass.
+ * ---------------------------------------------------------------------------
+ */
+typedef struct fft3d_real_plan_s* fft3d_real_plan;
+
+/*
+ * Plan `batch` real transforms of n^3 grids.
+ *   n         : even and fft3d_size_supported (FFT3D_ERR_UNSUPPORTED_SIZE
+ *               otherwise).
+ *   batch     : 1 .. 2^24 grids.
+ *   precision : as for fft3d_plan_create (tensor-core kinds at n = 64, 128).
+ *   direction : FFT3D_FORWARD (real -> half spectrum) or FFT3D_INVERSE
+ *               (half spectrum -> real).
+ *   norm      : fft3d_norm (1/n^3 or 1/sqrt(n^3) on the output).
+ * Validates its arguments before touching the GPU.  Owns a complex plan of
+ * ceil(batch/2) grids and a device workspace of ceil(batch/2) * n^3 complex64
+ * points, both allocated here and freed by fft3d_real_plan_destroy.
+ */
+int fft3d_real_plan_create(int n, int batch, int precision, int direction, int norm,
+                           fft3d_real_plan* out_plan);
+
+/*
+ * Transform every grid of the plan.  `in` and `out` are DEVICE pointers,
+ * 16-byte aligned, not overlapping (forward: in = real grids, out = half
+ * spectra; inverse: the other way round).  Asynchronous on `stream`,
+ * allocates nothing, capturable in a CUDA graph (three kernels and the
+ * complex plan's launch).  A plan may run on one stream at a time.
+ */
+int fft3d_real_execute(fft3d_real_plan plan, const void* in, void* out, void* stream);
+
+/* As fft3d_get_device_status, for the plan's complex transform. */
+int fft3d_real_get_device_status(fft3d_real_plan plan, void* stream);
+
+/* Release the plan's complex plan and workspace.  NULL is accepted. */
+int fft3d_real_plan_destroy(fft3d_real_plan plan);
+
 /* Largest batch fft3d_execute_noalloc accepts. */
 #define FFT3D_NOALLOC_MAX_BATCH 4096
 

@@ -7,6 +7,7 @@ of Eq. 1 computed as 1D FFTs along x, then y, then z, behind the C ABI of
 
 * ``fft3d(x, inverse=False, norm="none", precision="fp32")``
 * ``Plan`` / ``MixedPlan`` -- explicit plans (batched / mixed edges)
+* ``rfft3d`` / ``irfft3d`` / ``RealPlan`` -- real grids (half spectra)
 * ``FFT3d`` -- autograd Function whose backward is the adjoint transform
 * ``hartree_energy`` -- plane-wave Hartree energy with an adjoint-FFT gradient
 
@@ -16,11 +17,13 @@ and raises if it has not been built (there is no CPU fallback).
 from ._lib import FFT3DError  # noqa: F401
 
 __all__ = ["fft3d", "Plan", "MixedPlan", "FFT3d", "FFT3DError", "size_supported",
+           "rfft3d", "irfft3d", "RealPlan",
            "hartree_energy", "HartreeEnergy"]
 
 
 def __getattr__(name):
     if name in ("fft3d", "Plan", "MixedPlan", "FFT3d", "size_supported", "get_plan",
+                "rfft3d", "irfft3d", "RealPlan",
                 "twiddle_table", "selftest_wait_timeout", "autotune", "autotune_mixed"):
         from . import fft as _fft
         return getattr(_fft, name)

@@ -1,0 +1,229 @@
+// Transforms of REAL grids (a real density, the setting of the paper's
+// plane-wave DFT application, section "Introduction") on top of the complex
+// transform of Eq. 1.
+//
+// Forward (R2C): for a real grid r, F(-k) = conj(F(k)), so only the half
+// spectrum kx = 0 .. n/2 is returned.  Two real grids a, b of the batch are
+// transformed by ONE complex transform of c = a + i b: with C = F(c),
+//   F(a)(k) = (C(k) + conj(C(-k))) / 2,   F(b)(k) = (C(k) - conj(C(-k))) / (2i),
+// -k taken modulo n on every axis.  So a batch of B real grids costs
+// ceil(B/2) complex transforms plus a packing pass before and a separating
+// pass after.
+// Inverse (C2R): the grid is the real part of the inverse transform of the
+// Hermitian extension E(X) of the half spectrum X (E(X)(k) = X(k) for
+// kx <= n/2, conj(X(-k)) above).  That real part is the inverse transform of
+// the Hermitian part H(X)(k) = (E(X)(k) + conj(E(X)(-k))) / 2, which differs
+// from E(X) only in the self-mirrored columns kx = 0 and n/2.  Two half
+// spectra A, B are rebuilt as one full spectrum H(A) + i H(B), transformed
+// once, and the real and imaginary parts of the result are the two grids.
+//
+// The kernels here move data only (pack, separate, rebuild, split); the
+// transforms are the library's complex plans.  Packing two grids into one
+// makes each grid's rounding error relative to the larger of the pair.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "fft3d.h"
+
+struct fft3d_real_plan_s {
+  int n = 0, batch = 0, pairs = 0, direction = FFT3D_FORWARD;
+  fft3d_plan inner = nullptr;  // complex plan of `pairs` n^3 grids
+  float2* d_work = nullptr;    // pairs * n^3 complex points
+};
+
+namespace fft3d {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxBlocks = 152 * 8;
+
+int blocks_for(long long units, int per_block) {
+  const long long b = (units + per_block - 1) / per_block;
+  return (int)(b < 1 ? 1 : (b > kMaxBlocks ? kMaxBlocks : b));
+}
+
+// c_j = r_{2j} + i r_{2j+1} (0 for a missing partner).  q = n^3 / 4; index i
+// in [0, pairs * q) is pair j = i / q, points 4 e .. 4 e + 3 (e = i - j q).
+// Reads r[2j q + e] (< batch q: 2j <= batch - 1) and, when 2j + 1 < batch,
+// r[(2j + 1) q + e]; writes c[2i], c[2i + 1] (< 2 pairs q float4 = pairs n^3
+// complex points).
+__global__ void pack_pairs_kernel(const float4* __restrict__ r, float4* __restrict__ c,
+                                  long long q, int batch, long long total) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long j = i / q, e = i - j * q;
+    const float4 a = __ldcs(r + 2 * j * q + e);
+    float4 b = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (2 * j + 1 < batch) b = __ldcs(r + (2 * j + 1) * q + e);
+    c[2 * i] = make_float4(a.x, b.x, a.y, b.y);
+    c[2 * i + 1] = make_float4(a.z, b.z, a.w, b.w);
+  }
+}
+
+// The inverse of the packing: r_{2j} = Re c_j, r_{2j+1} = Im c_j.
+__global__ void split_pairs_kernel(const float4* __restrict__ c, float4* __restrict__ r,
+                                   long long q, int batch, long long total) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long j = i / q, e = i - j * q;
+    const float4 u = __ldcs(c + 2 * i), v = __ldcs(c + 2 * i + 1);
+    __stcs(r + 2 * j * q + e, make_float4(u.x, u.z, v.x, v.z));
+    if (2 * j + 1 < batch) __stcs(r + (2 * j + 1) * q + e, make_float4(u.y, u.w, v.y, v.w));
+  }
+}
+
+// One warp per row (pair j, kz, ky) of the complex result C_j; the row of
+// -k is (n - kz, n - ky) mod n, column n - kx mod n.  Writes the half rows
+// (h = n/2 + 1 points) of grids 2j and 2j + 1.  Both rows are read through
+// L2 (each row of C_j is read once directly and once as a mirror).
+__global__ void separate_pairs_kernel(const float2* __restrict__ c, float2* __restrict__ out,
+                                      int n, int batch, long long rows) {
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const int h = n / 2 + 1;
+  const long long nn = (long long)n * n;
+  for (long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < rows;
+       row += nwarps) {
+    const long long j = row / nn;
+    const int rem = (int)(row - j * nn);
+    const int kz = rem / n, ky = rem - kz * n;
+    const int mz = kz ? n - kz : 0, my = ky ? n - ky : 0;
+    const float2* cj = c + j * nn * n;
+    const float2* crow = cj + ((long long)kz * n + ky) * n;
+    const float2* mrow = cj + ((long long)mz * n + my) * n;
+    float2* oa = out + 2 * j * nn * h + (long long)rem * h;
+    const bool has_b = 2 * j + 1 < batch;
+    for (int kx = lane; kx < h; kx += 32) {
+      const float2 C = __ldg(crow + kx);
+      const float2 M = __ldg(mrow + (kx ? n - kx : 0));  // C(-k)
+      oa[kx] = make_float2(0.5f * (C.x + M.x), 0.5f * (C.y - M.y));
+      if (has_b) oa[nn * h + kx] = make_float2(0.5f * (C.y + M.y), 0.5f * (M.x - C.x));
+    }
+  }
+}
+
+// One warp per row (pair j, kz, ky) of the full spectrum H(A) + i H(B),
+// A = X_{2j}, B = X_{2j+1} (0 when missing).  Columns kx < n/2 but 0 come
+// straight from the half rows, kx > n/2 from conj of the mirrored row at
+// column n - kx (in 1 .. n/2 - 1), and the self-mirrored columns 0 and n/2
+// are the mean of the bin and the conjugate of its mirror.
+__global__ void rebuild_pairs_kernel(const float2* __restrict__ x, float2* __restrict__ c,
+                                     int n, int batch, long long rows) {
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const int h = n / 2 + 1, half = n / 2;
+  const long long nn = (long long)n * n;
+  for (long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < rows;
+       row += nwarps) {
+    const long long j = row / nn;
+    const int rem = (int)(row - j * nn);
+    const int kz = rem / n, ky = rem - kz * n;
+    const int mz = kz ? n - kz : 0, my = ky ? n - ky : 0;
+    const float2* xa = x + 2 * j * nn * h;
+    const float2* ar = xa + (long long)rem * h;
+    const float2* am = xa + ((long long)mz * n + my) * h;
+    const bool has_b = 2 * j + 1 < batch;
+    float2* crow = c + j * nn * n + (long long)rem * n;
+    for (int kx = lane; kx < n; kx += 32) {
+      float2 A, B = make_float2(0.0f, 0.0f);
+      if (kx == 0 || kx == half) {
+        const float2 p = __ldg(ar + kx), q = __ldg(am + kx);
+        A = make_float2(0.5f * (p.x + q.x), 0.5f * (p.y - q.y));
+        if (has_b) {
+          const float2 s = __ldg(ar + nn * h + kx), t = __ldg(am + nn * h + kx);
+          B = make_float2(0.5f * (s.x + t.x), 0.5f * (s.y - t.y));
+        }
+      } else if (kx < half) {
+        A = __ldg(ar + kx);
+        if (has_b) B = __ldg(ar + nn * h + kx);
+      } else {
+        const float2 p = __ldg(am + (n - kx));
+        A = make_float2(p.x, -p.y);
+        if (has_b) {
+          const float2 s = __ldg(am + nn * h + (n - kx));
+          B = make_float2(s.x, -s.y);
+        }
+      }
+      crow[kx] = make_float2(A.x - B.y, A.y + B.x);  // A + i B
+    }
+  }
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+}  // namespace
+}  // namespace fft3d
+
+extern "C" {
+
+int fft3d_real_plan_create(int n, int batch, int precision, int direction, int norm,
+                           fft3d_real_plan* out_plan) {
+  if (!out_plan) return FFT3D_ERR_NULL_PTR;
+  *out_plan = nullptr;
+  if (batch < 1 || batch > (1 << 24)) return FFT3D_ERR_INVALID_ARG;
+  if (n < 2 || (n & 1) || !fft3d_size_supported(n)) return FFT3D_ERR_UNSUPPORTED_SIZE;
+  const int pairs = (batch + 1) / 2;
+  fft3d_plan inner = nullptr;
+  int rc = fft3d_plan_create(n, n, n, pairs, precision, direction, norm, &inner);
+  if (rc) return rc;
+  auto* p = new fft3d_real_plan_s;
+  p->n = n;
+  p->batch = batch;
+  p->pairs = pairs;
+  p->direction = direction;
+  p->inner = inner;
+  const size_t bytes = (size_t)pairs * n * n * n * sizeof(float2);
+  if (cudaMalloc(&p->d_work, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    fft3d_plan_destroy(inner);
+    delete p;
+    return FFT3D_ERR_ALLOC;
+  }
+  *out_plan = p;
+  return FFT3D_SUCCESS;
+}
+
+int fft3d_real_execute(fft3d_real_plan plan, const void* in, void* out, void* stream) {
+  using namespace fft3d;
+  if (!plan || !in || !out) return FFT3D_ERR_NULL_PTR;
+  if (!aligned16(in) || !aligned16(out)) return FFT3D_ERR_MISALIGNED;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int n = plan->n, batch = plan->batch;
+  const long long q = (long long)n * n * n / 4, total = (long long)plan->pairs * q;
+  const long long rows = (long long)plan->pairs * n * n;
+  if (plan->direction == FFT3D_FORWARD) {
+    pack_pairs_kernel<<<blocks_for(total, kThreads), kThreads, 0, s>>>(
+        static_cast<const float4*>(in), reinterpret_cast<float4*>(plan->d_work), q, batch, total);
+    if (cudaGetLastError() != cudaSuccess) return FFT3D_ERR_CUDA;
+    const int rc = fft3d_execute(plan->inner, plan->d_work, plan->d_work, stream);
+    if (rc) return rc;
+    separate_pairs_kernel<<<blocks_for(rows, kThreads / 32), kThreads, 0, s>>>(
+        plan->d_work, static_cast<float2*>(out), n, batch, rows);
+  } else {
+    rebuild_pairs_kernel<<<blocks_for(rows, kThreads / 32), kThreads, 0, s>>>(
+        static_cast<const float2*>(in), plan->d_work, n, batch, rows);
+    if (cudaGetLastError() != cudaSuccess) return FFT3D_ERR_CUDA;
+    const int rc = fft3d_execute(plan->inner, plan->d_work, plan->d_work, stream);
+    if (rc) return rc;
+    split_pairs_kernel<<<blocks_for(total, kThreads), kThreads, 0, s>>>(
+        reinterpret_cast<const float4*>(plan->d_work), static_cast<float4*>(out), q, batch,
+        total);
+  }
+  return cudaGetLastError() == cudaSuccess ? FFT3D_SUCCESS : FFT3D_ERR_CUDA;
+}
+
+int fft3d_real_get_device_status(fft3d_real_plan plan, void* stream) {
+  if (!plan) return FFT3D_ERR_NULL_PTR;
+  return fft3d_get_device_status(plan->inner, stream);
+}
+
+int fft3d_real_plan_destroy(fft3d_real_plan plan) {
+  if (!plan) return FFT3D_SUCCESS;
+  cudaFree(plan->d_work);
+  const int rc = fft3d_plan_destroy(plan->inner);
+  delete plan;
+  return rc;
+}
+
+}  // extern "C"

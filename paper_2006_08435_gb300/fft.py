@@ -177,6 +177,62 @@ class MixedPlan:
             pass
 
 
+class RealPlan:
+    """A plan for ``batch`` transforms of real n^3 grids.
+
+    Forward: ``execute(x, out)`` with x float32 (batch, n, n, n) and out
+    complex64 (batch, n, n, n // 2 + 1), the half spectrum of Eq. 1.
+    Inverse (``inverse=True``): x is the half spectrum and out the float32
+    grids, the real part of the inverse transform of the Hermitian extension.
+    Two grids share one complex transform inside the library."""
+
+    def __init__(self, n: int, batch: int = 1, precision: str = "fp32", inverse: bool = False,
+                 norm: str = "none"):
+        self.n, self.batch = int(n), int(batch)
+        self.precision, self.inverse, self.norm = precision, bool(inverse), norm
+        h = ctypes.c_void_p()
+        L.check(L.lib().fft3d_real_plan_create(self.n, self.batch, _PREC[precision],
+                                               L.FFT3D_INVERSE if inverse else L.FFT3D_FORWARD,
+                                               _NORM[norm], ctypes.byref(h)),
+                "fft3d_real_plan_create")
+        self._h = h
+
+    def _check(self, t: torch.Tensor, name: str, dtype, points: int) -> None:
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.dtype != dtype or not t.is_contiguous():
+            raise TypeError(f"{name} must be contiguous {dtype}")
+        if t.numel() != points:
+            raise ValueError(f"{name}: expected {points} elements, got {t.numel()}")
+
+    def execute(self, x: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
+        n, b = self.n, self.batch
+        real_pts, half_pts = b * n * n * n, b * n * n * (n // 2 + 1)
+        if self.inverse:
+            self._check(x, "x", torch.complex64, half_pts)
+            self._check(out, "out", torch.float32, real_pts)
+        else:
+            self._check(x, "x", torch.float32, real_pts)
+            self._check(out, "out", torch.complex64, half_pts)
+        L.check(L.lib().fft3d_real_execute(self._h, x.data_ptr(), out.data_ptr(),
+                                           _stream_handle(stream)), "fft3d_real_execute")
+        return out
+
+    def device_status(self, stream=None) -> int:
+        return L.lib().fft3d_real_get_device_status(self._h, _stream_handle(stream))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            L.lib().fft3d_real_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 _plan_cache: dict = {}
 _cache_lock = threading.Lock()
 
@@ -209,6 +265,54 @@ def fft3d(x: torch.Tensor, inverse: bool = False, norm: str = "none", precision:
         return out
     plan = get_plan(nx, ny, nz, batch, precision, inverse, norm, x.device.index)
     return plan.execute(x, out)
+
+
+def _get_real_plan(n, batch, precision, inverse, norm, dev) -> RealPlan:
+    key = ("real", n, batch, precision, bool(inverse), norm, dev)
+    with _cache_lock:
+        p = _plan_cache.get(key)
+        if p is None:
+            with torch.cuda.device(dev):
+                p = RealPlan(n, batch, precision, inverse, norm)
+            _plan_cache[key] = p
+    return p
+
+
+def rfft3d(x: torch.Tensor, norm: str = "none", precision: str = "fp32",
+           out: torch.Tensor | None = None) -> torch.Tensor:
+    """Half spectrum (..., n, n, n // 2 + 1) of the forward transform (Eq. 1)
+    of real float32 CUDA grids (..., n, n, n); leading dims are a batch."""
+    if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype != torch.float32:
+        raise TypeError("x must be a float32 CUDA tensor")
+    if x.dim() < 3 or not (x.shape[-1] == x.shape[-2] == x.shape[-3]):
+        raise ValueError("need cubic (..., n, n, n)")
+    n = x.shape[-1]
+    x = x.contiguous()
+    batch = x.numel() // (n ** 3) if x.numel() else 0
+    if out is None:
+        out = torch.empty(x.shape[:-1] + (n // 2 + 1,), dtype=torch.complex64, device=x.device)
+    if batch == 0:
+        return out
+    return _get_real_plan(n, batch, precision, False, norm, x.device.index).execute(x, out)
+
+
+def irfft3d(x: torch.Tensor, norm: str = "none", precision: str = "fp32",
+            out: torch.Tensor | None = None) -> torch.Tensor:
+    """Real float32 grids (..., n, n, n) from half spectra (..., n, n,
+    n // 2 + 1): the real part of the inverse transform (exponent +1) of the
+    Hermitian extension; ``x`` is not modified."""
+    if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype != torch.complex64:
+        raise TypeError("x must be a complex64 CUDA tensor")
+    if x.dim() < 3 or x.shape[-2] != x.shape[-3] or x.shape[-1] != x.shape[-2] // 2 + 1:
+        raise ValueError("need (..., n, n, n // 2 + 1)")
+    n = x.shape[-2]
+    x = x.contiguous()
+    batch = x.numel() // (n * n * (n // 2 + 1)) if x.numel() else 0
+    if out is None:
+        out = torch.empty(x.shape[:-1] + (n,), dtype=torch.float32, device=x.device)
+    if batch == 0:
+        return out
+    return _get_real_plan(n, batch, precision, True, norm, x.device.index).execute(x, out)
 
 
 class FFT3d(torch.autograd.Function):

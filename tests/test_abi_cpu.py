@@ -166,3 +166,41 @@ def test_tc_operand_table_errors(fft3d_lib):
     assert fft3d_lib.fft3d_tc_operand_table(1, None) == L.FFT3D_ERR_NULL_PTR
     for bad in (0, 4, -1):
         assert fft3d_lib.fft3d_tc_operand_table(bad, buf) == L.FFT3D_ERR_INVALID_ARG
+
+
+def _create_real(lib, *args):
+    h = ctypes.c_void_p(1234)
+    rc = lib.fft3d_real_plan_create(*args, ctypes.byref(h))
+    return rc, h.value
+
+
+@pytest.mark.parametrize("args,code", [
+    ((64, 0, 0, -1, 0), L.FFT3D_ERR_INVALID_ARG),               # batch 0
+    ((64, (1 << 24) + 1, 0, -1, 0), L.FFT3D_ERR_INVALID_ARG),   # batch too large
+    ((64, 2, 7, -1, 0), L.FFT3D_ERR_INVALID_ARG),               # precision
+    ((64, 2, 0, 0, 0), L.FFT3D_ERR_INVALID_ARG),                # direction
+    ((64, 2, 0, 1, 5), L.FFT3D_ERR_INVALID_ARG),                # norm
+    ((15, 2, 0, -1, 0), L.FFT3D_ERR_UNSUPPORTED_SIZE),          # odd edge
+    ((7, 2, 0, -1, 0), L.FFT3D_ERR_UNSUPPORTED_SIZE),
+    ((256, 2, 0, -1, 0), L.FFT3D_ERR_UNSUPPORTED_SIZE),
+    ((32, 2, 1, -1, 0), L.FFT3D_ERR_UNSUPPORTED_PRECISION),     # tensor cores at 64, 128 only
+])
+def test_real_create_validates_before_device(fft3d_lib, args, code):
+    rc, h = _create_real(fft3d_lib, *args)
+    assert rc == code
+    assert h is None
+
+
+def test_real_null_handles(fft3d_lib):
+    assert fft3d_lib.fft3d_real_plan_create(64, 2, 0, -1, 0, None) == L.FFT3D_ERR_NULL_PTR
+    assert fft3d_lib.fft3d_real_execute(None, 16, 16, None) == L.FFT3D_ERR_NULL_PTR
+    assert fft3d_lib.fft3d_real_get_device_status(None, None) == L.FFT3D_ERR_NULL_PTR
+    assert fft3d_lib.fft3d_real_plan_destroy(None) == L.FFT3D_SUCCESS
+
+
+def test_real_valid_args_reach_device_check(fft3d_lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("has a GPU")
+    rc, h = _create_real(fft3d_lib, 64, 3, 0, -1, 0)
+    assert rc == L.FFT3D_ERR_NO_DEVICE and h is None

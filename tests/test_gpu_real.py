@@ -1,0 +1,163 @@
+"""Parity of the real-grid transforms (R2C / C2R, through the C ABI) with the
+FP64 oracle.
+
+Bar, per grid: relative L2 error <= 5e-6 on the FP32 path and <= 1e-5 on the
+split-FP16 path, the tolerances of the complex path (the packing adds a few
+FP32 additions per bin).  Two grids share a complex transform, so each
+check uses grids of like magnitude, except the one that pins the documented
+error of a lopsided pair."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle
+from paper_2006_08435_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 5e-6
+SPLIT_TOL = 1e-5
+FUSED = [16, 32, 48, 64, 80, 96, 128]
+
+
+def real_grids(n, batch, seed):
+    return np.ascontiguousarray(synth.uniform_grids(n, batch, seed=seed).real.astype(np.float32))
+
+
+def half_spectra(n, batch, seed):
+    """Arbitrary complex half spectra, NOT Hermitian in the self-mirrored
+    planes (the inverse must drop those imaginary parts as the oracle does)."""
+    g = synth.uniform_grids((n, n, n // 2 + 1), batch, seed=seed)
+    return np.ascontiguousarray(g)
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def rel(got, ref):
+    return oracle.rel_l2(np.asarray(got, dtype=np.complex128), ref)
+
+
+@pytest.mark.parametrize("n", FUSED)
+@pytest.mark.parametrize("batch", [1, 2, 3])
+def test_forward_every_edge_and_pairing(cuda, n, batch):
+    """Half spectra of every grid, for a lone grid, one pair, and a pair
+    plus a grid whose partner is zero."""
+    from paper_2006_08435_gb300 import rfft3d
+    if n >= 96 and batch == 3:
+        batch = 2
+    r = real_grids(n, batch, seed=10 * n + batch)
+    got = rfft3d(to_dev(r)).cpu().numpy()
+    assert got.shape == (batch, n, n, n // 2 + 1)
+    ref = oracle.rdft3d(r.astype(np.float64))
+    errs = [rel(got[b], ref[b]) for b in range(batch)]
+    assert max(errs) <= FP32_TOL, errs
+
+
+@pytest.mark.parametrize("n", FUSED)
+def test_inverse_arbitrary_half_spectra(cuda, n):
+    """C2R on half spectra that are not exactly Hermitian; the input is left
+    unchanged."""
+    from paper_2006_08435_gb300 import irfft3d
+    batch = 3 if n <= 64 else 2
+    h = half_spectra(n, batch, seed=n + 7)
+    hd = to_dev(h)
+    keep = hd.clone()
+    got = irfft3d(hd).cpu().numpy()
+    assert torch.equal(hd, keep)
+    ref = oracle.irdft3d(h.astype(np.complex128), n)
+    errs = [rel(got[b], ref[b]) for b in range(batch)]
+    assert max(errs) <= FP32_TOL, errs
+
+
+@pytest.mark.parametrize("n", [32, 64])
+def test_density_round_trip_and_norms(cuda, n):
+    """A real density (periodic Gaussians, the plane-wave DFT input):
+    forward, inverse with 1/n^3 gives it back; the norm options scale as
+    stated."""
+    from paper_2006_08435_gb300 import irfft3d, rfft3d
+    rho = np.stack([synth.hartree_density(n, seed=s)[0] for s in (1, 2)]).astype(np.float32)
+    rd = to_dev(rho)
+    f = rfft3d(rd)
+    ref = oracle.rdft3d(rho.astype(np.float64))
+    assert max(rel(f[b].cpu().numpy(), ref[b]) for b in range(2)) <= FP32_TOL
+    back = irfft3d(f, norm="by_n").cpu().numpy()
+    assert rel(back, rho.astype(np.float64)) <= 2 * FP32_TOL
+    fo = rfft3d(rd, norm="ortho").cpu().numpy()
+    assert rel(fo, ref / n ** 1.5) <= FP32_TOL
+    fb = rfft3d(rd, norm="by_n").cpu().numpy()
+    assert rel(fb, ref / n ** 3) <= FP32_TOL
+    bo = irfft3d(to_dev(fo.astype(np.complex64)), norm="ortho").cpu().numpy()
+    assert rel(bo, rho.astype(np.float64)) <= 2 * FP32_TOL
+
+
+@pytest.mark.parametrize("n", [64, 128])
+@pytest.mark.parametrize("precision", ["split_fp16", "split_bf16"])
+def test_tensor_core_precisions(cuda, n, precision):
+    """The complex transform inside may be a tensor-core kind."""
+    from paper_2006_08435_gb300 import irfft3d, rfft3d
+    tol = SPLIT_TOL if precision == "split_fp16" else 2e-4
+    r = real_grids(n, 3, seed=n + 3)
+    got = rfft3d(to_dev(r), precision=precision).cpu().numpy()
+    ref = oracle.rdft3d(r.astype(np.float64))
+    assert max(rel(got[b], ref[b]) for b in range(3)) <= tol
+    h = half_spectra(n, 2, seed=n + 4)
+    gi = irfft3d(to_dev(h), precision=precision).cpu().numpy()
+    ri = oracle.irdft3d(h.astype(np.complex128), n)
+    assert max(rel(gi[b], ri[b]) for b in range(2)) <= tol
+
+
+def test_lopsided_pair_error_is_relative_to_the_pair(cuda):
+    """Grid 1 is 1e3 times grid 0: grid 0's error, measured against the
+    pair's larger norm, stays within the FP32 bar (the documented bound)."""
+    from paper_2006_08435_gb300 import rfft3d
+    n = 32
+    r = real_grids(n, 2, seed=5)
+    r[1] *= 1e3
+    got = rfft3d(to_dev(r)).cpu().numpy().astype(np.complex128)
+    ref = oracle.rdft3d(r.astype(np.float64))
+    err0 = np.linalg.norm(got[0] - ref[0]) / np.linalg.norm(ref[1])
+    assert err0 <= FP32_TOL
+    assert rel(got[1], ref[1]) <= FP32_TOL
+
+
+def test_full_size_sampled(cuda):
+    """128^3 x 32 real grids in the configuration the benchmark times:
+    sampled grids of the forward transform against the oracle, and every
+    grid back through the inverse with 1/n^3."""
+    from paper_2006_08435_gb300 import RealPlan
+    n, batch = 128, 32
+    base = to_dev(real_grids(n, 1, seed=9))
+    scale = 1.0 + 0.05 * torch.arange(batch, device="cuda", dtype=torch.float32)
+    x = (base * scale.view(-1, 1, 1, 1) + 1e-3 * torch.arange(batch, device="cuda").view(-1, 1, 1, 1)).contiguous()
+    fwd = RealPlan(n, batch)
+    y = torch.empty((batch, n, n, n // 2 + 1), dtype=torch.complex64, device="cuda")
+    fwd.execute(x, y)
+    assert fwd.device_status() == 0
+    for b in (0, batch // 2 + 1, batch - 1):
+        ref = oracle.rdft3d(x[b].cpu().numpy().astype(np.float64))
+        assert rel(y[b].cpu().numpy(), ref) <= FP32_TOL
+    inv = RealPlan(n, batch, inverse=True, norm="by_n")
+    back = torch.empty_like(x)
+    inv.execute(y, back)
+    assert inv.device_status() == 0
+    err = (torch.linalg.vector_norm((back - x).reshape(batch, -1), dim=1)
+           / torch.linalg.vector_norm(x.reshape(batch, -1), dim=1))
+    assert float(err.max()) <= 2 * FP32_TOL
+
+
+def test_abi_errors(cuda, fft3d_lib):
+    from paper_2006_08435_gb300 import _lib as L
+    h = ctypes.c_void_p()
+    assert fft3d_lib.fft3d_real_plan_create(32, 2, 0, -1, 0, ctypes.byref(h)) == 0
+    a = torch.zeros(2 * 32 ** 3 + 4, device="cuda")
+    b = torch.zeros(2 * 32 * 32 * 17 + 2, dtype=torch.complex64, device="cuda")
+    assert fft3d_lib.fft3d_real_execute(h, a.data_ptr() + 4, b.data_ptr(), None) == L.FFT3D_ERR_MISALIGNED
+    assert fft3d_lib.fft3d_real_execute(h, a.data_ptr(), b.data_ptr() + 8, None) == L.FFT3D_ERR_MISALIGNED
+    assert fft3d_lib.fft3d_real_execute(h, None, b.data_ptr(), None) == L.FFT3D_ERR_NULL_PTR
+    assert fft3d_lib.fft3d_real_execute(h, a.data_ptr(), b.data_ptr(), None) == 0
+    assert fft3d_lib.fft3d_real_get_device_status(h, None) == 0
+    assert fft3d_lib.fft3d_real_plan_destroy(h) == 0
