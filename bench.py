@@ -60,6 +60,24 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(ms: float, ws: int, device=None) -> float:
+    """The largest of one per-rank duration over all ranks (an all-reduce
+    MAX on the default process group); ws == 1 returns it unchanged."""
+    if ws <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(ws: int, units_per_rank: int, steps: int, ms: float) -> float:
+    """Units per second over the whole job: every rank processes
+    `units_per_rank` units per step, the job takes `ms` (max over ranks)."""
+    return ws * units_per_rank * steps / (ms / 1e3)
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -258,14 +276,10 @@ def run_ours(args, ws, rank, local):
     t_all1.record(stream)
     barrier()
     clk = clocks.stop()
-    total_ms = t_all0.elapsed_time(t_all1)
+    total_ms = max_over_ranks(t_all0.elapsed_time(t_all1), ws, dev)
     launch_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
     ms_per_step = total_ms / args.steps
-    value = ws * batch * args.steps / (total_ms / 1e3)
+    value = whole_job_rate(ws, batch, args.steps, total_ms)
     assert plan.device_status() == 0, "device-side wait timed out"
 
     # end to end through the public API with pinned host buffers
@@ -289,12 +303,8 @@ def run_ours(args, ws, rank, local):
             plan.execute_host(hx, hy, stream)
         e1.record(stream)
         barrier()
-        e2e_ms = e0.elapsed_time(e1) / e_steps
-        if ws > 1:
-            t = torch.tensor([e2e_ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_ms = float(t.item())
-        e2e = {"value": ws * batch / (e2e_ms / 1e3), "unit": "transforms/s",
+        e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e_steps, ws, dev)
+        e2e = {"value": whole_job_rate(ws, batch, 1, e2e_ms), "unit": "transforms/s",
                "h2d_bytes_per_step": hx.numel() * hx.element_size(),
                "d2h_bytes_per_step": hy.numel() * hy.element_size()}
 
@@ -314,9 +324,9 @@ def run_ours(args, ws, rank, local):
             plan16.execute(x, y, stream)
         s1.record(stream)
         barrier()
-        ms16 = s0.elapsed_time(s1) / k16
+        ms16 = max_over_ranks(s0.elapsed_time(s1) / k16, ws, dev)
         assert plan16.device_status() == 0
-        split = {"value": ws * batch / (ms16 / 1e3), "unit": "transforms/s", "steps": k16,
+        split = {"value": whole_job_rate(ws, batch, 1, ms16), "unit": "transforms/s", "steps": k16,
                  "ms_per_step": ms16}
 
     # real grids (the real parts of the same batch): forward R2C to half
@@ -338,9 +348,9 @@ def run_ours(args, ws, rank, local):
             rplan.execute(xr, yr, stream)
         r1.record(stream)
         barrier()
-        msr = r0.elapsed_time(r1) / kr
+        msr = max_over_ranks(r0.elapsed_time(r1) / kr, ws, dev)
         assert rplan.device_status() == 0
-        real = {"value": ws * batch / (msr / 1e3), "unit": "transforms/s", "steps": kr,
+        real = {"value": whole_job_rate(ws, batch, 1, msr), "unit": "transforms/s", "steps": kr,
                 "ms_per_step": msr, "launches_per_step": 3,
                 "bytes_per_transform": 4 * n ** 3 + 8 * n * n * (n // 2 + 1)}
         del xr, yr, rplan
@@ -368,7 +378,9 @@ def run_ours(args, ws, rank, local):
                      "peak_source": f"{peak_kind} hbm_gbs",
                      "kernel": KERNEL_NAMES.get(n, "fused_fft3d_kernel"),
                      "bytes_per_launch": bytes_per_launch,
-                     "avg_launch_ms": avg_launch_ms},
+                     "avg_launch_ms": avg_launch_ms,
+                     "median_launch_ms": statistics.median(launch_ms),
+                     "min_launch_ms": min(launch_ms)},
         "e2e": e2e,
         "gpu_launches": args.steps,
         "clocks": clk,
