@@ -38,114 +38,116 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kMaxBlocks = 152 * 8;
 
-int blocks_for(long long units, int per_block) {
-  const long long b = (units + per_block - 1) / per_block;
-  return (int)(b < 1 ? 1 : (b > kMaxBlocks ? kMaxBlocks : b));
+// Launch shape: the points of a pair along x, at most two pairs along y at a
+// time (a block row loops over the pairs), about kMaxBlocks blocks in all.
+// The separating and rebuilding kernels read every row of a pair twice,
+// directly and as a mirror about half a pair later; with two pairs in flight
+// (34 MB at 128^3) the second read still finds the row in L2.
+dim3 grid_for(long long per_pair, int pairs) {
+  const int by = pairs < 2 ? pairs : 2;
+  long long bx = (per_pair + kThreads - 1) / kThreads;
+  const long long cap = kMaxBlocks / by > 0 ? kMaxBlocks / by : 1;
+  if (bx > cap) bx = cap;
+  return dim3((unsigned)(bx < 1 ? 1 : bx), (unsigned)by);
 }
 
-// c_j = r_{2j} + i r_{2j+1} (0 for a missing partner).  q = n^3 / 4; index i
-// in [0, pairs * q) is pair j = i / q, points 4 e .. 4 e + 3 (e = i - j q).
-// Reads r[2j q + e] (< batch q: 2j <= batch - 1) and, when 2j + 1 < batch,
-// r[(2j + 1) q + e]; writes c[2i], c[2i + 1] (< 2 pairs q float4 = pairs n^3
-// complex points).
-__global__ void pack_pairs_kernel(const float4* __restrict__ r, float4* __restrict__ c,
-                                  long long q, int batch, long long total) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long j = i / q, e = i - j * q;
-    const float4 a = __ldcs(r + 2 * j * q + e);
-    float4 b = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    if (2 * j + 1 < batch) b = __ldcs(r + (2 * j + 1) * q + e);
-    c[2 * i] = make_float4(a.x, b.x, a.y, b.y);
-    c[2 * i + 1] = make_float4(a.z, b.z, a.w, b.w);
-  }
-}
-
-// The inverse of the packing: r_{2j} = Re c_j, r_{2j+1} = Im c_j.
-__global__ void split_pairs_kernel(const float4* __restrict__ c, float4* __restrict__ r,
-                                   long long q, int batch, long long total) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long j = i / q, e = i - j * q;
-    const float4 u = __ldcs(c + 2 * i), v = __ldcs(c + 2 * i + 1);
-    __stcs(r + 2 * j * q + e, make_float4(u.x, u.z, v.x, v.z));
-    if (2 * j + 1 < batch) __stcs(r + (2 * j + 1) * q + e, make_float4(u.y, u.w, v.y, v.w));
-  }
-}
-
-// One warp per row (pair j, kz, ky) of the complex result C_j; the row of
-// -k is (n - kz, n - ky) mod n, column n - kx mod n.  Writes the half rows
-// (h = n/2 + 1 points) of grids 2j and 2j + 1.  Both rows are read through
-// L2 (each row of C_j is read once directly and once as a mirror).
-__global__ void separate_pairs_kernel(const float2* __restrict__ c, float2* __restrict__ out,
-                                      int n, int batch, long long rows) {
-  const int lane = threadIdx.x & 31;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  const int h = n / 2 + 1;
-  const long long nn = (long long)n * n;
-  for (long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < rows;
-       row += nwarps) {
-    const long long j = row / nn;
-    const int rem = (int)(row - j * nn);
-    const int kz = rem / n, ky = rem - kz * n;
-    const int mz = kz ? n - kz : 0, my = ky ? n - ky : 0;
-    const float2* cj = c + j * nn * n;
-    const float2* crow = cj + ((long long)kz * n + ky) * n;
-    const float2* mrow = cj + ((long long)mz * n + my) * n;
-    float2* oa = out + 2 * j * nn * h + (long long)rem * h;
+// c_j = r_{2j} + i r_{2j+1} (0 for a missing partner), 4 points per
+// thread: q = n^3 / 4 float4 per real grid, 2 q per complex grid.  Reads
+// r[2j q + e] (2j <= batch - 1) and, when 2j + 1 < batch, r[(2j + 1) q + e];
+// writes c[2 (j q + e)] and the next float4 (< 2 pairs q).
+__global__ void pack_pairs_kernel(const float4* __restrict__ r, float4* __restrict__ c, int q,
+                                  int batch, int pairs) {
+  for (int j = blockIdx.y; j < pairs; j += gridDim.y) {
+    const float4* ra = r + 2LL * j * q;
     const bool has_b = 2 * j + 1 < batch;
-    for (int kx = lane; kx < h; kx += 32) {
-      const float2 C = __ldg(crow + kx);
-      const float2 M = __ldg(mrow + (kx ? n - kx : 0));  // C(-k)
-      oa[kx] = make_float2(0.5f * (C.x + M.x), 0.5f * (C.y - M.y));
-      if (has_b) oa[nn * h + kx] = make_float2(0.5f * (C.y + M.y), 0.5f * (M.x - C.x));
+    float4* cj = c + 2LL * j * q;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < q; e += gridDim.x * blockDim.x) {
+      const float4 a = __ldcs(ra + e);
+      float4 b = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      if (has_b) b = __ldcs(ra + q + e);
+      cj[2 * e] = make_float4(a.x, b.x, a.y, b.y);
+      cj[2 * e + 1] = make_float4(a.z, b.z, a.w, b.w);
     }
   }
 }
 
-// One warp per row (pair j, kz, ky) of the full spectrum H(A) + i H(B),
-// A = X_{2j}, B = X_{2j+1} (0 when missing).  Columns kx < n/2 but 0 come
+// The inverse of the packing: r_{2j} = Re c_j, r_{2j+1} = Im c_j.
+__global__ void split_pairs_kernel(const float4* __restrict__ c, float4* __restrict__ r, int q,
+                                   int batch, int pairs) {
+  for (int j = blockIdx.y; j < pairs; j += gridDim.y) {
+    const float4* cj = c + 2LL * j * q;
+    float4* ra = r + 2LL * j * q;
+    const bool has_b = 2 * j + 1 < batch;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < q; e += gridDim.x * blockDim.x) {
+      const float4 u = __ldcs(cj + 2 * e), v = __ldcs(cj + 2 * e + 1);
+      __stcs(ra + e, make_float4(u.x, u.z, v.x, v.z));
+      if (has_b) __stcs(ra + q + e, make_float4(u.y, u.w, v.y, v.w));
+    }
+  }
+}
+
+// Half spectra of grids 2j and 2j + 1 from C_j: point i = (kz n + ky) h + kx
+// of the half layout (h = n/2 + 1; contiguous writes), read from C_j at
+// (kz, ky, kx) and at -k = ((n - kz) mod n, (n - ky) mod n, (n - kx) mod n).
+// A pair's C_j (n^3 points, 16.8 MB at 128^3) is read through L2: every row
+// is read once directly and once as a mirror while the pair is in flight.
+__global__ void separate_pairs_kernel(const float2* __restrict__ c, float2* __restrict__ out,
+                                      int n, int batch, int pairs) {
+  const int h = n / 2 + 1, m = n * n * h;
+  for (int j = blockIdx.y; j < pairs; j += gridDim.y) {
+    const float2* cj = c + (long long)j * n * n * n;
+    float2* oa = out + 2LL * j * m;
+    const bool has_b = 2 * j + 1 < batch;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+      const int row = i / h, kx = i - row * h;
+      const int kz = row / n, ky = row - kz * n;
+      const int mz = kz ? n - kz : 0, my = ky ? n - ky : 0;
+      const float2 C = __ldg(cj + row * n + kx);
+      const float2 M = __ldg(cj + (mz * n + my) * n + (kx ? n - kx : 0));  // C(-k)
+      oa[i] = make_float2(0.5f * (C.x + M.x), 0.5f * (C.y - M.y));
+      if (has_b) oa[m + i] = make_float2(0.5f * (C.y + M.y), 0.5f * (M.x - C.x));
+    }
+  }
+}
+
+// Full spectrum H(A) + i H(B) of pair j, A = X_{2j}, B = X_{2j+1} (0 when
+// missing), point i = (kz n + ky) n + kx.  Columns kx < n/2 but 0 come
 // straight from the half rows, kx > n/2 from conj of the mirrored row at
 // column n - kx (in 1 .. n/2 - 1), and the self-mirrored columns 0 and n/2
 // are the mean of the bin and the conjugate of its mirror.
 __global__ void rebuild_pairs_kernel(const float2* __restrict__ x, float2* __restrict__ c,
-                                     int n, int batch, long long rows) {
-  const int lane = threadIdx.x & 31;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  const int h = n / 2 + 1, half = n / 2;
-  const long long nn = (long long)n * n;
-  for (long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < rows;
-       row += nwarps) {
-    const long long j = row / nn;
-    const int rem = (int)(row - j * nn);
-    const int kz = rem / n, ky = rem - kz * n;
-    const int mz = kz ? n - kz : 0, my = ky ? n - ky : 0;
-    const float2* xa = x + 2 * j * nn * h;
-    const float2* ar = xa + (long long)rem * h;
-    const float2* am = xa + ((long long)mz * n + my) * h;
+                                     int n, int batch, int pairs) {
+  const int h = n / 2 + 1, half = n / 2, m = n * n * h, nf = n * n * n;
+  for (int j = blockIdx.y; j < pairs; j += gridDim.y) {
+    const float2* xa = x + 2LL * j * m;
     const bool has_b = 2 * j + 1 < batch;
-    float2* crow = c + j * nn * n + (long long)rem * n;
-    for (int kx = lane; kx < n; kx += 32) {
+    float2* cj = c + (long long)j * nf;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += gridDim.x * blockDim.x) {
+      const int row = i / n, kx = i - row * n;
+      const int kz = row / n, ky = row - kz * n;
+      const int mz = kz ? n - kz : 0, my = ky ? n - ky : 0;
+      const float2* ar = xa + row * h;
+      const float2* am = xa + (mz * n + my) * h;
       float2 A, B = make_float2(0.0f, 0.0f);
       if (kx == 0 || kx == half) {
         const float2 p = __ldg(ar + kx), q = __ldg(am + kx);
         A = make_float2(0.5f * (p.x + q.x), 0.5f * (p.y - q.y));
         if (has_b) {
-          const float2 s = __ldg(ar + nn * h + kx), t = __ldg(am + nn * h + kx);
+          const float2 s = __ldg(ar + m + kx), t = __ldg(am + m + kx);
           B = make_float2(0.5f * (s.x + t.x), 0.5f * (s.y - t.y));
         }
       } else if (kx < half) {
         A = __ldg(ar + kx);
-        if (has_b) B = __ldg(ar + nn * h + kx);
+        if (has_b) B = __ldg(ar + m + kx);
       } else {
         const float2 p = __ldg(am + (n - kx));
         A = make_float2(p.x, -p.y);
         if (has_b) {
-          const float2 s = __ldg(am + nn * h + (n - kx));
+          const float2 s = __ldg(am + m + (n - kx));
           B = make_float2(s.x, -s.y);
         }
       }
-      crow[kx] = make_float2(A.x - B.y, A.y + B.x);  // A + i B
+      cj[i] = make_float2(A.x - B.y, A.y + B.x);  // A + i B
     }
   }
 }
@@ -189,26 +191,25 @@ int fft3d_real_execute(fft3d_real_plan plan, const void* in, void* out, void* st
   if (!plan || !in || !out) return FFT3D_ERR_NULL_PTR;
   if (!aligned16(in) || !aligned16(out)) return FFT3D_ERR_MISALIGNED;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int n = plan->n, batch = plan->batch;
-  const long long q = (long long)n * n * n / 4, total = (long long)plan->pairs * q;
-  const long long rows = (long long)plan->pairs * n * n;
+  const int n = plan->n, batch = plan->batch, pairs = plan->pairs;
+  const int q = n * n * n / 4, h = n / 2 + 1;
   if (plan->direction == FFT3D_FORWARD) {
-    pack_pairs_kernel<<<blocks_for(total, kThreads), kThreads, 0, s>>>(
-        static_cast<const float4*>(in), reinterpret_cast<float4*>(plan->d_work), q, batch, total);
+    pack_pairs_kernel<<<grid_for(q, pairs), kThreads, 0, s>>>(
+        static_cast<const float4*>(in), reinterpret_cast<float4*>(plan->d_work), q, batch, pairs);
     if (cudaGetLastError() != cudaSuccess) return FFT3D_ERR_CUDA;
     const int rc = fft3d_execute(plan->inner, plan->d_work, plan->d_work, stream);
     if (rc) return rc;
-    separate_pairs_kernel<<<blocks_for(rows, kThreads / 32), kThreads, 0, s>>>(
-        plan->d_work, static_cast<float2*>(out), n, batch, rows);
+    separate_pairs_kernel<<<grid_for((long long)n * n * h, pairs), kThreads, 0, s>>>(
+        plan->d_work, static_cast<float2*>(out), n, batch, pairs);
   } else {
-    rebuild_pairs_kernel<<<blocks_for(rows, kThreads / 32), kThreads, 0, s>>>(
-        static_cast<const float2*>(in), plan->d_work, n, batch, rows);
+    rebuild_pairs_kernel<<<grid_for((long long)n * n * n, pairs), kThreads, 0, s>>>(
+        static_cast<const float2*>(in), plan->d_work, n, batch, pairs);
     if (cudaGetLastError() != cudaSuccess) return FFT3D_ERR_CUDA;
     const int rc = fft3d_execute(plan->inner, plan->d_work, plan->d_work, stream);
     if (rc) return rc;
-    split_pairs_kernel<<<blocks_for(total, kThreads), kThreads, 0, s>>>(
+    split_pairs_kernel<<<grid_for(q, pairs), kThreads, 0, s>>>(
         reinterpret_cast<const float4*>(plan->d_work), static_cast<float4*>(out), q, batch,
-        total);
+        pairs);
   }
   return cudaGetLastError() == cudaSuccess ? FFT3D_SUCCESS : FFT3D_ERR_CUDA;
 }
