@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <new>
 
 #include "fft3d.h"
 
@@ -169,7 +170,11 @@ int fft3d_real_plan_create(int n, int batch, int precision, int direction, int n
   fft3d_plan inner = nullptr;
   int rc = fft3d_plan_create(n, n, n, pairs, precision, direction, norm, &inner);
   if (rc) return rc;
-  auto* p = new fft3d_real_plan_s;
+  auto* p = new (std::nothrow) fft3d_real_plan_s();
+  if (!p) {
+    fft3d_plan_destroy(inner);
+    return FFT3D_ERR_ALLOC;
+  }
   p->n = n;
   p->batch = batch;
   p->pairs = pairs;
