@@ -97,6 +97,30 @@ int fft3d_size_supported(int n);
 int fft3d_twiddle_table(int n, float* out, int* l1, int* l2);
 
 /*
+ * Host-only view of the planner's ticket schedule (needs no GPU): the order
+ * in which the persistent kernels hand out work items.  Each grid g of
+ * edge dims[g] has a plane phase (x and y; planes or half-planes) and a slab
+ * phase (z); each phase is one block of `phase_items` consecutive tickets
+ * (dims[g] tickets when phase_items is 0).  Grids are taken largest edge
+ * first; a grid's slab block follows its plane block once `concurrency`
+ * more tickets have been emitted (the items resident at once), or earlier
+ * when the intermediates of the grids whose planes are done but whose slabs
+ * are not yet scheduled would exceed `l2_budget_bytes` (8 n^3 bytes each).
+ * A slab item waits only on plane items of its own grid, which hold smaller
+ * tickets, so the schedule cannot deadlock.  Plans call this with
+ * concurrency = resident blocks x items in flight per block and 40% of L2.
+ *   count      : 1 .. FFT3D_MAX_MIXED_GRIDS grids; dims: HOST array, 1..1024.
+ *   max_blocks : capacity of grid/phase/start (>= 2 * count).
+ *   grid, phase, start : HOST arrays receiving block i's grid, phase (0
+ *                plane, 1 slab) and first ticket; *nblocks = 2 * count;
+ *                *total_items = tickets in all.
+ * Errors: FFT3D_ERR_NULL_PTR, FFT3D_ERR_INVALID_ARG.
+ */
+int fft3d_schedule_preview(int count, const int* dims, int concurrency, double l2_budget_bytes,
+                           int phase_items, int max_blocks, int* grid, int* phase, int* start,
+                           int* nblocks, int* total_items);
+
+/*
  * Host-only view of the B operands of the tcgen05 tensor-core kernels
  * (variant 9; needs no GPU).  For k1 = 0..3, the 32 x 32 real form of the
  * complex 16 x 16 matrix M_k1[n2][k2] = W_64^(n2 (k1 + 4 k2)) (forward root,

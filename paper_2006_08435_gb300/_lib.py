@@ -57,6 +57,9 @@ _SIGS = {
     "fft3d_autotune": (_I, [_I, _I, _I, _I, ctypes.c_char_p, ctypes.POINTER(_I)]),
     "fft3d_autotune_mixed": (_I, [_I, ctypes.POINTER(_I), _I, ctypes.c_char_p, ctypes.POINTER(_I)]),
     "fft3d_complex_to_real": (_I, [_VP, _VP, ctypes.c_int64, _VP]),
+    "fft3d_schedule_preview": (_I, [_I, ctypes.POINTER(_I), _I, ctypes.c_double, _I, _I,
+                                   ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                                   ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "fft3d_real_plan_create": (_I, [_I, _I, _I, _I, _I, ctypes.POINTER(_VP)]),
     "fft3d_real_execute": (_I, [_VP, _VP, _VP, _VP]),
     "fft3d_real_get_device_status": (_I, [_VP, _VP]),

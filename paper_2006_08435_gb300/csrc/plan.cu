@@ -312,6 +312,15 @@ std::vector<SchedBlock> build_schedule(const std::vector<int>& dims, const std::
   return blocks;
 }
 
+// The order in which a unit's grids are scheduled: largest edge first,
+// ties in grid order.
+std::vector<int> schedule_order(const std::vector<int>& dims) {
+  std::vector<int> order(dims.size());
+  for (size_t l = 0; l < dims.size(); ++l) order[l] = (int)l;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return dims[a] > dims[b]; });
+  return order;
+}
+
 template <class T>
 int upload(T** dst, const T* src, size_t count) {
   if (cudaMalloc(dst, sizeof(T) * count) != cudaSuccess) {
@@ -367,12 +376,9 @@ int finish_unit(fft3d_plan p, Unit& u, bool identity) {
     }
     cluster_blocks = std::min(clusters, m) * u.kernel.cluster;
   }
-  std::vector<int> ldims(m), order(m);
-  for (int l = 0; l < m; ++l) {
-    ldims[l] = p->dims[u.grids[l]];
-    order[l] = l;
-  }
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ldims[a] > ldims[b]; });
+  std::vector<int> ldims(m);
+  for (int l = 0; l < m; ++l) ldims[l] = p->dims[u.grids[l]];
+  const std::vector<int> order = schedule_order(ldims);
   const int resident = per_sm * sms;
   int total_items = 0;
   const std::vector<SchedBlock> blocks = build_schedule(
@@ -757,6 +763,29 @@ int fft3d_twiddle_table(int n, float* out, int* l1, int* l2) {
   twiddle_table(n, split_l1(n), out);
   *l1 = split_l1(n);
   *l2 = split_l2(n);
+  return FFT3D_SUCCESS;
+}
+
+int fft3d_schedule_preview(int count, const int* dims, int concurrency, double l2_budget_bytes,
+                           int phase_items, int max_blocks, int* grid, int* phase, int* start,
+                           int* nblocks, int* total_items) {
+  if (!dims || !grid || !phase || !start || !nblocks || !total_items) return FFT3D_ERR_NULL_PTR;
+  if (count < 1 || count > FFT3D_MAX_MIXED_GRIDS || concurrency < 0 || phase_items < 0 ||
+      !(l2_budget_bytes >= 0.0) || max_blocks < 2 * count)
+    return FFT3D_ERR_INVALID_ARG;
+  std::vector<int> d(dims, dims + count);
+  for (int e : d)
+    if (e < 1 || e > 1024) return FFT3D_ERR_INVALID_ARG;
+  int total = 0;
+  const std::vector<SchedBlock> blocks =
+      build_schedule(d, schedule_order(d), concurrency, l2_budget_bytes, phase_items, &total);
+  for (size_t i = 0; i < blocks.size(); ++i) {
+    grid[i] = blocks[i].grid;
+    phase[i] = blocks[i].phase;
+    start[i] = blocks[i].start;
+  }
+  *nblocks = (int)blocks.size();
+  *total_items = total;
   return FFT3D_SUCCESS;
 }
 
