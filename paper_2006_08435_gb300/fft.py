@@ -6,6 +6,7 @@ the library's sm_103a kernels.  PyTorch supplies device memory and streams.
 """
 from __future__ import annotations
 
+import collections
 import ctypes
 import threading
 
@@ -267,14 +268,26 @@ def fft3d(x: torch.Tensor, inverse: bool = False, norm: str = "none", precision:
     return plan.execute(x, out)
 
 
+# Real plans own a workspace of ceil(batch/2) n^3 complex points (268 MB at
+# 128^3 x 32), so only the most recently used few are kept; an evicted
+# plan's memory is freed (cudaFree waits for work still using it).
+_REAL_CACHE_MAX = 4
+_real_cache: "collections.OrderedDict" = collections.OrderedDict()
+
+
 def _get_real_plan(n, batch, precision, inverse, norm, dev) -> RealPlan:
-    key = ("real", n, batch, precision, bool(inverse), norm, dev)
+    key = (n, batch, precision, bool(inverse), norm, dev)
     with _cache_lock:
-        p = _plan_cache.get(key)
-        if p is None:
-            with torch.cuda.device(dev):
-                p = RealPlan(n, batch, precision, inverse, norm)
-            _plan_cache[key] = p
+        p = _real_cache.get(key)
+        if p is not None:
+            _real_cache.move_to_end(key)
+            return p
+        with torch.cuda.device(dev):
+            p = RealPlan(n, batch, precision, inverse, norm)
+        _real_cache[key] = p
+        while len(_real_cache) > _REAL_CACHE_MAX:
+            _, old = _real_cache.popitem(last=False)
+            old.close()
     return p
 
 
