@@ -381,8 +381,8 @@ int fft3d_real_plan_create(int n, int batch, int precision, int direction, int n
  * Transform every grid of the plan.  `in` and `out` are DEVICE pointers,
  * 16-byte aligned, not overlapping (forward: in = real grids, out = half
  * spectra; inverse: the other way round).  Asynchronous on `stream`,
- * allocates nothing, capturable in a CUDA graph (three kernels and the
- * complex plan's launch).  A plan may run on one stream at a time.
+ * allocates nothing, capturable in a CUDA graph (a packing or rebuilding
+ * kernel, the complex plan's launch, a separating or splitting kernel).  A plan may run on one stream at a time.
  */
 int fft3d_real_execute(fft3d_real_plan plan, const void* in, void* out, void* stream);
 
