@@ -36,3 +36,16 @@ def test_lru_bound_and_reuse(monkeypatch):
     get(32, 1, "fp32", True, "by_n", 0)
     assert _FakePlan.closed[-1] == (64, 4, "fp32", False, "none")
     assert len(_FakePlan.made) == 2 + fft._REAL_CACHE_MAX
+
+
+def test_binding_rejects_host_tensors_and_wrong_dtypes():
+    """The real-grid helpers check their arguments before any library call
+    (so these run without a GPU)."""
+    import pytest
+    import torch
+    with pytest.raises(TypeError):
+        fft.rfft3d(torch.zeros(2, 8, 8, 8))                       # host tensor
+    with pytest.raises(TypeError):
+        fft.irfft3d(torch.zeros(2, 8, 8, 5, dtype=torch.complex64))
+    with pytest.raises(TypeError):
+        fft.rfft3d(torch.zeros(2, 8, 8, 8, dtype=torch.complex64))  # not real
