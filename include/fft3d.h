@@ -19,7 +19,13 @@
  *
  * Pointers: `in`/`out` are DEVICE pointers owned by the caller, 16-byte
  * aligned, valid for the whole grid set.  `in == out` (in place) is allowed;
- * other overlaps are not.  A plan owns the device memory it allocates at
+ * other overlaps are not.  Known limitation: the 128^3 split-y kernels
+ * (FP32 variant 6, tensor-core variant 9, the defaults from 4 grids) split
+ * each plane into two half-plane items, the even rows' item writing output
+ * rows 0..63 while the odd rows' item still has to read rows 1..63; in place
+ * this relies on the second item's tensor copy landing before the first
+ * item's stores (several microseconds apart in the schedule; never seen to
+ * fail in the tests, but not enforced).  Out of place is unaffected.  A plan owns the device memory it allocates at
  * create (twiddle tables, schedule, work counters, status word) and frees it
  * at destroy.  `stream` is a cudaStream_t passed as void* (NULL = legacy
  * default stream).
