@@ -19,13 +19,9 @@
  *
  * Pointers: `in`/`out` are DEVICE pointers owned by the caller, 16-byte
  * aligned, valid for the whole grid set.  `in == out` (in place) is allowed;
- * other overlaps are not.  Known limitation: the 128^3 split-y kernels
- * (FP32 variant 6, tensor-core variant 9, the defaults from 4 grids) split
- * each plane into two half-plane items, the even rows' item writing output
- * rows 0..63 while the odd rows' item still has to read rows 1..63; in place
- * this relies on the second item's tensor copy landing before the first
- * item's stores (several microseconds apart in the schedule; never seen to
- * fail in the tests, but not enforced).  Out of place is unaffected.  A plan owns the device memory it allocates at
+ * other overlaps are not.  (Kernels whose work items cover part of a plane,
+ * such as the 128^3 half-plane items, order an item's stores after the
+ * loads of the items that read the same rows.)  A plan owns the device memory it allocates at
  * create (twiddle tables, schedule, work counters, status word) and frees it
  * at destroy.  `stream` is a cudaStream_t passed as void* (NULL = legacy
  * default stream).
@@ -419,16 +415,30 @@ int fft3d_real_plan_destroy(fft3d_real_plan plan);
  *   batch     : 1 .. FFT3D_NOALLOC_MAX_BATCH grids; larger batches return
  *               FFT3D_ERR_EXCEEDS_STATIC_SCRATCH.
  *   direction, norm, in, out, stream : as for fft3d_plan_create/execute.
- * The first call on a device looks up the array's device address (and the
- * kernel's occupancy) with that device current; make that first call before
- * any stream capture.  Every call on a device shares the one array and
- * rewrites it (counters and status are cleared at the start of each call),
- * so calls whose work overlaps on the GPU -- on different streams, or from
- * different host threads -- race.  Host threads are serialised inside the
- * call.  A bounded wait that times out inside such a call is not reported.
+ * Each call enqueues two kernels on `stream`: a set-up kernel that clears
+ * the counters and the status word and writes the schedule and twiddle
+ * table (computed on the host, passed as kernel parameters), then the
+ * transform; nothing is copied between host and device.  The first call on
+ * a device looks up the array's device address (and the kernel's
+ * occupancy) with that device current; make that first call before any
+ * stream capture.  Every call on a device shares the one array and rewrites
+ * it, so calls whose work overlaps on the GPU -- on different streams, or
+ * from different host threads -- race.  Host threads are serialised inside
+ * the call.  A bounded wait that times out is recorded in the array's
+ * status word; fft3d_noalloc_get_device_status reads it.
  */
 int fft3d_execute_noalloc(int n, int batch, int direction, int norm,
                           const void* in, void* out, void* stream);
+
+/*
+ * Status of the last fft3d_execute_noalloc call on the current device:
+ * synchronises `stream` (the stream of that call), then reads and clears the
+ * status word in the library's device array.  Returns FFT3D_SUCCESS (also
+ * when no call has run on this device), FFT3D_ERR_DEVICE_TIMEOUT (a bounded
+ * inter-block wait ran out; that call's outputs are undefined) or
+ * FFT3D_ERR_CUDA.  Allocates nothing.
+ */
+int fft3d_noalloc_get_device_status(void* stream);
 
 #ifdef __cplusplus
 }

@@ -138,6 +138,33 @@ __device__ __forceinline__ void pair_radix2(float2* v, int p, int xm, Store stor
   });
 }
 
+// In place, the two half-planes of a plane overlap: the even rows' item
+// writes output rows 0..63, among them the odd rows 1..63 that its partner
+// (the odd rows' item) reads, and the partner writes rows 64..127, among
+// them the even rows 64..126 that the first item reads.  The two are the
+// consecutive tickets 2 m and 2 m + 1 of one ticket pair (a phase has an
+// even number of items and starts at an even ticket), so they are the
+// adjacent items k and k ^ 1 of the same block, taken by the two compute
+// groups.  Before its y stores an item waits until the partner's tile has
+// landed, after which the partner reads nothing more from global memory.
+// The wait cannot match a stale phase: the partner's (group, tile) barrier
+// is next reused by item (k ^ 1) + 6, which needs the tile freed by item
+// (k ^ 1) + 3, which follows this item in its own group's order; and the
+// use before it, item (k ^ 1) - 6, completed before the tile was reloaded
+// for (k ^ 1) - 3 < k.  The fence orders the partner's tensor-copy reads
+// (async proxy) before this item's stores (generic proxy).
+template <int N>
+__device__ __forceinline__ bool partner_loaded(int k, const Desc& d, unsigned long long* full,
+                                               const FusedArgs& a) {
+  using K = Cfg<N>;
+  const int kp = (d.idx & 1) ? k - 1 : k + 1;
+  if (!warp_wait(&full[rowk::full_idx<K::NTILE, K::GROUPS>(kp)],
+                 rowk::full_par<K::NTILE, K::GROUPS>(kp), a))
+    return false;
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+  return true;
+}
+
 // ------------------------------------------------------------- producer
 // Lanes 0..7 issue the tensor boxes; lane 0 takes and resolves tickets
 // (pairs, one pair ahead).  Tensors are [N * batch][N][2N] floats.
@@ -409,6 +436,10 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
             constexpr int k2 = decltype(K)::value;
             v[k2] = twc<k2, 128, DIR>(v[k2]);
           });
+        if (a.in == a.out && !sy::partner_loaded<N>(k, d, full, a)) {
+          fail = true;
+          break;
+        }
         // the intermediate: kept in L2 until its slabs have read it
         const unsigned long long keep = policy_evict_last();
         float2* dst = gout + (long long)(d.idx >> 1) * NN + (long long)par * H * N + gt;

@@ -189,6 +189,12 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
             constexpr int k2 = decltype(K2)::value;
             v[k2] = twc<k2, 128, DIR>(v[k2]);
           });
+        // in place: the partner half-plane's tile has landed (a group-wide
+        // decision, so that no thread is left at a later barrier)
+        if (a.in == a.out && !group_and(1 + g, K::GT, sy::partner_loaded<N>(k, d, full, a))) {
+          fail = true;
+          break;
+        }
         // the intermediate: kept in L2 until its slabs have read it
         const unsigned long long keep = policy_evict_last();
         float2* dst = gout + (long long)(d.idx >> 1) * NN + (long long)par * H * N + gt;
