@@ -45,6 +45,7 @@ _SIGS = {
     "fft3d_error_string": (ctypes.c_char_p, [_I]),
     "fft3d_selftest_wait_timeout": (_I, [ctypes.c_int64]),
     "fft3d_execute_noalloc": (_I, [_I, _I, _I, _I, _VP, _VP, _VP]),
+    "fft3d_noalloc_get_device_status": (_I, [_VP]),
     "fft3d_hartree_workspace_bytes": (ctypes.c_size_t, [_I, _I]),
     "fft3d_hartree_energy": (_I, [_VP, _I, _I, ctypes.c_double, _VP, _VP, ctypes.c_size_t, _VP]),
     "fft3d_hartree_seed": (_I, [_VP, _I, _I, ctypes.c_double, _VP, _VP, _VP]),

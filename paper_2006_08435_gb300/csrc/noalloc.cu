@@ -12,16 +12,21 @@
 // loads this library holds until the process exits.
 //
 // The kernels are the same ones the planned path launches; only where their
-// scratch lives differs.
+// scratch lives differs.  A call enqueues two kernels and nothing else: a
+// set-up kernel that clears the counters and the status word and writes the
+// schedule and the twiddle table into the array (both computed on the host
+// and handed over as kernel parameters), then the transform.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 #include <mutex>
 
 #include "fft3d.h"
 #include "internal.h"
+#include "schedule.h"
 #include "sizes.h"
 
 namespace fft3d {
@@ -46,46 +51,59 @@ struct DeviceState {
 DeviceState g_dev[kMaxDevices];
 std::mutex g_mu;
 
-// Host staging for the schedule and the twiddles; copied to the device array
-// with cudaMemcpyAsync from pageable memory, which returns once the bytes
-// are staged, so the buffers can be reused by the next call.
+// Host storage of the schedule builder (shared with the planner), reused by
+// every call under g_mu.
 SchedBlock g_host_blocks[2 * FFT3D_NOALLOC_MAX_BATCH];
+int g_dims[FFT3D_NOALLOC_MAX_BATCH];
+int g_order[FFT3D_NOALLOC_MAX_BATCH];
 int g_plane_end[FFT3D_NOALLOC_MAX_BATCH];
-float g_host_tw[2 * 128];
 
-// The planner's ticket order for `batch` grids of edge n, written without
-// heap storage: plane blocks grid after grid; grid g's slab block once
-// `concurrency` more tickets have been handed out after its last plane
-// ticket, or earlier when the grids still waiting for their slabs would
-// exceed `l2_budget` bytes.  Grids leave that waiting set in FIFO order, so
-// it is the index range [head, next).  Returns the number of blocks.
-int uniform_schedule(int n, int batch, int concurrency, double l2_budget, SchedBlock* out,
-                     int* total_items) {
-  const double bytes = 8.0 * n * n * n;
-  int start = 0, nb = 0, head = 0;
-  double pending = 0.0;
-  auto emit = [&](int g, int phase) {
-    out[nb++] = SchedBlock{g, phase, start, n};
-    start += n;
-  };
-  auto flush = [&](int next, bool force_one) {
-    while (head < next) {
-      if (start - g_plane_end[head] < concurrency && !force_one) break;
-      force_one = false;
-      pending -= bytes;
-      emit(head++, 1);
+// What the set-up kernel writes.  A uniform batch's schedule is fixed by
+// the phase of each block: plane blocks come in grid order, slab blocks in
+// grid order too (a grid's slabs follow its planes, first in, first out),
+// and every block is n tickets.  So block i is grid "number of blocks of
+// its phase before i" and starts at ticket i * n; bit i of `phase` holds
+// its phase.
+constexpr int kPhaseWords = 2 * FFT3D_NOALLOC_MAX_BATCH / 32;
+struct SetupArgs {
+  unsigned phase[kPhaseWords];
+  float2 tw[128];
+  int n, batch, nblocks;
+  unsigned work_words;  // ticket counter and per-grid plane counters
+  size_t off_work, off_blocks, off_tw;
+};
+
+// One block of kPhaseWords threads: thread t expands the 32 blocks of word
+// t (an exclusive prefix count of slab bits over the words gives the grid
+// numbers), copies twiddles, and clears the counters and the status word.
+__global__ void __launch_bounds__(kPhaseWords) noalloc_setup_kernel(const SetupArgs s) {
+  __shared__ int before[kPhaseWords];
+  const int t = threadIdx.x;
+  const unsigned w = s.phase[t];
+  before[t] = __popc(w);
+  __syncthreads();
+  if (t == 0) {
+    int acc = 0;
+    for (int i = 0; i < kPhaseWords; ++i) {
+      const int c = before[i];
+      before[i] = acc;
+      acc += c;
     }
-  };
-  for (int g = 0; g < batch; ++g) {
-    while (head < g && pending + bytes > l2_budget) flush(g, true);
-    emit(g, 0);
-    g_plane_end[g] = start;
-    pending += bytes;
-    flush(g + 1, false);
   }
-  while (head < batch) flush(batch, true);
-  *total_items = start;
-  return nb;
+  __syncthreads();
+  SchedBlock* blocks = reinterpret_cast<SchedBlock*>(g_noalloc_scratch + s.off_blocks);
+  for (int j = 0; j < 32; ++j) {
+    const int i = 32 * t + j;
+    if (i >= s.nblocks) break;
+    const int slabs_before = before[t] + __popc(w & ((1u << j) - 1u));
+    const int phase = (w >> j) & 1u;
+    blocks[i] = SchedBlock{phase ? slabs_before : i - slabs_before, phase, i * s.n, s.n};
+  }
+  float2* tw = reinterpret_cast<float2*>(g_noalloc_scratch + s.off_tw);
+  for (int i = t; i < s.n; i += blockDim.x) tw[i] = s.tw[i];
+  unsigned* work = reinterpret_cast<unsigned*>(g_noalloc_scratch + s.off_work);
+  for (unsigned i = t; i < s.work_words; i += blockDim.x) work[i] = 0u;
+  if (t == 0) *reinterpret_cast<unsigned*>(g_noalloc_scratch) = kStatusOk;
 }
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -163,24 +181,35 @@ extern "C" int fft3d_execute_noalloc(int n, int batch, int direction, int norm, 
   }
   const int resident = st.per_sm[di][si] * st.sms;
 
-  // schedule and twiddles (FP64 host values rounded to FP32), as a plan does
+  // schedule (the planner's builder) and twiddles (FP64 host values rounded
+  // to FP32), as a plan computes them, handed to the set-up kernel by value
+  static SetupArgs su;  // under g_mu; copied into the launch
+  for (int g = 0; g < batch; ++g) {
+    g_dims[g] = n;
+    g_order[g] = g;  // equal edges: the planner's largest-first order is the grid order
+  }
   int total_items = 0;
-  const int nblocks = uniform_schedule(n, batch, resident * k.items_in_flight, 0.4 * (double)st.l2,
-                                       g_host_blocks, &total_items);
+  const int nblocks = schedule_blocks(batch, g_dims, g_order, resident * k.items_in_flight,
+                                      0.4 * (double)st.l2, 0, g_plane_end, g_host_blocks,
+                                      &total_items);
+  std::memset(su.phase, 0, sizeof(su.phase));
+  for (int i = 0; i < nblocks; ++i)
+    if (g_host_blocks[i].phase) su.phase[i >> 5] |= 1u << (i & 31);
   int l1 = 0, l2 = 0;
-  if (fft3d_twiddle_table(n, g_host_tw, &l1, &l2) != FFT3D_SUCCESS) return FFT3D_ERR_CUDA;
+  if (fft3d_twiddle_table(n, reinterpret_cast<float*>(su.tw), &l1, &l2) != FFT3D_SUCCESS)
+    return FFT3D_ERR_CUDA;
+  su.n = n;
+  su.batch = batch;
+  su.nblocks = nblocks;
+  su.work_words = (unsigned)(1 + batch);
+  su.off_work = off_work;
+  su.off_blocks = off_blocks;
+  su.off_tw = off_tw;
 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   unsigned char* base = st.base;
-  // the counters and the status word must start at zero on every call
-  if (cudaMemsetAsync(base, 0, off_blocks, s) != cudaSuccess ||
-      cudaMemcpyAsync(base + off_blocks, g_host_blocks, sizeof(SchedBlock) * (size_t)nblocks,
-                      cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(base + off_tw, g_host_tw, sizeof(float2) * (size_t)n,
-                      cudaMemcpyHostToDevice, s) != cudaSuccess) {
-    cudaGetLastError();
-    return FFT3D_ERR_CUDA;
-  }
+  noalloc_setup_kernel<<<1, kPhaseWords, 0, s>>>(su);
+  if (cudaGetLastError() != cudaSuccess) return FFT3D_ERR_CUDA;
 
   FusedArgs a{};
   a.in = static_cast<const float2*>(in);
@@ -209,4 +238,26 @@ extern "C" int fft3d_execute_noalloc(int n, int batch, int direction, int norm, 
     return FFT3D_ERR_CUDA;
   }
   return FFT3D_SUCCESS;
+}
+
+extern "C" int fft3d_noalloc_get_device_status(void* stream) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return FFT3D_ERR_NO_DEVICE;
+  }
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+    cudaGetLastError();
+    return FFT3D_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lock(g_mu);
+  const DeviceState& st = g_dev[dev];
+  if (!st.ready) return FFT3D_SUCCESS;  // no call on this device yet
+  unsigned w = 0;
+  if (cudaMemcpy(&w, st.base, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemset(st.base, 0, sizeof(unsigned)) != cudaSuccess) {
+    cudaGetLastError();
+    return FFT3D_ERR_CUDA;
+  }
+  return w == kStatusOk ? FFT3D_SUCCESS : FFT3D_ERR_DEVICE_TIMEOUT;
 }

@@ -15,6 +15,7 @@
 
 #include "../../include/fft3d.h"
 #include "internal.h"
+#include "schedule.h"
 #include "sizes.h"
 #include "tc_stage.cuh"
 
@@ -266,49 +267,16 @@ int check_device() {
   return FFT3D_SUCCESS;
 }
 
-// Ticket order.  Plane blocks are emitted grid after grid (in `order`); the
-// slab block of grid g is emitted once at least `concurrency` tickets (the
-// number of items resident at once) have been handed out after the last
-// plane ticket of g, so a slab item rarely waits, or earlier when the grids
-// whose planes are done but whose slabs are not yet scheduled would exceed
-// `l2_budget` bytes (their intermediate must stay in L2).
+// Ticket order (schedule_blocks, schedule.h) into a vector.
 std::vector<SchedBlock> build_schedule(const std::vector<int>& dims, const std::vector<int>& order,
                                        int concurrency, double l2_budget, int phase_items,
                                        int* total_items) {
-  std::vector<SchedBlock> blocks;
-  int start = 0;
-  auto push = [&](int g, int phase) {
-    blocks.push_back(SchedBlock{g, phase, start, dims[g]});
-    start += phase_items > 0 ? phase_items : dims[g];
-  };
-  struct Pending {
-    int g;
-    int plane_end;
-    double bytes;
-  };
-  std::vector<Pending> pending;  // FIFO
-  double pending_bytes = 0.0;
-  auto flush_ready = [&](bool force_one) {
-    while (!pending.empty()) {
-      const Pending& p = pending.front();
-      const bool ready = start - p.plane_end >= concurrency;
-      if (!ready && !force_one) break;
-      force_one = false;
-      pending_bytes -= p.bytes;
-      push(p.g, 1);
-      pending.erase(pending.begin());
-    }
-  };
-  for (int g : order) {
-    const double bytes = 8.0 * dims[g] * dims[g] * dims[g];
-    while (!pending.empty() && pending_bytes + bytes > l2_budget) flush_ready(true);
-    push(g, 0);
-    pending.push_back(Pending{g, start, bytes});
-    pending_bytes += bytes;
-    flush_ready(false);
-  }
-  while (!pending.empty()) flush_ready(true);
-  *total_items = start;
+  std::vector<SchedBlock> blocks(2 * dims.size());
+  std::vector<int> plane_end(dims.size());
+  const int nb = schedule_blocks((int)dims.size(), dims.data(), order.data(), concurrency,
+                                 l2_budget, phase_items, plane_end.data(), blocks.data(),
+                                 total_items);
+  blocks.resize(nb);
   return blocks;
 }
 
