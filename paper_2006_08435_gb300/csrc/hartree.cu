@@ -60,8 +60,13 @@ __global__ void __launch_bounds__(kRedThreads) hartree_energy_kernel(
     const int m2 = m_squared(i, n);
     if (m2 != 0) {
       const float2 v = fb[i];
-      const float inv = 1.0f / (float)m2;
-      acc += ((double)v.x * v.x + (double)v.y * v.y) * (double)inv;
+      // 1/m2 in FP64: the correctly rounded FP32 reciprocal (relative error
+      // <= 2^-24) refined by one Newton-Raphson step r = r0 + r0 (1 - m2 r0),
+      // which squares the relative error (two FP64 FMAs instead of a
+      // division on the FP64 units)
+      const double r0 = (double)(1.0f / (float)m2);
+      const double inv = fma(r0, fma(-(double)m2, r0, 1.0), r0);
+      acc += ((double)v.x * v.x + (double)v.y * v.y) * inv;
     }
   }
   __shared__ double warp_part[kRedThreads / 32];

@@ -238,9 +238,14 @@ _plan_cache: dict = {}
 _cache_lock = threading.Lock()
 
 
-def get_plan(nx, ny, nz, batch, precision="fp32", inverse=False, norm="none", device=None) -> Plan:
+def get_plan(nx, ny, nz, batch, precision="fp32", inverse=False, norm="none", device=None,
+             stream=None) -> Plan:
+    """The cached plan for this problem on this device AND stream: a plan's
+    work counters and status word may serve one stream at a time (executes
+    that overlap on two streams would share them), so each stream gets its
+    own plan."""
     dev = torch.cuda.current_device() if device is None else device
-    key = (nx, ny, nz, batch, precision, bool(inverse), norm, dev)
+    key = (nx, ny, nz, batch, precision, bool(inverse), norm, dev, _stream_handle(stream))
     with _cache_lock:
         p = _plan_cache.get(key)
         if p is None:
@@ -264,19 +269,24 @@ def fft3d(x: torch.Tensor, inverse: bool = False, norm: str = "none", precision:
         out = torch.empty_like(x)
     if batch == 0:
         return out
-    plan = get_plan(nx, ny, nz, batch, precision, inverse, norm, x.device.index)
-    return plan.execute(x, out)
+    with torch.cuda.device(x.device):
+        stream = torch.cuda.current_stream()
+        plan = get_plan(nx, ny, nz, batch, precision, inverse, norm, x.device.index, stream)
+        return plan.execute(x, out, stream)
 
 
 # Real plans own a workspace of ceil(batch/2) n^3 complex points (268 MB at
-# 128^3 x 32), so only the most recently used few are kept; an evicted
-# plan's memory is freed (cudaFree waits for work still using it).
+# 128^3 x 32), so only the most recently used few are kept.  An evicted plan
+# is only dropped from the cache, not closed: a caller in another thread may
+# still be executing it, and its memory is released (plan destroy, whose
+# cudaFree waits for work still using it) once the last reference to it
+# goes.  Like complex plans, real plans are kept per stream.
 _REAL_CACHE_MAX = 4
 _real_cache: "collections.OrderedDict" = collections.OrderedDict()
 
 
-def _get_real_plan(n, batch, precision, inverse, norm, dev) -> RealPlan:
-    key = (n, batch, precision, bool(inverse), norm, dev)
+def _get_real_plan(n, batch, precision, inverse, norm, dev, stream=None) -> RealPlan:
+    key = (n, batch, precision, bool(inverse), norm, dev, _stream_handle(stream))
     with _cache_lock:
         p = _real_cache.get(key)
         if p is not None:
@@ -286,8 +296,7 @@ def _get_real_plan(n, batch, precision, inverse, norm, dev) -> RealPlan:
             p = RealPlan(n, batch, precision, inverse, norm)
         _real_cache[key] = p
         while len(_real_cache) > _REAL_CACHE_MAX:
-            _, old = _real_cache.popitem(last=False)
-            old.close()
+            _real_cache.popitem(last=False)
     return p
 
 
@@ -306,7 +315,10 @@ def rfft3d(x: torch.Tensor, norm: str = "none", precision: str = "fp32",
         out = torch.empty(x.shape[:-1] + (n // 2 + 1,), dtype=torch.complex64, device=x.device)
     if batch == 0:
         return out
-    return _get_real_plan(n, batch, precision, False, norm, x.device.index).execute(x, out)
+    with torch.cuda.device(x.device):
+        stream = torch.cuda.current_stream()
+        p = _get_real_plan(n, batch, precision, False, norm, x.device.index, stream)
+        return p.execute(x, out, stream)
 
 
 def irfft3d(x: torch.Tensor, norm: str = "none", precision: str = "fp32",
@@ -325,7 +337,10 @@ def irfft3d(x: torch.Tensor, norm: str = "none", precision: str = "fp32",
         out = torch.empty(x.shape[:-1] + (n,), dtype=torch.float32, device=x.device)
     if batch == 0:
         return out
-    return _get_real_plan(n, batch, precision, True, norm, x.device.index).execute(x, out)
+    with torch.cuda.device(x.device):
+        stream = torch.cuda.current_stream()
+        p = _get_real_plan(n, batch, precision, True, norm, x.device.index, stream)
+        return p.execute(x, out, stream)
 
 
 class FFT3d(torch.autograd.Function):

@@ -18,7 +18,9 @@ _ws_cache: dict = {}
 
 
 def _workspace(n: int, batch: int, device) -> torch.Tensor:
-    key = (n, batch, device)
+    """Reduction workspace (partial sums and counters), one per (problem,
+    device, stream): calls on two streams must not share the counters."""
+    key = (n, batch, device, _stream_handle(None))
     ws = _ws_cache.get(key)
     if ws is None:
         nbytes = int(L.lib().fft3d_hartree_workspace_bytes(n, batch))
