@@ -8,10 +8,14 @@ than L2, so no flush is needed between steps).  Roofline bytes per
 transform = 16 * N^3 (one read and one write of the grid).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload 128x32|64x256|128x16|64x64] [--no-cpu-baseline] [--no-e2e]
-                  [--no-split] [--no-real]
+                  [--workload 128x32|64x256|128x16|64x64|64x128] [--no-cpu-baseline]
+                  [--no-e2e] [--no-split] [--no-real] [--no-64] [--no-mixed] [--no-batch1]
 
-The two small workloads exist for profiler captures of the same kernels.
+The small workloads exist for profiler captures of the same kernels.  Beside
+the headline the line carries sub-objects: split_fp16 (the same batch in
+split FP16), real_r2c_fp32 (real grids), w64x256 (64^3 x 256 in FP32 and
+split FP16), mixed_c2 (64 mixed-edge grids, forward + inverse in one CUDA
+graph) and batch1 (one grid per launch, L2 flushed, the paper's setting).
 
 Under torchrun each rank transforms its own batch (weak scaling, no
 collective on the data path); rank 0 prints one JSON line.
@@ -76,6 +80,36 @@ def whole_job_rate(ws: int, units_per_rank: int, steps: int, ms: float) -> float
     """Units per second over the whole job: every rank processes
     `units_per_rank` units per step, the job takes `ms` (max over ranks)."""
     return ws * units_per_rank * steps / (ms / 1e3)
+
+
+def timed_ms(fn, steps: int, stream) -> float:
+    """Mean milliseconds per call of `fn` over `steps` back-to-back calls,
+    CUDA events on `stream` (the stream the library launches on), with a
+    synchronize on both sides."""
+    import torch
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def batched_inputs(n: int, batch: int, seed: int, dev):
+    """The bench's seeded Gaussian-sum batch: up to four generated grids,
+    repeated, each copy times its own phase exp(0.37 i b), so every grid of
+    the batch differs."""
+    import torch
+    from paper_2006_08435_gb300 import synth
+    base = synth.gaussian_sum_grids(n, min(batch, 4), seed=seed)
+    xb = torch.from_numpy(base).to(dev)
+    reps = (batch + xb.shape[0] - 1) // xb.shape[0]
+    x = xb.repeat(reps, 1, 1, 1)[:batch].contiguous()
+    ph = torch.exp(1j * 0.37 * torch.arange(batch, device=dev, dtype=torch.float32))
+    return (x * ph.view(-1, 1, 1, 1).to(torch.complex64)).contiguous()
 
 
 def measured_peaks():
@@ -241,12 +275,7 @@ def run_ours(args, ws, rank, local):
     B.build()
 
     # seeded Gaussian-sum inputs; distinct grids from one generated grid set
-    base = synth.gaussian_sum_grids(n, min(batch, 4), seed=rank)
-    xb = torch.from_numpy(base).to(dev)
-    reps = (batch + xb.shape[0] - 1) // xb.shape[0]
-    x = xb.repeat(reps, 1, 1, 1)[:batch].contiguous()
-    ph = torch.exp(1j * 0.37 * torch.arange(batch, device=dev, dtype=torch.float32))
-    x = (x * ph.view(-1, 1, 1, 1).to(torch.complex64)).contiguous()
+    x = batched_inputs(n, batch, rank, dev)
     y = torch.empty_like(x)
     plan = Plan(n, n, n, batch)
     stream = torch.cuda.current_stream()
@@ -355,11 +384,104 @@ def run_ours(args, ws, rank, local):
                 "bytes_per_transform": 4 * n ** 3 + 8 * n * n * (n // 2 + 1)}
         del xr, yr, rplan
 
+    peak, peak_kind = measured_peaks()
+
+    # the metric's other size: 64^3 x 256 grids (537 MB, larger than L2),
+    # FP32 and split FP16, each through its default kernel, timed like the
+    # split leg
+    w64 = None
+    if not args.no_64 and (n, batch) != (64, 256):
+        del x, y
+        n6, b6 = 64, 256
+        x6 = batched_inputs(n6, b6, rank, dev)
+        y6 = torch.empty_like(x6)
+        w64 = {"workload": f"fft3d_c2c_fwd_{n6}cubed_batch{b6}", "n": n6, "batch_per_gpu": b6,
+               "bytes_per_transform": 16 * n6 ** 3}
+        for prec in ("fp32", "split_fp16"):
+            p6 = Plan(n6, n6, n6, b6, precision=prec)
+            for _ in range(3):
+                p6.execute(x6, y6, stream)
+            barrier()
+            k6 = max(1, args.steps)
+            ms6 = max_over_ranks(timed_ms(lambda: p6.execute(x6, y6, stream), k6, stream), ws, dev)
+            assert p6.device_status() == 0
+            w64[prec] = {"value": whole_job_rate(ws, b6, 1, ms6), "unit": "transforms/s",
+                         "steps": k6, "ms_per_step": ms6, "variant": p6.variant,
+                         "roofline_frac": 16.0 * n6 ** 3 * b6 / (ms6 / 1e3) / 1e9 / peak}
+            del p6
+        del x6, y6
+
+    # the mixed-edge batch: 64 grids with edges drawn from {32, 48, 64, 80,
+    # 96, 128}, forward then inverse captured in one CUDA graph and replayed
+    # (a replay = 128 transforms; bytes = one read and one write of every
+    # grid per direction)
+    mixed = None
+    if not args.no_mixed:
+        import numpy as np
+        from paper_2006_08435_gb300 import MixedPlan
+        sizes = synth.mixed_sizes(64, seed=0)
+        fwd, inv = MixedPlan(sizes), MixedPlan(sizes, inverse=True)
+        packed = np.concatenate([g.ravel() for g in synth.mixed_grids(sizes, seed=1 + rank)])
+        xm = torch.from_numpy(packed).to(dev)
+        ym, bm = torch.empty_like(xm), torch.empty_like(xm)
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            fwd.execute(xm, ym)
+            inv.execute(ym, bm)
+        stream.wait_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            fwd.execute(xm, ym)
+            inv.execute(ym, bm)
+        for _ in range(3):
+            graph.replay()
+        barrier()
+        km = max(1, args.steps)
+        msm = max_over_ranks(timed_ms(graph.replay, km, stream), ws, dev)
+        assert fwd.device_status() == 0 and inv.device_status() == 0
+        pts = sum(e ** 3 for e in sizes)
+        mixed = {"workload": "fft3d_c2c_mixed64_fwd_inv_graph", "edges": sorted(set(sizes)),
+                 "grids": len(sizes), "points": pts, "variant_fwd": fwd.variant,
+                 "value": whole_job_rate(ws, 2 * len(sizes), 1, msm), "unit": "transforms/s",
+                 "steps": km, "ms_per_replay": msm, "l2": "inputs larger than L2 (no flush)",
+                 "roofline_frac": 2 * 16.0 * pts / (msm / 1e3) / 1e9 / peak}
+        del xm, ym, bm, graph, fwd, inv
+
+    # the paper's setting: one grid per transform (Table 1), latency of
+    # one execute with L2 flushed before each timed launch
+    batch1 = None
+    if not args.no_batch1:
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        batch1 = {"l2": "flushed (256 MB write) before each timed launch", "launches": 25,
+                  "paper_context_us": {"fpga_kernel": {"16": 110, "32": 220, "64": 740},
+                                       "fftw_40_cores": {"16": 10, "32": 30, "64": 140}}}
+        for e in (16, 32, 64, 128):
+            x1 = batched_inputs(e, 1, rank, dev)
+            y1 = torch.empty_like(x1)
+            p1 = Plan(e, e, e, 1)
+            for _ in range(3):
+                p1.execute(x1, y1, stream)
+            us = []
+            for i in range(25):
+                flush.fill_(i & 255)
+                a0 = torch.cuda.Event(enable_timing=True)
+                a1 = torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                p1.execute(x1, y1, stream)
+                a1.record(stream)
+                a1.synchronize()
+                us.append(1e3 * a0.elapsed_time(a1))
+            assert p1.device_status() == 0
+            us_med = max_over_ranks(statistics.median(us), ws, dev)
+            batch1[str(e)] = {"us_median": us_med, "us_min": min(us), "variant": p1.variant,
+                              "roofline_frac_median": 16.0 * e ** 3 / (us_med / 1e6) / 1e9 / peak}
+        del flush
+
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
         return 0
-    peak, peak_kind = measured_peaks()
     bytes_per_launch = 16.0 * n ** 3 * batch
     avg_launch_ms = statistics.mean(launch_ms)
     achieved = bytes_per_launch / (avg_launch_ms / 1e3) / 1e9
@@ -392,6 +514,12 @@ def run_ours(args, ws, rank, local):
         real["roofline_frac"] = (real["bytes_per_transform"] * batch / (real["ms_per_step"] / 1e3)
                                  / 1e9 / peak)
         line["real_r2c_fp32"] = real
+    if w64 is not None:
+        line["w64x256"] = w64
+    if mixed is not None:
+        line["mixed_c2"] = mixed
+    if batch1 is not None:
+        line["batch1"] = batch1
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(n)
     print(json.dumps(line), flush=True)
@@ -411,6 +539,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-split", action="store_true")
     ap.add_argument("--no-real", action="store_true")
+    ap.add_argument("--no-64", action="store_true", help="skip the 64^3 x 256 sub-leg")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-edge graph sub-leg")
+    ap.add_argument("--no-batch1", action="store_true", help="skip the batch-1 latency sub-leg")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
