@@ -139,6 +139,59 @@ int oracle_dft3d_brute(const double* in, double* out, int nx, int ny, int nz,
   return 0;
 }
 
+/*
+ * Selected outputs of Eq. 1 for one grid, one by one: for each requested
+ * (kz, ky, kx) the sums over x, then y, then z of the definition,
+ *   F = sum_z W_nz^(z kz) sum_y W_ny^(y ky) sum_x W_nx^(x kx) f(x, y, z),
+ * each root taken from the reduced exponent (x kx mod nx, ...).  O(nx ny nz)
+ * per output, for checking single outputs of grids too large for
+ * oracle_dft3d.  points: npts triples (kz, ky, kx); out: npts complex.
+ */
+int oracle_dft3d_points(const double* in, int nx, int ny, int nz, const int* points, int npts,
+                        int sign, double* out) {
+  if (!in || !points || !out || nx < 1 || ny < 1 || nz < 1 || npts < 0) return -1;
+  if (sign != -1 && sign != 1) return -1;
+  double* tx = make_roots(nx, sign);
+  double* ty = make_roots(ny, sign);
+  double* tz = make_roots(nz, sign);
+  if (!tx || !ty || !tz) {
+    free(tx); free(ty); free(tz);
+    return -2;
+  }
+  for (int p = 0; p < npts; ++p) {
+    const int kz = points[3 * p], ky = points[3 * p + 1], kx = points[3 * p + 2];
+    if (kz < 0 || kz >= nz || ky < 0 || ky >= ny || kx < 0 || kx >= nx) {
+      free(tx); free(ty); free(tz);
+      return -1;
+    }
+    double re = 0.0, im = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : re, im)
+    for (int z = 0; z < nz; ++z) {
+      double zr = 0.0, zi = 0.0;  /* sum over y of (sum over x) W^(y ky) */
+      for (int y = 0; y < ny; ++y) {
+        const double* row = in + 2 * (((int64_t)z * ny + y) * nx);
+        double xr = 0.0, xi = 0.0;
+        for (int x = 0; x < nx; ++x) {
+          const int m = (int)(((int64_t)x * kx) % nx);
+          const double wr = tx[2 * m], wi = tx[2 * m + 1];
+          xr += row[2 * x] * wr - row[2 * x + 1] * wi;
+          xi += row[2 * x] * wi + row[2 * x + 1] * wr;
+        }
+        const int my = (int)(((int64_t)y * ky) % ny);
+        zr += xr * ty[2 * my] - xi * ty[2 * my + 1];
+        zi += xr * ty[2 * my + 1] + xi * ty[2 * my];
+      }
+      const int mz = (int)(((int64_t)z * kz) % nz);
+      re += zr * tz[2 * mz] - zi * tz[2 * mz + 1];
+      im += zr * tz[2 * mz + 1] + zi * tz[2 * mz];
+    }
+    out[2 * p] = re;
+    out[2 * p + 1] = im;
+  }
+  free(tx); free(ty); free(tz);
+  return 0;
+}
+
 /* Threads the OpenMP runtime will use for the parallel loops above. */
 int oracle_num_threads(void) {
 #ifdef _OPENMP

@@ -14,6 +14,9 @@ Contents
   lines.  O(n^4) for an n^3 grid.
 * ``dft3d_brute``  -- the literal triple sum of Eq. 1, O(n^6); pins the
   separable form on tiny grids.
+* ``dft3d_points`` -- single outputs of Eq. 1, each from the definition
+  (sums over x, then y, then z), O(n^3) per output: checks of grids too
+  large for ``dft3d`` (256^3 and up).
 * ``rdft3d`` / ``irdft3d`` -- Eq. 1 for real grids (a real density, the
   paper's plane-wave DFT setting): the forward transform of a real grid
   keeps the half spectrum kx <= nx/2 (the rest is its complex conjugate
@@ -75,6 +78,9 @@ def _load():
             lib.oracle_dft3d.restype = ctypes.c_int
             lib.oracle_dft3d_brute.argtypes = [dp, dp] + [ctypes.c_int] * 4
             lib.oracle_dft3d_brute.restype = ctypes.c_int
+            lib.oracle_dft3d_points.argtypes = [dp] + [ctypes.c_int] * 3 + [
+                ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int, dp]
+            lib.oracle_dft3d_points.restype = ctypes.c_int
             lib.oracle_num_threads.argtypes = []
             lib.oracle_num_threads.restype = ctypes.c_int
             _lib = lib
@@ -121,6 +127,25 @@ def dft3d_brute(x, sign: int = -1) -> np.ndarray:
     rc = _load().oracle_dft3d_brute(_dp(a), _dp(out), nx, ny, nz, int(sign))
     if rc != 0:
         raise RuntimeError(f"oracle_dft3d_brute failed ({rc})")
+    return out
+
+
+def dft3d_points(x, points, sign: int = -1) -> np.ndarray:
+    """Selected outputs F(kz, ky, kx) of Eq. 1 for ONE grid (nz, ny, nx),
+    each computed by itself from the definition (sums over x, y, z), for
+    grids too large for ``dft3d``.  ``points``: (m, 3) integer array of
+    (kz, ky, kx).  Returns m complex128 values."""
+    a = _as_c128(x)
+    if a.ndim != 3:
+        raise ValueError("one grid (nz, ny, nx)")
+    nz, ny, nx = a.shape
+    pts = np.ascontiguousarray(np.asarray(points, dtype=np.int32).reshape(-1, 3))
+    out = np.empty(pts.shape[0], dtype=np.complex128)
+    rc = _load().oracle_dft3d_points(_dp(a), nx, ny, nz,
+                                     pts.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                     pts.shape[0], int(sign), _dp(out))
+    if rc != 0:
+        raise RuntimeError(f"oracle_dft3d_points failed ({rc})")
     return out
 
 

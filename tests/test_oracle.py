@@ -203,3 +203,47 @@ def test_synth_deterministic_and_in_range():
     rho, c, s, w = synth.hartree_density(16, 10.0, seed=0)
     assert w.sum() == pytest.approx(128.0) and (w > 0).all()
     assert (s >= 0.3).all() and (s <= 1.0).all() and (rho > 0).all()
+
+
+# ------------------------------------------------ single outputs (dft3d_points)
+
+@pytest.mark.parametrize("shape", SHAPES_TINY + [(3, 4, 5)])
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_points_match_triple_sum_everywhere(shape, sign):
+    """Every output of dft3d_points equals the literal triple sum of Eq. 1
+    (non-cubic shapes, so a swapped axis or index order fails)."""
+    x = _rand(shape, 11)
+    ref = oracle.dft3d_brute(x, sign)
+    pts = np.array(list(itertools.product(*[range(s) for s in shape])))
+    got = oracle.dft3d_points(x, pts, sign)
+    assert np.max(np.abs(got - ref.ravel())) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_points_match_library_on_a_larger_non_cubic_grid():
+    x = _rand((12, 20, 45), 12)
+    ref = np.fft.fftn(x)
+    rng = np.random.default_rng(13)
+    pts = np.stack([rng.integers(0, s, 40) for s in x.shape], axis=1)
+    got = oracle.dft3d_points(x, pts, -1)
+    want = ref[pts[:, 0], pts[:, 1], pts[:, 2]]
+    assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_points_plane_wave_closed_form():
+    """exp(+2 pi i (kx0 x/nx + ky0 y/ny + kz0 z/nz)) has the forward
+    transform nx ny nz at (kz0, ky0, kx0) and 0 elsewhere."""
+    nz, ny, nx = 24, 30, 40
+    k0 = (5, 7, 33)
+    z, y, xx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    f = np.exp(2j * np.pi * (k0[2] * xx / nx + k0[1] * y / ny + k0[0] * z / nz))
+    pts = np.array([k0, (0, 0, 0), (5, 7, 32), (k0[0], (k0[1] + 1) % ny, k0[2])])
+    got = oracle.dft3d_points(f, pts, -1)
+    assert abs(got[0] - nx * ny * nz) <= 1e-9 * nx * ny * nz
+    assert np.max(np.abs(got[1:])) <= 1e-9 * nx * ny * nz
+
+
+def test_points_reject_out_of_range():
+    x = _rand((2, 3, 4), 14)
+    for bad in ((2, 0, 0), (0, 3, 0), (0, 0, 4), (-1, 0, 0)):
+        with pytest.raises(RuntimeError):
+            oracle.dft3d_points(x, [bad], -1)
