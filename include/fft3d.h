@@ -81,11 +81,24 @@ enum {
 
 /*
  * 1 if an edge length n can be planned on every axis, else 0.  Host only,
- * needs no GPU.  Supported: n in {2,...,128} whose prime factors are 2, 3
- * and 5 and which splits as n = L1*L2 with L1, L2 <= 16 (all configs use
- * 16, 32, 48, 64, 80, 96, 128).
+ * needs no GPU.  Supported: 2 <= n <= 512 with prime factors 2, 3 and 5.
+ * Cubic grids of edge 16, 32, 48, 64, 80, 96 or 128 have fused single-launch
+ * kernels (and the tensor-core precisions at 64 and 128); every other grid,
+ * cubic or not (nx, ny, nz each supported), runs on the general path: one
+ * pencil pass per axis (FP32).
  */
 int fft3d_size_supported(int n);
+
+/*
+ * Host-only view of the general path's 1D plan for edge n (needs no GPU):
+ * the radices R_0 .. R_(s-1) (product n) of its decimation-in-frequency
+ * stages, *nstages = s <= 12, and the digit-reversal map: after the stages
+ * output K = k_0 + R_0 (k_1 + R_1 (k_2 + ...)), k_t < R_t, sits at position
+ * pos[K] = sum_t k_t * n / (R_0 ... R_t) of the pencil.  radix holds 12
+ * ints, pos n ints.  Errors: FFT3D_ERR_NULL_PTR, FFT3D_ERR_UNSUPPORTED_SIZE
+ * (n outside 2..512 or with a prime factor above 5).
+ */
+int fft3d_axis_digit_map(int n, int* nstages, int* radix, int* pos);
 
 /*
  * Host-only view of the planner's split and twiddle table for edge n (needs
@@ -141,7 +154,8 @@ int fft3d_tc_operand_table(int precision, uint16_t* out);
 
 /*
  * Plan `batch` grids of nx*ny*nz points (Eq. 1 per grid).
- *   nx, ny, nz : edge lengths, each fft3d_size_supported.
+ *   nx, ny, nz : edge lengths, each fft3d_size_supported (non-cubic grids
+ *                and edges without a fused kernel take the general path).
  *   batch      : number of grids, >= 1, packed back to back.
  *   precision  : fft3d_precision; the tensor-core kinds (SPLIT_FP16,
  *                SPLIT_BF16, FP16) are planned for cubic n = 64 and 128
@@ -255,8 +269,14 @@ int fft3d_selftest_wait_timeout(int64_t timeout_ns);
  * tensor-TMA items with tcgen05 products, operands and accumulators in
  * tensor memory (64^3 two-plane, 128^3 split-y; all of a multiprocessor's
  * tensor memory, one block per multiprocessor); 8 and 9 have the same buffer
- * requirements as the tensor-TMA FP32 variants.  Mixed plans:
- * 0 one launch of the mixed-edge kernel, 1 one launch per distinct edge.
+ * requirements as the tensor-TMA FP32 variants.  10: the general path
+ * (every plan that is not cubic with a fused edge; selectable for those
+ * too): per chunk of grids that fits 40% of L2, three launches, the x pass
+ * (in -> out) and the y and z passes in place on out, each a batched 1D
+ * transform of the pencils of one axis in shared-memory tiles (mixed
+ * radices 2, 3, 4, 5, 6, 8, 9, 10, 12, 15, 16; fft3d_axis_digit_map).
+ * Mixed plans: 0 one launch of the mixed-edge kernel, 1 one launch per
+ * distinct edge.
  * At create the variant comes from FFT3D_VARIANT / FFT3D_MIXED_VARIANT if
  * set, else from the tuning cache named by FFT3D_TUNE_CACHE (tuned on the
  * spot when FFT3D_TUNE=1 and the entry is missing), else a built-in default.

@@ -33,6 +33,7 @@ _VP = ctypes.c_void_p
 _I = ctypes.c_int
 _SIGS = {
     "fft3d_size_supported": (_I, [_I]),
+    "fft3d_axis_digit_map": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "fft3d_twiddle_table": (_I, [_I, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "fft3d_tc_operand_table": (_I, [_I, ctypes.POINTER(ctypes.c_uint16)]),
     "fft3d_plan_create": (_I, [_I, _I, _I, _I, _I, _I, _I, ctypes.POINTER(_VP)]),

@@ -67,6 +67,74 @@ struct KernelInfo {
   int umma_b = 0;               // mma_frag holds the tcgen05 B table (tcgen.cuh), not mma.sync fragments
 };
 
+// ---------------------------------------------------------------- general path
+// Pencil passes for any edge 2..kAxisMaxLen with prime factors 2, 3, 5, one
+// axis at a time (axis.cu).
+constexpr int kAxisMaxLen = 512;
+constexpr int kGeneralVariant = 10;  // plan variant of the general path
+constexpr int kAxisMaxStages = 12;
+
+// n / d = (hi32(n * mul) + n) >> shift for every n < 2^32 (make_fastdiv).
+struct FastDiv {
+  unsigned mul;
+  int shift;
+};
+FastDiv make_fastdiv(unsigned d);
+
+// One pencil length, planned on the host: the radices of its
+// decimation-in-frequency stages and the device tables (W_L^m, m < L, FP64
+// rounded to FP32; the position each output K holds after the stages).
+struct AxisTable {
+  int L = 0, nst = 0;
+  int radix[kAxisMaxStages] = {};
+  float2* d_tw = nullptr;
+  unsigned short* d_pos = nullptr;
+};
+int axis_stages(int L, int* radix);                              // 0: not plannable
+void axis_positions(int L, int nst, const int* radix, int* pos);  // pos[K], K < L
+
+// Which pencils a pass transforms.  contiguous: `rows` rows of L points
+// packed back to back (the x pass).  Strided: for each of `outer` slices,
+// the nx pencils at base + x (x < nx), element i at + i * pi, with
+// base = (outer / d1) * s1 + (outer % d1) * s0.
+struct AxisGeom {
+  int contiguous = 0;
+  long long rows = 0;
+  long long outer = 0;
+  int nx = 0, d1 = 1;
+  long long s1 = 0, s0 = 0, pi = 0;
+  float scale = 1.0f;
+  int do_scale = 0;
+};
+
+// Kernel arguments of one pass (axis.cu).
+struct AxisArgs {
+  const float2* in;  // may equal out (a tile is read before it is written)
+  float2* out;
+  const float2* tw;
+  const unsigned short* pos;
+  int L, nst, W, lw;  // W = 2^lw pencils per tile
+  int radix[kAxisMaxStages], span[kAxisMaxStages], sub[kAxisMaxStages], twst[kAxisMaxStages];
+  FastDiv divsub[kAxisMaxStages];  // division by sub[t], the span M of a stage's sub-blocks
+  FastDiv divL;
+  int contiguous;
+  unsigned ntiles;
+  long long rows;
+  int nx, xtiles, d1;  // strided: tile -> (outer, x0 = 16 * (tile % xtiles))
+  FastDiv divx, divd1;
+  long long s1, s0, pi;
+  float scale;
+  int do_scale;
+};
+struct AxisLaunch {
+  AxisArgs args{};
+  int dir = -1;
+  int grid = 0;
+  size_t smem = 0;
+};
+int prepare_axis_pass(const AxisTable& tab, int dir, const AxisGeom& g, int sms, AxisLaunch* out);
+cudaError_t launch_axis_pass(const AxisLaunch& l, const float2* in, float2* out, cudaStream_t stream);
+
 // Defined in the inst_*.cu translation units.
 KernelInfo fused_kernel_info(int n, int dir, int variant);   // single-size kernel
 KernelInfo mixed_kernel_info(int dir);          // all fused sizes

@@ -155,18 +155,22 @@ static bool fused_size(int n) { return fused_slot(n) >= 0; }
 // warp-owned two-phase kernel (64^3, 128^3), 6 to 8 the tensor-TMA
 // thread-per-pencil kernels.  Tensor-core precisions: 0 the plain persistent
 // kernel, 8 (64^3) the two-plane tensor-TMA kernel with mma.sync, 9 the
-// tensor-TMA items with tcgen05 products (64^3 two-plane, 128^3 split-y).  Mixed plans: 0 one
+// tensor-TMA items with tcgen05 products (64^3 two-plane, 128^3 split-y).
+// Variant 10 (kGeneralVariant): the general path, one pencil pass per axis
+// (axis.cu), the only one for non-cubic grids and edges without a fused
+// kernel, selectable for the others.  Mixed plans: 0 one
 // launch of the mixed-edge kernel, 1 one launch per distinct edge with that
 // edge's default kernel.
 std::vector<int> variant_candidates(bool mixed, int n, int precision) {
   if (mixed) return {0, 1};
   if (precision != FFT3D_FP32) return n == 64 ? std::vector<int>{0, 8, 9} : std::vector<int>{0, 9};
+  if (!fused_size(n)) return {kGeneralVariant};
   switch (n) {
-    case 16: return {0, 1, 3};
-    case 32: return {0, 1, 3, 4};
-    case 64: return {0, 1, 2, 3, 4, 5, 6, 7, 8};
-    case 128: return {0, 1, 2, 5, 6};
-    default: return {0, 1, 4};  // 48, 80, 96
+    case 16: return {0, 1, 3, kGeneralVariant};
+    case 32: return {0, 1, 3, 4, kGeneralVariant};
+    case 64: return {0, 1, 2, 3, 4, 5, 6, 7, 8, kGeneralVariant};
+    case 128: return {0, 1, 2, 5, 6, kGeneralVariant};
+    default: return {0, 1, 4, kGeneralVariant};  // 48, 80, 96
   }
 }
 
@@ -225,6 +229,13 @@ struct fft3d_plan_s {
   // device buffers shared by the units (owned)
   long long* d_off = nullptr;
   unsigned* d_status = nullptr;
+  // general path (variant kGeneralVariant): one pass per axis over chunks of
+  // `chunk` grids (the last chunk `tail` grids); pass[axis][0] for a full
+  // chunk, pass[axis][1] for the tail
+  bool general = false;
+  std::vector<AxisTable> tables;
+  AxisLaunch pass[3][2];
+  int chunk = 0, nchunks = 0, tail = 0;
 };
 
 namespace {
@@ -249,6 +260,12 @@ void free_plan_buffers(fft3d_plan p) {
   cudaFree(p->d_status);
   p->d_off = nullptr;
   p->d_status = nullptr;
+  for (AxisTable& t : p->tables) {
+    cudaFree(t.d_tw);
+    cudaFree(t.d_pos);
+    t.d_tw = nullptr;
+    t.d_pos = nullptr;
+  }
 }
 
 int check_device() {
@@ -421,8 +438,27 @@ int validate_common(int precision, int direction, int norm, fft3d_plan* out_plan
   return FFT3D_SUCCESS;
 }
 
+// General path: per chunk of grids, the x pass (in -> out), then y and z in
+// place on out; a chunk's intermediate (at most 40% of L2 when the grids
+// allow) stays in L2 between its passes.
+int launch_general(fft3d_plan p, const float2* in, float2* out, cudaStream_t stream) {
+  const long long grid_pts = (long long)p->nx * p->ny * p->nz;
+  for (int c = 0; c < p->nchunks; ++c) {
+    const int w = (c == p->nchunks - 1 && p->tail != p->chunk) ? 1 : 0;
+    const long long off = (long long)c * p->chunk * grid_pts;
+    if (launch_axis_pass(p->pass[0][w], in + off, out + off, stream) != cudaSuccess ||
+        launch_axis_pass(p->pass[1][w], out + off, out + off, stream) != cudaSuccess ||
+        launch_axis_pass(p->pass[2][w], out + off, out + off, stream) != cudaSuccess) {
+      cudaGetLastError();
+      return FFT3D_ERR_CUDA;
+    }
+  }
+  return FFT3D_SUCCESS;
+}
+
 int launch(fft3d_plan p, const float2* in, float2* out, const float2* const* in_ptrs,
            float2* const* out_ptrs, cudaStream_t stream) {
+  if (p->general) return launch_general(p, in, out, stream);
   for (const Unit& u : p->units) {
     // ticket kernels start from zeroed counters; cluster kernels use none
     if (u.kernel.cluster == 0 && cudaMemsetAsync(u.d_work, 0, u.work_bytes, stream) != cudaSuccess) {
@@ -455,15 +491,100 @@ int launch(fft3d_plan p, const float2* in, float2* out, const float2* const* in_
   return FFT3D_SUCCESS;
 }
 
+// W_L^m = exp(-2 pi i m / L), m < L, evaluated in FP64 by the host math
+// library and rounded to nearest FP32: the twiddle table of the general
+// path's passes.
+void root_table(int L, float* out /* 2 * L */) {
+  for (int m = 0; m < L; ++m) {
+    const double a = 2.0 * 3.14159265358979323846 * (double)m / (double)L;
+    out[2 * m] = (float)std::cos(a);
+    out[2 * m + 1] = (float)(-std::sin(a));
+  }
+}
+
+// Plan of the general path: tables for each distinct edge, chunking by the
+// L2 budget, the three passes prepared for a full chunk and for the tail.
+int create_general(fft3d_plan p) {
+  int rc;
+  const int lens[3] = {p->nx, p->ny, p->nz};
+  int tab_of[3];
+  for (int a = 0; a < 3; ++a) {
+    tab_of[a] = -1;
+    for (size_t t = 0; t < p->tables.size(); ++t)
+      if (p->tables[t].L == lens[a]) tab_of[a] = (int)t;
+    if (tab_of[a] >= 0) continue;
+    AxisTable t;
+    t.L = lens[a];
+    t.nst = axis_stages(t.L, t.radix);
+    if (!t.nst) return FFT3D_ERR_UNSUPPORTED_SIZE;
+    std::vector<float> tw(2 * (size_t)t.L);
+    root_table(t.L, tw.data());
+    std::vector<int> pos(t.L);
+    axis_positions(t.L, t.nst, t.radix, pos.data());
+    std::vector<unsigned short> pos16(pos.begin(), pos.end());
+    p->tables.push_back(t);
+    AxisTable& tt = p->tables.back();
+    if ((rc = upload(&tt.d_tw, reinterpret_cast<const float2*>(tw.data()), (size_t)t.L))) return rc;
+    if ((rc = upload(&tt.d_pos, pos16.data(), pos16.size()))) return rc;
+    tab_of[a] = (int)p->tables.size() - 1;
+  }
+  int sms = 0, l2_bytes = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&l2_bytes, cudaDevAttrL2CacheSize, p->device) != cudaSuccess)
+    return FFT3D_ERR_CUDA;
+  const long long nx = p->nx, ny = p->ny, nz = p->nz;
+  const double grid_bytes = 8.0 * (double)(nx * ny * nz);
+  long long chunk = (long long)(0.4 * (double)l2_bytes / grid_bytes);
+  // a pass's tile count stays below 2^31 (every pass has fewer tiles than
+  // pencils, at most max(ny nz, nz nx, ny nx) per grid)
+  const long long cap = std::max(1LL, (1LL << 30) / std::max({ny * nz, nz * nx, ny * nx}));
+  chunk = std::max(1LL, std::min({chunk, (long long)p->batch, cap}));
+  p->chunk = (int)chunk;
+  p->nchunks = (int)((p->batch + chunk - 1) / chunk);
+  p->tail = p->batch - (p->nchunks - 1) * p->chunk;
+  for (int w = 0; w < 2; ++w) {
+    const long long c = w == 0 ? p->chunk : p->tail;
+    AxisGeom gx, gy, gz;
+    gx.contiguous = 1;
+    gx.rows = c * ny * nz;
+    gy.outer = c * nz;  // (grid, z) slices: base = outer * ny * nx
+    gy.nx = (int)nx;
+    gy.d1 = 1;
+    gy.s1 = ny * nx;
+    gy.pi = nx;
+    gz.outer = c * ny;  // (grid, y) slices: base = grid * nz ny nx + y nx
+    gz.nx = (int)nx;
+    gz.d1 = (int)ny;
+    gz.s1 = nz * ny * nx;
+    gz.s0 = nx;
+    gz.pi = nx * ny;
+    gz.scale = p->scale;
+    gz.do_scale = p->do_scale;
+    const AxisGeom* gs[3] = {&gx, &gy, &gz};
+    for (int a = 0; a < 3; ++a)
+      if ((rc = prepare_axis_pass(p->tables[tab_of[a]], p->direction, *gs[a], sms, &p->pass[a][w])))
+        return rc;
+  }
+  return FFT3D_SUCCESS;
+}
+
 // Validated arguments -> plan (variant < 0: environment override, tuning
 // cache, or the built-in default).
 int create_uniform(int nx, int ny, int nz, int batch, int precision, int direction, int norm,
                    int variant, fft3d_plan* out_plan) {
   int rc;
   if ((rc = check_device())) return rc;
-  if (variant < 0) variant = pick_variant(false, nx, batch, precision, direction, nullptr, 0);
-  const std::vector<int> cand = variant_candidates(false, nx, precision);
-  if (std::find(cand.begin(), cand.end(), variant) == cand.end()) return FFT3D_ERR_INVALID_ARG;
+  const bool fused = nx == ny && ny == nz && fused_size(nx);
+  if (!fused) {
+    // the general path is the only one for these edges
+    if (precision != FFT3D_FP32) return FFT3D_ERR_UNSUPPORTED_PRECISION;
+    if (variant < 0) variant = kGeneralVariant;
+    if (variant != kGeneralVariant) return FFT3D_ERR_INVALID_ARG;
+  } else {
+    if (variant < 0) variant = pick_variant(false, nx, batch, precision, direction, nullptr, 0);
+    const std::vector<int> cand = variant_candidates(false, nx, precision);
+    if (std::find(cand.begin(), cand.end(), variant) == cand.end()) return FFT3D_ERR_INVALID_ARG;
+  }
   fft3d_plan p = new (std::nothrow) fft3d_plan_s();
   if (!p) return FFT3D_ERR_ALLOC;
   cudaGetDevice(&p->device);
@@ -476,6 +597,22 @@ int create_uniform(int nx, int ny, int nz, int batch, int precision, int directi
   for (int g = 0; g < batch; ++g) p->offsets[g] = (long long)g * pts;
   p->total_points = pts * batch;
   set_scale(p, (double)pts);
+  if (variant == kGeneralVariant) {
+    p->general = true;
+    if (cudaMalloc(&p->d_status, sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(p->d_status, 0, sizeof(unsigned)) != cudaSuccess)
+      rc = FFT3D_ERR_ALLOC;
+    else
+      rc = create_general(p);
+    if (rc) {
+      cudaGetLastError();
+      free_plan_buffers(p);
+      delete p;
+      return rc;
+    }
+    *out_plan = p;
+    return FFT3D_SUCCESS;
+  }
   Unit u;
   u.kernel = precision == FFT3D_FP32 ? fused_kernel_info(nx, direction, variant)
                                      : tc_kernel_info(nx, direction, precision, variant);
@@ -553,10 +690,22 @@ int create_mixed(int count, const int* dims, int direction, int norm, int varian
   return FFT3D_SUCCESS;
 }
 
+bool general_size(int n) {
+  int r[kAxisMaxStages];
+  return axis_stages(n, r) > 0;
+}
+
 int validate_uniform(int nx, int ny, int nz, int batch, int precision) {
   if (nx < 1 || ny < 1 || nz < 1 || batch < 1) return FFT3D_ERR_INVALID_ARG;
   if (batch > (1 << 24)) return FFT3D_ERR_INVALID_ARG;
-  if (!fused_size(nx) || nx != ny || ny != nz) return FFT3D_ERR_UNSUPPORTED_SIZE;
+  if (!(nx == ny && ny == nz && fused_size(nx))) {
+    // general path: every edge 2..512 with prime factors 2, 3, 5; FP32
+    if (!general_size(nx) || !general_size(ny) || !general_size(nz))
+      return FFT3D_ERR_UNSUPPORTED_SIZE;
+    if (precision != FFT3D_FP32) return FFT3D_ERR_UNSUPPORTED_PRECISION;
+    if ((long long)nx * ny * nz * batch >= (1LL << 40)) return FFT3D_ERR_INVALID_ARG;
+    return FFT3D_SUCCESS;
+  }
   if (precision != FFT3D_FP32 && !tc_size(nx)) return FFT3D_ERR_UNSUPPORTED_PRECISION;
   // ticket counters are 32-bit: 2 * n items per grid
   if ((long long)batch * 2 * nx >= (1LL << 31)) return FFT3D_ERR_INVALID_ARG;
@@ -634,14 +783,14 @@ int fft3d_plan_host_io(fft3d_plan plan, int chunk_grids) {
   }
   HostIO* h = new (std::nothrow) HostIO();
   if (!h) return FFT3D_ERR_ALLOC;
-  const int n = plan->nx;
+  const int nx = plan->nx, ny = plan->ny, nz = plan->nz;
   h->grids = chunk_grids;
-  h->grid_bytes = sizeof(float2) * (size_t)n * n * n;
-  int rc = create_uniform(n, n, n, chunk_grids, plan->precision, plan->direction, plan->norm,
+  h->grid_bytes = sizeof(float2) * (size_t)nx * ny * nz;
+  int rc = create_uniform(nx, ny, nz, chunk_grids, plan->precision, plan->direction, plan->norm,
                           plan->variant, &h->chunk);
   const int rem = plan->batch % chunk_grids;
   if (!rc && rem)
-    rc = create_uniform(n, n, n, rem, plan->precision, plan->direction, plan->norm,
+    rc = create_uniform(nx, ny, nz, rem, plan->precision, plan->direction, plan->norm,
                         plan->variant, &h->tail);
   const size_t bytes = h->grid_bytes * (size_t)chunk_grids;
   for (int b = 0; b < 2 && !rc; ++b)
@@ -716,7 +865,7 @@ int fft3d_execute_host(fft3d_plan plan, const void* host_in, void* host_out, voi
 
 extern "C" {
 
-int fft3d_size_supported(int n) { return fused_size(n) ? 1 : 0; }
+int fft3d_size_supported(int n) { return fused_size(n) || general_size(n) ? 1 : 0; }
 
 int fft3d_tc_operand_table(int precision, uint16_t* out) {
   if (!out) return FFT3D_ERR_NULL_PTR;

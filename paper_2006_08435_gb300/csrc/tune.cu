@@ -182,7 +182,11 @@ int pick_variant(bool mixed, int n, int batch, int precision, int direction, con
   const std::vector<int> cand = variant_candidates(mixed, n, precision);
   auto allowed = [&](int v) { return std::find(cand.begin(), cand.end(), v) != cand.end(); };
   const char* ov = std::getenv(mixed ? "FFT3D_MIXED_VARIANT" : "FFT3D_VARIANT");
-  if (ov && ov[0] >= '0' && ov[0] <= '9' && ov[1] == 0 && allowed(ov[0] - '0')) return ov[0] - '0';
+  if (ov && *ov) {
+    char* end = nullptr;
+    const long v = std::strtol(ov, &end, 10);
+    if (end && *end == 0 && v >= 0 && v < 100 && allowed((int)v)) return (int)v;
+  }
   const char* path = std::getenv("FFT3D_TUNE_CACHE");
   if (path && *path) {
     const std::string key = problem_key(mixed, n, batch, precision, direction, dims, count);

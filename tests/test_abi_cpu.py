@@ -50,7 +50,10 @@ def _create(lib, *args):
     ((64, 64, 64, 1, 0, -1, 5), L.FFT3D_ERR_INVALID_ARG),      # norm
     ((0, 64, 64, 1, 0, -1, 0), L.FFT3D_ERR_INVALID_ARG),       # zero edge
     ((7, 7, 7, 1, 0, -1, 0), L.FFT3D_ERR_UNSUPPORTED_SIZE),    # prime 7
-    ((256, 256, 256, 1, 0, -1, 0), L.FFT3D_ERR_UNSUPPORTED_SIZE),
+    ((1024, 1024, 1024, 1, 0, -1, 0), L.FFT3D_ERR_UNSUPPORTED_SIZE),  # above 512
+    ((64, 128, 14, 1, 0, -1, 0), L.FFT3D_ERR_UNSUPPORTED_SIZE),  # one edge with a 7
+    ((64, 128, 96, 1, 1, -1, 0), L.FFT3D_ERR_UNSUPPORTED_PRECISION),  # general path: FP32
+    ((256, 256, 256, 1, 2, -1, 0), L.FFT3D_ERR_UNSUPPORTED_PRECISION),
 ])
 def test_create_validates_before_device(fft3d_lib, args, code):
     rc, h = _create(fft3d_lib, *args)
@@ -84,11 +87,87 @@ def test_valid_args_reach_device_check(fft3d_lib):
     assert rc == L.FFT3D_ERR_NO_DEVICE
 
 
+def _smooth(n):
+    for p in (2, 3, 5):
+        while n % p == 0:
+            n //= p
+    return n == 1
+
+
 def test_size_supported(fft3d_lib):
+    """Every edge 2..512 whose prime factors are 2, 3, 5, nothing else."""
     for n in FUSED:
         assert fft3d_lib.fft3d_size_supported(n) == 1
-    for n in (0, 1, 7, 11, 13, 256, 1024):
-        assert fft3d_lib.fft3d_size_supported(n) == 0
+    for n in range(-1, 1100):
+        want = 2 <= n <= 512 and _smooth(n)
+        assert fft3d_lib.fft3d_size_supported(n) == int(want), n
+
+
+def _digit_map(lib, n):
+    ns = ctypes.c_int()
+    radix = (ctypes.c_int * 12)()
+    pos = (ctypes.c_int * n)()
+    rc = lib.fft3d_axis_digit_map(n, ctypes.byref(ns), radix, pos)
+    return rc, list(radix)[:ns.value], list(pos)
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 6, 12, 16, 45, 96, 100, 128, 243, 250, 256, 375, 384,
+                               480, 500, 512])
+def test_axis_digit_map_is_the_mixed_radix_reversal(fft3d_lib, n):
+    """Bit-exact against the digit reversal written from its definition:
+    output K with digits k_t (K = k_0 + R_0 (k_1 + R_1 (...))) sits at
+    position sum_t k_t n / (R_0 ... R_t); a bijection; radices multiply to n
+    and each has a register codelet."""
+    rc, radix, pos = _digit_map(fft3d_lib, n)
+    assert rc == L.FFT3D_SUCCESS
+    assert int(np.prod(radix)) == n
+    assert set(radix) <= {2, 3, 4, 5, 6, 8, 9, 10, 12, 15, 16}
+    for K in range(n):
+        digits, rem = [], K
+        for r in radix:
+            digits.append(rem % r)
+            rem //= r
+        p, span = 0, n
+        for r, d in zip(radix, digits):
+            span //= r
+            p += d * span
+        assert pos[K] == p
+    assert sorted(pos) == list(range(n))
+
+
+@pytest.mark.parametrize("n", [6, 16, 45, 96, 100, 128, 250, 384, 512])
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_axis_stages_compute_the_dft(fft3d_lib, n, sign):
+    """The stage algorithm the general path's kernel runs (decimation in
+    frequency over the library's radices: y_k = sum_r x[j + r M] W_R^(r k)
+    times W_N^(j k) to position j + k M), carried out here in FP64 NumPy,
+    and read through the library's digit map, is the DFT (numpy.fft)."""
+    rc, radix, pos = _digit_map(fft3d_lib, n)
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    a = x.copy()
+    span = n
+    for R in radix:
+        M = span // R
+        wr = np.exp(sign * 2j * np.pi * np.outer(np.arange(R), np.arange(R)) / R)
+        for blk in range(n // span):
+            for j in range(M):
+                idx = blk * span + j + M * np.arange(R)
+                y = wr.T @ a[idx]
+                y *= np.exp(sign * 2j * np.pi * j * np.arange(R) / span)
+                a[idx] = y
+        span = M
+    got = a[np.asarray(pos)]
+    want = np.fft.fft(x) if sign < 0 else np.fft.ifft(x) * n
+    assert np.max(np.abs(got - want)) <= 1e-10 * np.max(np.abs(want))
+
+
+def test_axis_digit_map_rejects(fft3d_lib):
+    for n in (0, 1, 7, 14, 1024, 2048):
+        rc, _, _ = _digit_map(fft3d_lib, max(n, 1))
+        assert rc == L.FFT3D_ERR_UNSUPPORTED_SIZE
+    ns = ctypes.c_int()
+    assert fft3d_lib.fft3d_axis_digit_map(16, None, None, None) == L.FFT3D_ERR_NULL_PTR
 
 
 @pytest.mark.parametrize("n", FUSED)
@@ -182,7 +261,7 @@ def _create_real(lib, *args):
     ((64, 2, 0, 1, 5), L.FFT3D_ERR_INVALID_ARG),                # norm
     ((15, 2, 0, -1, 0), L.FFT3D_ERR_UNSUPPORTED_SIZE),          # odd edge
     ((7, 2, 0, -1, 0), L.FFT3D_ERR_UNSUPPORTED_SIZE),
-    ((256, 2, 0, -1, 0), L.FFT3D_ERR_UNSUPPORTED_SIZE),
+    ((1024, 2, 0, -1, 0), L.FFT3D_ERR_UNSUPPORTED_SIZE),
     ((32, 2, 1, -1, 0), L.FFT3D_ERR_UNSUPPORTED_PRECISION),     # tensor cores at 64, 128 only
 ])
 def test_real_create_validates_before_device(fft3d_lib, args, code):
