@@ -69,40 +69,89 @@ __device__ __forceinline__ void stage(float2* tile, const float2* tw, const Args
   }
 }
 
-template <int DIR>
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Where tile t lives: its first element and how many of its W pencils
+// exist (the last row tile, or an x tile at the edge, can be partial).
+struct TileRef {
+  long long base;
+  int nv;
+};
+__device__ __forceinline__ TileRef tile_of(const Args& a, unsigned t) {
+  TileRef r;
+  if (a.contiguous) {
+    const long long r0 = (long long)t << a.lw;
+    r.nv = (int)min((long long)a.W, a.rows - r0);
+    r.base = r0 * a.L;
+  } else {
+    const unsigned outer = fdiv(t, a.divx);
+    const int x0 = (int)(t - outer * (unsigned)a.xtiles) << a.lw;
+    r.nv = min(a.W, a.nx - x0);
+    const unsigned o1 = fdiv(outer, a.divd1);
+    r.base = (long long)o1 * a.s1 + (long long)(outer - o1 * (unsigned)a.d1) * a.s0 + x0;
+  }
+  return r;
+}
+
+// Asynchronous copies of tile t into buf ([i][q], pitch P), 8 bytes each:
+// every copy of a thread is in flight at once.
+__device__ __forceinline__ void load_tile(const Args& a, unsigned t, float2* buf, int P) {
+  const TileRef r = tile_of(a, t);
+  const uint32_t sb = (uint32_t)__cvta_generic_to_shared(buf);
+  if (a.contiguous) {
+    const float2* src = a.in + r.base;
+    for (int e = threadIdx.x; e < r.nv * a.L; e += kThreads) {
+      const unsigned q = fdiv((unsigned)e, a.divL);
+      cp_async8(sb + 8u * (uint32_t)((e - (int)q * a.L) * P + (int)q), src + e);
+    }
+  } else {
+    const int pts = a.L << a.lw;
+    for (int e = threadIdx.x; e < pts; e += kThreads) {
+      const int q = e & (a.W - 1), i = e >> a.lw;
+      if (q < r.nv) cp_async8(sb + 8u * (uint32_t)(i * P + q), a.in + r.base + q + i * a.pi);
+    }
+  }
+}
+
+// NBUF = 2: the next tile's copies are issued before the current tile is
+// transformed (two tile buffers); NBUF = 1: one buffer, the copies of a
+// tile all in flight at once, other blocks on the multiprocessor overlap.
+template <int DIR, int NBUF>
 __global__ void __launch_bounds__(kThreads) axis_pass_kernel(const Args a) {
   extern __shared__ __align__(16) float2 sm[];
   const int P = a.W + 1;
-  float2* tile = sm;
-  float2* tw = sm + (size_t)a.L * P;
+  const size_t bstride = (size_t)a.L * P;  // buffer b at sm + b * bstride
+  float2* tw = sm + NBUF * bstride;
   unsigned short* pos = reinterpret_cast<unsigned short*>(tw + a.L);
   for (int i = threadIdx.x; i < a.L; i += kThreads) {
     tw[i] = a.tw[i];
     pos[i] = a.pos[i];
   }
   const int pts = a.L << a.lw;
-  for (unsigned t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
-    long long base;
-    int nv;
-    if (a.contiguous) {
-      const long long r0 = (long long)t << a.lw;
-      nv = (int)min((long long)a.W, a.rows - r0);
-      base = r0 * a.L;
-      const float2* src = a.in + base;
-      for (int e = threadIdx.x; e < nv * a.L; e += kThreads) {
-        const unsigned q = fdiv((unsigned)e, a.divL);
-        tile[(e - (int)q * a.L) * P + (int)q] = src[e];
-      }
+  unsigned t = blockIdx.x;
+  if (NBUF == 2 && t < a.ntiles) {
+    load_tile(a, t, sm, P);
+    cp_async_commit();
+  }
+  for (int it = 0; t < a.ntiles; t += gridDim.x, ++it) {
+    float2* tile = sm + (NBUF == 2 ? (it & 1) : 0) * bstride;
+    if (NBUF == 2) {
+      if (t + gridDim.x < a.ntiles) load_tile(a, t + gridDim.x, sm + ((it & 1) ^ 1) * bstride, P);
+      cp_async_commit();
+      cp_async_wait<1>();
     } else {
-      const unsigned outer = fdiv(t, a.divx);
-      const int x0 = (int)(t - outer * (unsigned)a.xtiles) << a.lw;
-      nv = min(a.W, a.nx - x0);
-      const unsigned o1 = fdiv(outer, a.divd1);
-      base = (long long)o1 * a.s1 + (long long)(outer - o1 * (unsigned)a.d1) * a.s0 + x0;
-      for (int e = threadIdx.x; e < pts; e += kThreads) {
-        const int q = e & (a.W - 1), i = e >> a.lw;
-        if (q < nv) tile[i * P + q] = a.in[base + q + i * a.pi];
-      }
+      load_tile(a, t, tile, P);
+      cp_async_commit();
+      cp_async_wait<0>();
     }
     __syncthreads();
     for (int s = 0; s < a.nst; ++s) {
@@ -122,31 +171,35 @@ __global__ void __launch_bounds__(kThreads) axis_pass_kernel(const Args a) {
       __syncthreads();
     }
     const float sc = a.do_scale ? a.scale : 1.0f;
+    const TileRef r = tile_of(a, t);
     if (a.contiguous) {
-      float2* dst = a.out + base;
-      for (int e = threadIdx.x; e < nv * a.L; e += kThreads) {
+      float2* dst = a.out + r.base;
+#pragma unroll 4
+      for (int e = threadIdx.x; e < r.nv * a.L; e += kThreads) {
         const unsigned q = fdiv((unsigned)e, a.divL);
         dst[e] = cscale(tile[pos[e - (int)q * a.L] * P + (int)q], sc);
       }
     } else {
+#pragma unroll 4
       for (int e = threadIdx.x; e < pts; e += kThreads) {
         const int q = e & (a.W - 1), k = e >> a.lw;
-        if (q < nv) a.out[base + q + k * a.pi] = cscale(tile[pos[k] * P + q], sc);
+        if (q < r.nv) a.out[r.base + q + k * a.pi] = cscale(tile[pos[k] * P + q], sc);
       }
     }
-    __syncthreads();  // the tile is reloaded next
+    __syncthreads();  // this buffer is reloaded next
   }
 }
 
 constexpr int kRadices[] = {16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2};
 
-size_t smem_bytes(int L, int W) {
-  return ((size_t)L * (W + 1) + L) * sizeof(float2) + (size_t)L * sizeof(unsigned short);
+size_t smem_bytes(int L, int W, int nbuf) {
+  return ((size_t)nbuf * L * (W + 1) + L) * sizeof(float2) + (size_t)L * sizeof(unsigned short);
 }
-// The largest smem_bytes of any pass (L W <= 8192 pencil points, L <= 512):
-// the kernel's dynamic shared-memory limit is set once to this, since the
-// passes of one plan (different L and W) share the kernel.
-constexpr size_t kSmemLimit = (8192 + 2 * 512) * sizeof(float2) + 512 * sizeof(unsigned short);
+// The largest smem_bytes of any pass (L W <= 8192 pencil points, L <= 512,
+// two buffers): the kernels' dynamic shared-memory limit is set once to
+// this, since the passes of one plan (different L and W) share a kernel.
+constexpr size_t kSmemLimit =
+    (2 * (8192 + 512) + 512) * sizeof(float2) + 512 * sizeof(unsigned short);
 
 }  // namespace ax
 
@@ -199,13 +252,21 @@ int prepare_axis_pass(const AxisTable& tab, int dir, const AxisGeom& g, int sms,
   a.L = tab.L;
   a.nst = tab.nst;
   a.contiguous = g.contiguous;
-  if (g.contiguous) {
-    int lw = 4;  // at least 16 rows, about 8192 points per tile
-    while (lw < 9 && (tab.L << (lw + 1)) <= 8192) ++lw;
-    a.lw = lw;
-  } else {
-    a.lw = 4;  // 16 adjacent pencils: one 128-byte run per element
-  }
+  // two tile buffers (the next tile's copies in flight during this one's
+  // transform) unless they would leave one block per multiprocessor (the
+  // 512-point strided passes, measured faster with one buffer and three
+  // blocks)
+  // (x pass: at least 16 rows, about 8192 points per tile, 4096 with two
+  // buffers; y and z passes: 16 adjacent pencils, one 128-byte run per
+  // element)
+  auto tile_lw = [&](int nb) {
+    int lw = 4;
+    if (g.contiguous)
+      while (lw < 9 && (tab.L << (lw + 1)) <= (nb == 2 ? 4096 : 8192)) ++lw;
+    return lw;
+  };
+  const int nbuf = ax::smem_bytes(tab.L, 1 << tile_lw(2), 2) <= 110 * 1024 ? 2 : 1;
+  a.lw = tile_lw(nbuf);
   a.W = 1 << a.lw;
   int span = tab.L;
   for (int t = 0; t < tab.nst; ++t) {
@@ -236,9 +297,11 @@ int prepare_axis_pass(const AxisTable& tab, int dir, const AxisGeom& g, int sms,
   a.ntiles = (unsigned)ntiles;
   a.scale = g.scale;
   a.do_scale = g.do_scale;
-  const size_t smem = ax::smem_bytes(tab.L, a.W);
-  const void* fn =
-      dir < 0 ? (const void*)&ax::axis_pass_kernel<-1> : (const void*)&ax::axis_pass_kernel<1>;
+  const size_t smem = ax::smem_bytes(tab.L, a.W, nbuf);
+  const void* fn = nbuf == 2 ? (dir < 0 ? (const void*)&ax::axis_pass_kernel<-1, 2>
+                                        : (const void*)&ax::axis_pass_kernel<1, 2>)
+                             : (dir < 0 ? (const void*)&ax::axis_pass_kernel<-1, 1>
+                                        : (const void*)&ax::axis_pass_kernel<1, 1>);
   int per_sm = 0;
   if (smem > ax::kSmemLimit) return FFT3D_ERR_INVALID_ARG;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -251,6 +314,7 @@ int prepare_axis_pass(const AxisTable& tab, int dir, const AxisGeom& g, int sms,
   }
   out->args = a;
   out->dir = dir;
+  out->nbuf = nbuf;
   out->smem = smem;
   out->grid = (int)std::min<long long>(ntiles, (long long)per_sm * sms);
   return FFT3D_SUCCESS;
@@ -261,10 +325,17 @@ cudaError_t launch_axis_pass(const AxisLaunch& l, const float2* in, float2* out,
   ax::Args a = l.args;
   a.in = in;
   a.out = out;
-  if (l.dir < 0)
-    ax::axis_pass_kernel<-1><<<l.grid, ax::kThreads, l.smem, stream>>>(a);
-  else
-    ax::axis_pass_kernel<1><<<l.grid, ax::kThreads, l.smem, stream>>>(a);
+  if (l.nbuf == 2) {
+    if (l.dir < 0)
+      ax::axis_pass_kernel<-1, 2><<<l.grid, ax::kThreads, l.smem, stream>>>(a);
+    else
+      ax::axis_pass_kernel<1, 2><<<l.grid, ax::kThreads, l.smem, stream>>>(a);
+  } else {
+    if (l.dir < 0)
+      ax::axis_pass_kernel<-1, 1><<<l.grid, ax::kThreads, l.smem, stream>>>(a);
+    else
+      ax::axis_pass_kernel<1, 1><<<l.grid, ax::kThreads, l.smem, stream>>>(a);
+  }
   return cudaGetLastError();
 }
 

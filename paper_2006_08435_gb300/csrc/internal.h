@@ -129,6 +129,7 @@ struct AxisArgs {
 struct AxisLaunch {
   AxisArgs args{};
   int dir = -1;
+  int nbuf = 1;  // tile buffers per block
   int grid = 0;
   size_t smem = 0;
 };
