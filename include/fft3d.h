@@ -53,7 +53,14 @@ typedef enum {
   FFT3D_FP32 = 0,        /* plain single precision (the paper's FP64->FP32 step, Abstract/Results) */
   FFT3D_SPLIT_FP16 = 1,  /* radix-16 stages on tensor cores, hi+lo FP16 operands, FP32 accumulate */
   FFT3D_SPLIT_BF16 = 2,  /* same with BF16 hi+lo operands */
-  FFT3D_FP16 = 3         /* radix-16 stages on tensor cores, FP16 hi only (reported, not gated) */
+  FFT3D_FP16 = 3,        /* radix-16 stages on tensor cores, FP16 hi only (reported, not gated) */
+  /* Custom precisions (the paper's closing paragraph names custom-precision
+   * floating-point units as future work): operand formats of the tcgen05
+   * kernels only (64^3 and 128^3, variant 9), each with one power-of-two
+   * exponent per 64-point pencil; reported, not gated. */
+  FFT3D_BFP16 = 4,       /* block floating point: 11-bit fixed-point mantissas in FP16, B = hi + lo */
+  FFT3D_SPLIT_FP8 = 5,   /* E4M3 hi + lo operands, three products (kind::f8f6f4) */
+  FFT3D_FP8 = 6          /* E4M3 operands, one product */
 } fft3d_precision;
 
 /* Sign of the exponent of W (Eq. 1 uses -1). */
@@ -146,9 +153,13 @@ int fft3d_schedule_preview(int count, const int* dims, int concurrency, double l
  * kk / 8) * 128 + (nn % 8) * 16 + (kk % 8) * 2) / 2 of `out` holds term 0
  * hi = rn(b) and term 1 lo = rn(b - hi) of entry b, each rounded once from
  * its FP64 value to FP16 (precision FFT3D_SPLIT_FP16 or FFT3D_FP16) or BF16
- * (FFT3D_SPLIT_BF16).  `out` holds 8192 halfwords.  Errors:
- * FFT3D_ERR_NULL_PTR, FFT3D_ERR_INVALID_ARG (precision FFT3D_FP32 or out of
- * range).
+ * (FFT3D_SPLIT_BF16).  `out` holds 8192 halfwords.  FFT3D_BFP16 uses the
+ * FP16 table.  FFT3D_SPLIT_FP8 / FFT3D_FP8: byte (term * 4 + k1) * 1024 +
+ * ((nn / 8) * 2 + kk / 16) * 128 + (nn % 8) * 16 + kk % 16 of `out` (the
+ * first 8 KB; the rest is zero) holds the E4M3 code of hi = rn(16 b)
+ * (term 0) and lo = rn(16 b - hi) (term 1), rounded to nearest even with
+ * saturation.  Errors: FFT3D_ERR_NULL_PTR, FFT3D_ERR_INVALID_ARG (precision
+ * FFT3D_FP32 or out of range).
  */
 int fft3d_tc_operand_table(int precision, uint16_t* out);
 
@@ -158,8 +169,9 @@ int fft3d_tc_operand_table(int precision, uint16_t* out);
  *                and edges without a fused kernel take the general path).
  *   batch      : number of grids, >= 1, packed back to back.
  *   precision  : fft3d_precision; the tensor-core kinds (SPLIT_FP16,
- *                SPLIT_BF16, FP16) are planned for cubic n = 64 and 128
- *                (FFT3D_ERR_UNSUPPORTED_PRECISION otherwise).
+ *                SPLIT_BF16, FP16, BFP16, SPLIT_FP8, FP8) are planned for
+ *                cubic n = 64 and 128 (FFT3D_ERR_UNSUPPORTED_PRECISION
+ *                otherwise).
  *   direction  : FFT3D_FORWARD or FFT3D_INVERSE.
  *   norm       : fft3d_norm.
  *   out_plan   : receives the handle (set to NULL on failure).

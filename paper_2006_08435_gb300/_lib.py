@@ -13,6 +13,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libfft3d.so")
 
 FFT3D_FP32, FFT3D_SPLIT_FP16, FFT3D_SPLIT_BF16, FFT3D_FP16 = 0, 1, 2, 3
+FFT3D_BFP16, FFT3D_SPLIT_FP8, FFT3D_FP8 = 4, 5, 6
 FFT3D_FORWARD, FFT3D_INVERSE = -1, 1
 FFT3D_NORM_NONE, FFT3D_NORM_BY_N, FFT3D_NORM_ORTHO = 0, 1, 2
 FFT3D_SUCCESS = 0

@@ -3,6 +3,7 @@
 // launches.  See include/fft3d.h for the contract of each entry point.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -120,6 +121,30 @@ static void mma_fragments(int prec, uint32_t* out /* tc::kFragWords */) {
 // hi halves, 1 the lo halves (FP16, or BF16 for prec 2): hi = rn(b),
 // lo = rn(b - hi), each rounded once from the FP64 value.
 static void umma_b_table(int prec, uint16_t* out /* 8192 */) {
+  if (prec == FFT3D_SPLIT_FP8 || prec == FFT3D_FP8) {
+    // E4M3 entries of 16 b: hi = rn(16 b), lo = rn(16 b - hi) (round to
+    // nearest even, saturating), byte ((row / 8) * 2 + kk / 16) * 128 +
+    // (row % 8) * 16 + kk % 16 of block (term * 4 + k1) * 1024
+    unsigned char* bytes = reinterpret_cast<unsigned char*>(out);
+    std::memset(bytes, 0, 16384);
+    for (int k1 = 0; k1 < 4; ++k1)
+      for (int row = 0; row < 32; ++row)
+        for (int kk = 0; kk < 32; ++kk) {
+          const int k2 = row / 2, d = row % 2, n2 = kk / 2, c = kk % 2;
+          const int m = (n2 * (k1 + 4 * k2)) % 64;
+          const double a = -2.0 * 3.14159265358979323846 * (double)m / 64.0;
+          const double wr = std::cos(a), wi = std::sin(a);
+          const double v = 16.0 * (c == 0 ? (d == 0 ? wr : wi) : (d == 0 ? -wi : wr));
+          const __nv_fp8_storage_t hi = __nv_cvt_double_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+          const __half_raw hr = __nv_cvt_fp8_to_halfraw(hi, __NV_E4M3);
+          const double hv = (double)__half2float(__half(hr));
+          const __nv_fp8_storage_t lo = __nv_cvt_double_to_fp8(v - hv, __NV_SATFINITE, __NV_E4M3);
+          const int byte = ((row / 8) * 2 + kk / 16) * 128 + (row % 8) * 16 + kk % 16;
+          bytes[(0 * 4 + k1) * 1024 + byte] = hi;
+          bytes[(1 * 4 + k1) * 1024 + byte] = lo;
+        }
+    return;
+  }
   for (int k1 = 0; k1 < 4; ++k1)
     for (int row = 0; row < 32; ++row)
       for (int kk = 0; kk < 32; ++kk) {
@@ -163,6 +188,8 @@ static bool fused_size(int n) { return fused_slot(n) >= 0; }
 // edge's default kernel.
 std::vector<int> variant_candidates(bool mixed, int n, int precision) {
   if (mixed) return {0, 1};
+  // the block-floating-point and FP8 kinds exist on the tcgen05 kernels only
+  if (precision >= FFT3D_BFP16) return {9};
   if (precision != FFT3D_FP32) return n == 64 ? std::vector<int>{0, 8, 9} : std::vector<int>{0, 9};
   if (!fused_size(n)) return {kGeneralVariant};
   switch (n) {
@@ -182,6 +209,7 @@ int builtin_default_variant(bool mixed, int n, int batch, int precision) {
   // tensor-core precisions: the tcgen05 kernels (measured 0.50 of the HBM
   // roofline at 64^3 x 256 against 0.40 for mma.sync and 0.24 for the plain
   // persistent kernel; 0.37 at 128^3 x 32 against 0.20)
+  if (precision >= FFT3D_BFP16) return 9;
   if (precision != FFT3D_FP32) return (n == 64 && batch >= 16) || (n == 128 && batch >= 4) ? 9 : 0;
   if (n == 128) return batch >= 4 ? 6 : 2;  // split-y from 4 grids, measured faster
   if ((n == 16 || n == 32) && batch >= 64) return 3;
@@ -432,7 +460,7 @@ void set_scale(fft3d_plan p, double points) {
 int validate_common(int precision, int direction, int norm, fft3d_plan* out_plan) {
   if (!out_plan) return FFT3D_ERR_NULL_PTR;
   *out_plan = nullptr;
-  if (precision < FFT3D_FP32 || precision > FFT3D_FP16) return FFT3D_ERR_INVALID_ARG;
+  if (precision < FFT3D_FP32 || precision > FFT3D_FP8) return FFT3D_ERR_INVALID_ARG;
   if (direction != FFT3D_FORWARD && direction != FFT3D_INVERSE) return FFT3D_ERR_INVALID_ARG;
   if (norm < FFT3D_NORM_NONE || norm > FFT3D_NORM_ORTHO) return FFT3D_ERR_INVALID_ARG;
   return FFT3D_SUCCESS;
@@ -869,7 +897,7 @@ int fft3d_size_supported(int n) { return fused_size(n) || general_size(n) ? 1 : 
 
 int fft3d_tc_operand_table(int precision, uint16_t* out) {
   if (!out) return FFT3D_ERR_NULL_PTR;
-  if (precision < FFT3D_SPLIT_FP16 || precision > FFT3D_FP16) return FFT3D_ERR_INVALID_ARG;
+  if (precision < FFT3D_SPLIT_FP16 || precision > FFT3D_FP8) return FFT3D_ERR_INVALID_ARG;
   umma_b_table(precision, out);
   return FFT3D_SUCCESS;
 }

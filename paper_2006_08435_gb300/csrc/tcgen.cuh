@@ -39,6 +39,8 @@
 // apart along N (the stride byte offset).
 #pragma once
 
+#include <cuda_fp8.h>
+
 #include "tcrow.cuh"
 
 namespace fft3d {
@@ -59,6 +61,34 @@ using tcr::sts4;
 constexpr int kBBytes = 2 * 4 * 2048;  // B operands: term (hi, lo) x k1 x 32 x 32 halves
 constexpr int kTmemCols = 512;         // 2 groups x (A: 8 x 16, D: 4 x 32 columns)
 
+// Operand kinds (PREC, the fft3d_precision value):
+//   1 split FP16, 2 split BF16: A = hi + lo (hi a fixed-point mantissa under
+//     the pencil's exponent, lo the rounded remainder), B = hi + lo;
+//     A_hi B_hi + A_hi B_lo + A_lo B_hi.
+//   3 FP16: A = rn(x), B = hi; A B_hi.
+//   4 block floating point FP16: A = the fixed-point mantissa hi alone (one
+//     exponent per pencil, values multiples of 16 below 2^15: 11 bits and a
+//     sign), B = hi + lo; A_hi B_hi + A_hi B_lo -- the error is the data's
+//     quantisation alone.
+//   5 split FP8 (E4M3): A = hi + lo, each rounded to E4M3, B = 16 b split the
+//     same way; A_hi B_hi + A_hi B_lo + A_lo B_hi, kind::f8f6f4 (K = 32 per
+//     product).
+//   6 FP8 (E4M3): A = rn(x), B = hi; A B_hi.
+template <int PREC>
+struct Kind {
+  static constexpr bool fp8 = PREC == 5 || PREC == 6;
+  static constexpr bool a_lo = PREC == 1 || PREC == 2 || PREC == 5;  // an A_lo B_hi product
+  static constexpr bool b_lo = PREC != 3 && PREC != 6;               // an A_hi B_lo product
+  static constexpr bool neg_hi = PREC == 1 || PREC == 2 || PREC == 4;  // -hi stored (fixed point)
+  // the pencil's largest component is scaled to [2^E, 2^(E+1)): below 2^15
+  // after the radix-4 stage for the FP16 containers, below 448 (the E4M3
+  // maximum) for FP8; block floating point measures it after the radix-4
+  // stage, so that its largest mantissa uses all 11 bits
+  static constexpr bool post = PREC == 4;
+  static constexpr int E = fp8 ? 5 : (post ? 14 : 12);
+  static constexpr float bscale = fp8 ? 16.0f : 1.0f;  // B table entries are bscale * b
+};
+
 // Shared-memory matrix descriptor: start address, leading byte offset 128
 // (next core matrix along K), stride byte offset 512 (next eight rows),
 // descriptor version 1, no swizzle.
@@ -67,13 +97,50 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
          ((uint64_t)(512u >> 4) << 32) | (1ull << 46);
 }
 
-// Instruction descriptor of kind::f16: FP32 accumulator, A and B FP16 (or
-// BF16 for PREC 2), A negated if NEG, both K-major, N = 32, M = 128.
+// Shared-memory descriptor of the FP8 B operands: 8-row x 16-byte core
+// matrices (16 E4M3 entries along K per row), the next core matrix along K
+// 128 bytes on, the next eight rows 256 bytes on.
+__device__ __forceinline__ uint64_t sdesc8(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(128u >> 4) << 16) |
+         ((uint64_t)(256u >> 4) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16 (A and B FP16, or BF16 for PREC 2) and
+// of kind::f8f6f4 (A and B E4M3, format code 0): FP32 accumulator, A
+// negated if NEG, both K-major, N = 32, M = 128.
 template <int PREC, bool NEG = false>
 constexpr uint32_t idesc() {
   constexpr uint32_t ab = PREC == 2 ? 1u : 0u;
   return (1u << 4) | (ab << 7) | (ab << 10) | ((NEG ? 1u : 0u) << 13) | ((32u >> 3) << 17) |
          ((128u >> 4) << 24);
+}
+
+// Two floats to two E4M3 bytes (round to nearest even, saturating to the
+// largest finite value), x.x in the low byte, and back.
+__device__ __forceinline__ uint32_t to_e4m3x2(float2 v) {
+  return (uint32_t)__nv_cvt_float2_to_fp8x2(v, __NV_SATFINITE, __NV_E4M3);
+}
+__device__ __forceinline__ float2 from_e4m3x2(uint32_t b) {
+  const __half2_raw h = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)b, __NV_E4M3);
+  return __half22float2(*reinterpret_cast<const __half2*>(&h));
+}
+
+// FP8 A operands: y = x s and the next point's, rounded to E4M3 as hi and
+// (split kind) lo = rn(y - hi); one 32-bit word holds the two points
+// (re, im, re, im from the low byte).
+template <int PREC>
+__device__ __forceinline__ void split8(float2 x0, float2 x1, float2 s, uint32_t& hi,
+                                       uint32_t& lo) {
+  const float2 y0 = mul2(x0, s), y1 = mul2(x1, s);
+  const uint32_t h0 = to_e4m3x2(y0), h1 = to_e4m3x2(y1);
+  hi = h0 | (h1 << 16);
+  if constexpr (Kind<PREC>::a_lo) {
+    const uint32_t l0 = to_e4m3x2(csub(y0, from_e4m3x2(h0)));
+    const uint32_t l1 = to_e4m3x2(csub(y1, from_e4m3x2(h1)));
+    lo = l0 | (l1 << 16);
+  } else {
+    lo = 0u;
+  }
 }
 
 // y = x s split as hi + lo for the split kinds, returning -hi: the adding
@@ -82,6 +149,7 @@ constexpr uint32_t idesc() {
 // FP16 returns hi = rn(y) itself.
 template <int PREC>
 __device__ __forceinline__ void split_nhi(float2 x, float2 s, uint32_t& nhi, uint32_t& lo) {
+  static_assert(!Kind<PREC>::fp8, "FP8 operands: split8");
   if constexpr (PREC == 3) {
     tcr::split<3>(x, s, nhi, lo);
   } else {
@@ -109,6 +177,13 @@ __device__ __forceinline__ void umma(uint32_t d, uint32_t a, uint64_t b, uint32_
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+      "r"(a), "l"(b), "r"(id), "r"(acc));
+}
+// The same for 8-bit operands (K = 32 per product).
+__device__ __forceinline__ void umma8(uint32_t d, uint32_t a, uint64_t b, uint32_t id, int acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
       "r"(a), "l"(b), "r"(id), "r"(acc));
 }
 
@@ -212,9 +287,12 @@ struct Pass {
 template <int DIR, int PREC, class Store>
 __device__ __forceinline__ bool pass(float2 (&v)[64], const Pass& P, unsigned& phase,
                                      const FusedArgs& a, float out_scale, Store store) {
-  const float m = absmax64(v);
-  const int ex = m > 0.0f ? tc::exponent_of(m) : 0;
-  const float sc = tc::pow2(12 - ex);
+  using KD = Kind<PREC>;
+  int ex = 0;
+  if constexpr (!KD::post) {
+    const float m = absmax64(v);
+    ex = m > 0.0f ? tc::exponent_of(m) : 0;
+  }
   const float cj = DIR > 0 ? -1.0f : 1.0f;
   // radix-4 over n1: v[16 k1 + n2] = R[k1][n2]
 #pragma unroll
@@ -226,18 +304,36 @@ __device__ __forceinline__ bool pass(float2 (&v)[64], const Pass& P, unsigned& p
     v[32 + n2] = q[2];
     v[48 + n2] = q[3];
   }
+  if constexpr (KD::post) {
+    const float m = absmax64(v);
+    ex = m > 0.0f ? tc::exponent_of(m) : 0;
+  }
+  const float sc = tc::pow2(KD::E - ex);
   // A rows: lane gt of matrix (term, k1), column n2 = (re, im) of point n2
   const float2 s2 = make_float2(sc, cj * sc);
+  if constexpr (KD::fp8) {
+    // 16 points of a row: 32 E4M3 entries, 8 columns
 #pragma unroll
-  for (int k1 = 0; k1 < 4; ++k1)
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
+    for (int k1 = 0; k1 < 4; ++k1) {
       uint32_t h[8], l[8];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) split_nhi<PREC>(v[16 * k1 + 8 * e + i], s2, h[i], l[i]);
-      tmem_st8(P.col + P.lanes + 16 * k1 + 8 * e, h);
-      if constexpr (PREC != 3) tmem_st8(P.col + P.lanes + 16 * (4 + k1) + 8 * e, l);
+      for (int i = 0; i < 8; ++i)
+        split8<PREC>(v[16 * k1 + 2 * i], v[16 * k1 + 2 * i + 1], s2, h[i], l[i]);
+      tmem_st8(P.col + P.lanes + 16 * k1, h);
+      if constexpr (KD::a_lo) tmem_st8(P.col + P.lanes + 16 * (4 + k1), l);
     }
+  } else {
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        uint32_t h[8], l[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) split_nhi<PREC>(v[16 * k1 + 8 * e + i], s2, h[i], l[i]);
+        tmem_st8(P.col + P.lanes + 16 * k1 + 8 * e, h);
+        if constexpr (KD::a_lo) tmem_st8(P.col + P.lanes + 16 * (4 + k1) + 8 * e, l);
+      }
+  }
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
   tc_fence_before();
   named_bar(1 + P.g, Cfg<64>::GT);  // every A row is written, every D row read
@@ -246,18 +342,27 @@ __device__ __forceinline__ bool pass(float2 (&v)[64], const Pass& P, unsigned& p
     // keep the tensor cores busier than one (each instruction costs its
     // issuing thread some tens of cycles)
     tc_fence_after();
-    // the A_hi columns hold -hi for the split kinds: those products negate A
-    constexpr uint32_t idh = idesc<PREC, PREC != 3>(), idl = idesc<PREC>();
-    {
-      const int k1 = P.gt >> 5;
-      const uint32_t d = P.col + 128 + 32 * k1;
-      const uint32_t ahi = P.col + 16 * k1, alo = P.col + 16 * (4 + k1);
+    // the A_hi columns hold -hi for the fixed-point kinds: those products
+    // negate A
+    constexpr uint32_t idh = idesc<PREC, KD::neg_hi>(), idl = idesc<PREC>();
+    const int k1 = P.gt >> 5;
+    const uint32_t d = P.col + 128 + 32 * k1;
+    const uint32_t ahi = P.col + 16 * k1, alo = P.col + 16 * (4 + k1);
+    if constexpr (KD::fp8) {
+      // one product per term (K = 32); B blocks of 1 KB
+      const uint32_t bhi = P.bsm + k1 * 1024, blo = P.bsm + (4 + k1) * 1024;
+      umma8(d, ahi, sdesc8(bhi), idh, 0);
+      if constexpr (KD::b_lo) umma8(d, ahi, sdesc8(blo), idh, 1);
+      if constexpr (KD::a_lo) umma8(d, alo, sdesc8(bhi), idl, 1);
+    } else {
       const uint32_t bhi = P.bsm + k1 * 2048, blo = P.bsm + (4 + k1) * 2048;
 #pragma unroll
       for (int ks = 0; ks < 2; ++ks) umma(d, ahi + 8 * ks, sdesc(bhi + 256 * ks), idh, ks);
-      if constexpr (PREC != 3) {
+      if constexpr (KD::b_lo) {
 #pragma unroll
         for (int ks = 0; ks < 2; ++ks) umma(d, ahi + 8 * ks, sdesc(blo + 256 * ks), idh, 1);
+      }
+      if constexpr (KD::a_lo) {
 #pragma unroll
         for (int ks = 0; ks < 2; ++ks) umma(d, alo + 8 * ks, sdesc(bhi + 256 * ks), idl, 1);
       }
@@ -267,7 +372,7 @@ __device__ __forceinline__ bool pass(float2 (&v)[64], const Pass& P, unsigned& p
   if (!group_and(1 + P.g, Cfg<64>::GT, warp_wait(P.bar, phase & 1, a))) return false;
   ++phase;
   tc_fence_after();
-  const float inv = tc::pow2(ex - 12) * out_scale;
+  const float inv = tc::pow2(ex - KD::E) * (out_scale / KD::bscale);
   const float2 o = make_float2(inv, cj * inv);
   float dk[4][32];  // the four D rows of this pencil, read before one wait
 #pragma unroll

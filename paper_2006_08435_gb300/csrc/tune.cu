@@ -254,7 +254,7 @@ int fft3d_autotune(int n, int batch, int precision, int direction, const char* c
   if (!best_variant) return FFT3D_ERR_NULL_PTR;
   if (n < 1 || batch < 1) return FFT3D_ERR_INVALID_ARG;
   if (fft3d_size_supported(n) != 1) return FFT3D_ERR_UNSUPPORTED_SIZE;
-  if (precision < FFT3D_FP32 || precision > FFT3D_FP16) return FFT3D_ERR_INVALID_ARG;
+  if (precision < FFT3D_FP32 || precision > FFT3D_FP8) return FFT3D_ERR_INVALID_ARG;
   if (direction != FFT3D_FORWARD && direction != FFT3D_INVERSE) return FFT3D_ERR_INVALID_ARG;
   return run_autotune(false, n, batch, precision, direction, nullptr, 0, cache_path, best_variant);
 }

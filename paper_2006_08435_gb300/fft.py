@@ -15,7 +15,8 @@ import torch
 from . import _lib as L
 
 _PREC = {"fp32": L.FFT3D_FP32, "split_fp16": L.FFT3D_SPLIT_FP16,
-         "split_bf16": L.FFT3D_SPLIT_BF16, "fp16": L.FFT3D_FP16}
+         "split_bf16": L.FFT3D_SPLIT_BF16, "fp16": L.FFT3D_FP16, "bfp16": L.FFT3D_BFP16,
+         "split_fp8": L.FFT3D_SPLIT_FP8, "fp8": L.FFT3D_FP8}
 _NORM = {"none": L.FFT3D_NORM_NONE, "n": L.FFT3D_NORM_BY_N, "by_n": L.FFT3D_NORM_BY_N,
          "ortho": L.FFT3D_NORM_ORTHO}
 

@@ -46,6 +46,7 @@ def _create(lib, *args):
 @pytest.mark.parametrize("args,code", [
     ((64, 64, 64, 0, 0, -1, 0), L.FFT3D_ERR_INVALID_ARG),      # batch 0
     ((64, 64, 64, 1, 7, -1, 0), L.FFT3D_ERR_INVALID_ARG),      # precision
+    ((48, 48, 48, 1, 5, -1, 0), L.FFT3D_ERR_UNSUPPORTED_PRECISION),  # FP8 at 64, 128 only
     ((64, 64, 64, 1, 0, 0, 0), L.FFT3D_ERR_INVALID_ARG),       # direction
     ((64, 64, 64, 1, 0, -1, 5), L.FFT3D_ERR_INVALID_ARG),      # norm
     ((0, 64, 64, 1, 0, -1, 0), L.FFT3D_ERR_INVALID_ARG),       # zero edge
@@ -243,8 +244,68 @@ def test_tc_operand_table_is_the_twiddled_dft16(fft3d_lib, prec):
 def test_tc_operand_table_errors(fft3d_lib):
     buf = (ctypes.c_uint16 * 8192)()
     assert fft3d_lib.fft3d_tc_operand_table(1, None) == L.FFT3D_ERR_NULL_PTR
-    for bad in (0, 4, -1):
+    for bad in (0, 7, -1):
         assert fft3d_lib.fft3d_tc_operand_table(bad, buf) == L.FFT3D_ERR_INVALID_ARG
+
+
+def _e4m3_values():
+    """Every finite E4M3 value by code (1 sign, 4 exponent bits with bias 7,
+    3 mantissa bits; exponent field 0 is subnormal, 2^-6 m / 8; the all-ones
+    code is NaN, so the largest finite value is 2^8 * 1.75 = 448)."""
+    vals = {}
+    for code in range(256):
+        s, e, m = code >> 7, (code >> 3) & 15, code & 7
+        if e == 15 and m == 7:
+            continue
+        v = (m / 8.0) * 2.0 ** -6 if e == 0 else (1 + m / 8.0) * 2.0 ** (e - 7)
+        vals[code] = -v if s else v
+    return vals
+
+
+def _e4m3_rn(x, vals):
+    """Round to nearest E4M3, ties to the even code, saturating at +-448."""
+    x = max(-448.0, min(448.0, x))
+    best = min(vals, key=lambda c: (abs(vals[c] - x), c & 1, c))
+    return vals[best]
+
+
+def test_tc_operand_table_fp8_is_the_twiddled_dft16(fft3d_lib):
+    """The FP8 (E4M3) B operands: hi = rn(16 b), lo = rn(16 b - hi) of the
+    FP64 entry b, at the documented byte positions, the same for the split
+    and the plain FP8 kinds; hi + lo reproduces 16 times the complex matrix
+    to the E4M3 resolution; the second half of the buffer is zero."""
+    vals = _e4m3_values()
+    for prec in (L.FFT3D_SPLIT_FP8, L.FFT3D_FP8):
+        buf = (ctypes.c_uint16 * 8192)()
+        assert fft3d_lib.fft3d_tc_operand_table(prec, buf) == 0
+        raw = np.frombuffer(buf, dtype=np.uint8)
+        assert not raw[8192:].any()
+        for k1 in range(4):
+            m_rec = np.zeros((16, 16), np.complex128)
+            for nn in range(32):
+                for kk in range(32):
+                    k2, d, n2, c = nn // 2, nn % 2, kk // 2, kk % 2
+                    a = -2.0 * math.pi * ((n2 * (k1 + 4 * k2)) % 64) / 64.0
+                    wr, wi = math.cos(a), math.sin(a)
+                    b = 16.0 * ((wr if d == 0 else wi) if c == 0 else (-wi if d == 0 else wr))
+                    off = ((nn // 8) * 2 + kk // 16) * 128 + (nn % 8) * 16 + kk % 16
+                    hi = vals[int(raw[(0 * 4 + k1) * 1024 + off])]
+                    lo = vals[int(raw[(1 * 4 + k1) * 1024 + off])]
+                    assert hi == _e4m3_rn(b, vals)
+                    assert lo == _e4m3_rn(b - hi, vals)
+                    if c == 0:
+                        m_rec[n2, k2] += (hi + lo) if d == 0 else 1j * (hi + lo)
+            n2g, k2g = np.meshgrid(np.arange(16), np.arange(16), indexing="ij")
+            expect = 16.0 * np.exp(-2j * np.pi * n2g * (k1 + 4 * k2g) / 64)
+            assert np.abs(m_rec - expect).max() < 2.0 ** -4
+
+
+def test_tc_operand_table_bfp16_uses_the_fp16_table(fft3d_lib):
+    a = (ctypes.c_uint16 * 8192)()
+    b = (ctypes.c_uint16 * 8192)()
+    assert fft3d_lib.fft3d_tc_operand_table(L.FFT3D_BFP16, a) == 0
+    assert fft3d_lib.fft3d_tc_operand_table(L.FFT3D_SPLIT_FP16, b) == 0
+    assert bytes(a) == bytes(b)
 
 
 def _create_real(lib, *args):
