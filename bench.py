@@ -13,7 +13,8 @@ transform = 16 * N^3 (one read and one write of the grid).
 
 The small workloads exist for profiler captures of the same kernels.  Beside
 the headline the line carries sub-objects: split_fp16 (the same batch in
-split FP16), real_r2c_fp32 (real grids), w64x256 (64^3 x 256 in FP32 and
+split FP16), tensor_core_kinds (split BF16, FP16, block floating point
+FP16, split FP8, FP8 on the same batch), real_r2c_fp32 (real grids), w64x256 (64^3 x 256 in FP32 and
 split FP16), mixed_c2 (64 mixed-edge grids, forward + inverse in one CUDA
 graph) and batch1 (one grid per launch, L2 flushed, the paper's setting).
 
@@ -358,6 +359,24 @@ def run_ours(args, ws, rank, local):
         split = {"value": whole_job_rate(ws, batch, 1, ms16), "unit": "transforms/s", "steps": k16,
                  "ms_per_step": ms16}
 
+    # the other tensor-core operand kinds on the same batch (accuracy in the
+    # error study of the GPU tests): throughput of each, timed like the
+    # split leg
+    kinds = None
+    if not args.no_split:
+        kinds = {}
+        for kind in ("split_bf16", "fp16", "bfp16", "split_fp8", "fp8"):
+            pk = Plan(n, n, n, batch, precision=kind)
+            for _ in range(3):
+                pk.execute(x, y, stream)
+            barrier()
+            kk = max(1, args.steps // 4)
+            msk = max_over_ranks(timed_ms(lambda: pk.execute(x, y, stream), kk, stream), ws, dev)
+            assert pk.device_status() == 0
+            kinds[kind] = {"value": whole_job_rate(ws, batch, 1, msk), "ms_per_step": msk,
+                           "steps": kk, "variant": pk.variant}
+            del pk
+
     # real grids (the real parts of the same batch): forward R2C to half
     # spectra, two grids per complex transform (pack, transform, separate)
     real = None
@@ -510,6 +529,10 @@ def run_ours(args, ws, rank, local):
     if split is not None:
         split["roofline_frac"] = 16.0 * n ** 3 * batch / (split["ms_per_step"] / 1e3) / 1e9 / peak
         line["split_fp16"] = split
+    if kinds is not None:
+        for v in kinds.values():
+            v["roofline_frac"] = 16.0 * n ** 3 * batch / (v["ms_per_step"] / 1e3) / 1e9 / peak
+        line["tensor_core_kinds"] = kinds
     if real is not None:
         real["roofline_frac"] = (real["bytes_per_transform"] * batch / (real["ms_per_step"] / 1e3)
                                  / 1e9 / peak)

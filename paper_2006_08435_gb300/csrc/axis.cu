@@ -27,7 +27,7 @@
 #include <algorithm>
 #include <cmath>
 
-#include "../../include/fft3d.h"
+#include "fft3d.h"
 #include "codelets.cuh"
 #include "internal.h"
 

@@ -14,7 +14,7 @@
 #include <new>
 #include <vector>
 
-#include "../../include/fft3d.h"
+#include "fft3d.h"
 #include "internal.h"
 #include "schedule.h"
 #include "sizes.h"
@@ -205,13 +205,18 @@ std::vector<int> variant_candidates(bool mixed, int n, int precision) {
 // cluster-fused kernel for 16^3 and 32^3 batches of 64 grids or more, the
 // plain persistent kernel otherwise.
 int builtin_default_variant(bool mixed, int n, int batch, int precision) {
-  if (mixed) return 0;
+  // mixed edges: one launch per distinct edge (the mixed workload of 64
+  // grids: 0.41 ms against 0.48 ms for the one mixed-edge launch)
+  if (mixed) return 1;
   // tensor-core precisions: the tcgen05 kernels (measured 0.50 of the HBM
   // roofline at 64^3 x 256 against 0.40 for mma.sync and 0.24 for the plain
   // persistent kernel; 0.37 at 128^3 x 32 against 0.20)
   if (precision >= FFT3D_BFP16) return 9;
   if (precision != FFT3D_FP32) return (n == 64 && batch >= 16) || (n == 128 && batch >= 4) ? 9 : 0;
-  if (n == 128) return batch >= 4 ? 6 : 2;  // split-y from 4 grids, measured faster
+  // split-y from 2 grids (L2 flushed: 37.5 us for two, 43.7 us for three,
+  // the fastest); one grid: the plain persistent kernel (26.7 us against
+  // 32.4 us for the TMA-fed kernel, 34.4 us for split-y)
+  if (n == 128) return batch >= 2 ? 6 : 0;
   if ((n == 16 || n == 32) && batch >= 64) return 3;
   if (n == 64 && batch >= 128) return 8;  // two-plane items, measured faster from 128 grids
   if (n == 64 && batch >= 16) return 7;   // thread-per-pencil, measured faster from 16 grids
@@ -703,8 +708,13 @@ int create_mixed(int count, const int* dims, int direction, int norm, int varian
       Unit u;
       for (int g = 0; g < count; ++g)
         if (p->dims[g] == n) u.grids.push_back(g);
-      u.kernel = fused_kernel_info(
-          n, direction, builtin_default_variant(false, n, (int)u.grids.size(), FFT3D_FP32));
+      // the edge's default kernel, unless it is one of the tensor-map kernels
+      // (64^3: 7, 8; 128^3: 6), which need the unit's grids as one packed
+      // batch; the unit addresses its grids through the plan's map, so those
+      // edges take the fastest kernel that does (64^3: 6, 128^3: 2)
+      int v = builtin_default_variant(false, n, (int)u.grids.size(), FFT3D_FP32);
+      if ((n == 64 && (v == 7 || v == 8)) || (n == 128 && v == 6)) v = n == 64 ? 6 : 2;
+      u.kernel = fused_kernel_info(n, direction, v);
       p->units.push_back(u);
     }
   }

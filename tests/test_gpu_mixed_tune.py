@@ -94,11 +94,37 @@ def test_mixed_schedules_agree(cuda, mixed_env, variant):
         assert oracle.rel_l2(outs[i].cpu().numpy().reshape(n, n, n), ref) <= FP32_TOL
 
 
+def test_per_edge_schedule_with_many_grids_per_edge(cuda, mixed_env):
+    """One launch per edge (variant 1) when an edge has enough grids that its
+    default kernel would be a tensor-map kernel (which needs one packed
+    batch): the 64 grids of the mixed workload agree with the one-launch
+    schedule, and sampled grids with the oracle."""
+    from paper_2006_08435_gb300 import MixedPlan
+    sizes = synth.mixed_sizes(64, seed=0) + [64] * 16
+    grids, packed = _packed(sizes, seed=8)
+    outs = []
+    for variant in (0, 1):
+        os.environ["FFT3D_MIXED_VARIANT"] = str(variant)
+        p = MixedPlan(sizes)
+        assert p.variant == variant
+        y = torch.empty_like(packed)
+        p.execute(packed, y)
+        torch.cuda.synchronize()
+        assert p.device_status() == 0
+        outs.append(y)
+    assert oracle.rel_l2(outs[1].cpu().numpy(), outs[0].cpu().numpy()) <= FP32_TOL
+    yc = outs[1].cpu().numpy()
+    for i in (sizes.index(128), len(sizes) - 1):
+        n = sizes[i]
+        ref = oracle.dft3d(grids[i].astype(np.complex128), -1)
+        assert oracle.rel_l2(yc[p.offsets[i]:p.offsets[i + 1]].reshape(n, n, n), ref) <= FP32_TOL
+
+
 def test_autotune_records_and_plans_use_the_choice(cuda, tmp_path, monkeypatch):
     from paper_2006_08435_gb300 import Plan, MixedPlan, autotune, autotune_mixed
     cache = str(tmp_path / "tune.json")
     best = autotune(64, 16, cache_path=cache)
-    assert best in range(9)  # the 64^3 candidates
+    assert best in list(range(9)) + [10]  # the 64^3 candidates
     sizes = synth.mixed_sizes(16, seed=3)
     best_m = autotune_mixed(sizes, cache_path=cache)
     assert best_m in (0, 1)
