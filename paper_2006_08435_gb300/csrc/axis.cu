@@ -8,9 +8,11 @@
 // [i][q] (element i of pencil q at i * (W + 1) + q; the odd pitch keeps the
 // column accesses of the x pass free of bank conflicts):
 //   x pass (contiguous pencils): W consecutive rows, read row by row;
-//   y and z passes (strided): the W = 16 pencils at x0 .. x0 + 15 of one
-//     (grid, z) or (grid, y) slice, element i of all 16 being one 128-byte
-//     run in memory.
+//   y and z passes (strided): the 16 pencils at x0 .. x0 + 15 of W / 16
+//     consecutive (grid, z) or (grid, y) slices, element i of the 16 of a
+//     slice being one 128-byte run in memory.
+// A tile holds about 8192 points (4096 per buffer when two buffers let the
+// next tile's copies run during this one's transform).
 // The L-point transform of each pencil runs in place in the tile as
 // decimation in frequency over the radices R_0, R_1, ... (product L):
 // stage t splits each block of N_t = L / (R_0 ... R_{t-1}) points into R_t
@@ -80,11 +82,16 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Where tile t lives: its first element and how many of its W pencils
-// exist (the last row tile, or an x tile at the edge, can be partial).
+// Where tile t lives.  x pass: W consecutive rows from base (nv of them
+// exist; the last tile can be partial).  y and z passes: the 16 pencils at
+// x0 .. x0 + 15 (nvx < 16 at the x edge) of G = W / 16 consecutive slices
+// o0 .. o0 + G - 1 (ng of them exist); pencil c of the tile is (g, q) =
+// (c / 16, c % 16).
 struct TileRef {
-  long long base;
-  int nv;
+  long long base;  // x pass
+  int nv;          // x pass: rows
+  unsigned o0;     // strided: first slice
+  int x0, nvx, ng;
 };
 __device__ __forceinline__ TileRef tile_of(const Args& a, unsigned t) {
   TileRef r;
@@ -93,16 +100,21 @@ __device__ __forceinline__ TileRef tile_of(const Args& a, unsigned t) {
     r.nv = (int)min((long long)a.W, a.rows - r0);
     r.base = r0 * a.L;
   } else {
-    const unsigned outer = fdiv(t, a.divx);
-    const int x0 = (int)(t - outer * (unsigned)a.xtiles) << a.lw;
-    r.nv = min(a.W, a.nx - x0);
-    const unsigned o1 = fdiv(outer, a.divd1);
-    r.base = (long long)o1 * a.s1 + (long long)(outer - o1 * (unsigned)a.d1) * a.s0 + x0;
+    const unsigned ot = fdiv(t, a.divx);
+    r.x0 = (int)(t - ot * (unsigned)a.xtiles) << 4;
+    r.nvx = min(16, a.nx - r.x0);
+    r.o0 = ot << (a.lw - 4);
+    r.ng = (int)min((long long)(a.W >> 4), a.outer - (long long)r.o0);
   }
   return r;
 }
+// First element of slice o: (o / d1) s1 + (o % d1) s0.
+__device__ __forceinline__ long long slice_base(const Args& a, unsigned o) {
+  const unsigned o1 = fdiv(o, a.divd1);
+  return (long long)o1 * a.s1 + (long long)(o - o1 * (unsigned)a.d1) * a.s0;
+}
 
-// Asynchronous copies of tile t into buf ([i][q], pitch P), 8 bytes each:
+// Asynchronous copies of tile t into buf ([i][c], pitch P), 8 bytes each:
 // every copy of a thread is in flight at once.
 __device__ __forceinline__ void load_tile(const Args& a, unsigned t, float2* buf, int P) {
   const TileRef r = tile_of(a, t);
@@ -114,10 +126,12 @@ __device__ __forceinline__ void load_tile(const Args& a, unsigned t, float2* buf
       cp_async8(sb + 8u * (uint32_t)((e - (int)q * a.L) * P + (int)q), src + e);
     }
   } else {
-    const int pts = a.L << a.lw;
-    for (int e = threadIdx.x; e < pts; e += kThreads) {
-      const int q = e & (a.W - 1), i = e >> a.lw;
-      if (q < r.nv) cp_async8(sb + 8u * (uint32_t)(i * P + q), a.in + r.base + q + i * a.pi);
+    // W <= kThreads: a thread's pencil c is the same in every step
+    const int c = threadIdx.x & (a.W - 1), q = c & 15, g = c >> 4;
+    if (q < r.nvx && g < r.ng) {
+      const float2* src = a.in + slice_base(a, r.o0 + g) + r.x0 + q;
+      for (int i = threadIdx.x >> a.lw; i < a.L; i += kThreads >> a.lw)
+        cp_async8(sb + 8u * (uint32_t)(i * P + c), src + (long long)i * a.pi);
     }
   }
 }
@@ -136,7 +150,6 @@ __global__ void __launch_bounds__(kThreads) axis_pass_kernel(const Args a) {
     tw[i] = a.tw[i];
     pos[i] = a.pos[i];
   }
-  const int pts = a.L << a.lw;
   unsigned t = blockIdx.x;
   if (NBUF == 2 && t < a.ntiles) {
     load_tile(a, t, sm, P);
@@ -180,10 +193,12 @@ __global__ void __launch_bounds__(kThreads) axis_pass_kernel(const Args a) {
         dst[e] = cscale(tile[pos[e - (int)q * a.L] * P + (int)q], sc);
       }
     } else {
+      const int c = threadIdx.x & (a.W - 1), q = c & 15, g = c >> 4;
+      if (q < r.nvx && g < r.ng) {
+        float2* dst = a.out + slice_base(a, r.o0 + g) + r.x0 + q;
 #pragma unroll 4
-      for (int e = threadIdx.x; e < pts; e += kThreads) {
-        const int q = e & (a.W - 1), k = e >> a.lw;
-        if (q < r.nv) a.out[r.base + q + k * a.pi] = cscale(tile[pos[k] * P + q], sc);
+        for (int k = threadIdx.x >> a.lw; k < a.L; k += kThreads >> a.lw)
+          dst[(long long)k * a.pi] = cscale(tile[pos[k] * P + c], sc);
       }
     }
     __syncthreads();  // this buffer is reloaded next
@@ -259,10 +274,14 @@ int prepare_axis_pass(const AxisTable& tab, int dir, const AxisGeom& g, int sms,
   // (x pass: at least 16 rows, about 8192 points per tile, 4096 with two
   // buffers; y and z passes: 16 adjacent pencils, one 128-byte run per
   // element)
+  // x pass: W consecutive rows; y and z passes: 16 adjacent pencils of
+  // W / 16 consecutive slices (at most as many slices as there are, and W
+  // at most the block's threads)
   auto tile_lw = [&](int nb) {
     int lw = 4;
-    if (g.contiguous)
-      while (lw < 9 && (tab.L << (lw + 1)) <= (nb == 2 ? 4096 : 8192)) ++lw;
+    while (lw < (g.contiguous ? 9 : 8) && (tab.L << (lw + 1)) <= (nb == 2 ? 4096 : 8192) &&
+           (g.contiguous || (1LL << (lw + 1 - 4)) <= g.outer))
+      ++lw;
     return lw;
   };
   const int nbuf = ax::smem_bytes(tab.L, 1 << tile_lw(2), 2) <= 110 * 1024 ? 2 : 1;
@@ -284,14 +303,16 @@ int prepare_axis_pass(const AxisTable& tab, int dir, const AxisGeom& g, int sms,
     ntiles = (g.rows + a.W - 1) >> a.lw;
   } else {
     a.nx = g.nx;
-    a.xtiles = (g.nx + a.W - 1) >> a.lw;
+    a.xtiles = (g.nx + 15) >> 4;
+    a.outer = g.outer;
     a.d1 = g.d1;
     a.divx = make_fastdiv((unsigned)a.xtiles);
     a.divd1 = make_fastdiv((unsigned)g.d1);
     a.s1 = g.s1;
     a.s0 = g.s0;
     a.pi = g.pi;
-    ntiles = g.outer * a.xtiles;
+    const long long G = a.W >> 4;
+    ntiles = ((g.outer + G - 1) / G) * a.xtiles;
   }
   if (ntiles <= 0 || ntiles >= (1ll << 31)) return FFT3D_ERR_INVALID_ARG;
   a.ntiles = (unsigned)ntiles;

@@ -120,7 +120,8 @@ struct AxisArgs {
   int contiguous;
   unsigned ntiles;
   long long rows;
-  int nx, xtiles, d1;  // strided: tile -> (outer, x0 = 16 * (tile % xtiles))
+  long long outer;     // strided: slices in all
+  int nx, xtiles, d1;  // strided: tile -> (slice group, x0 = 16 * (tile % xtiles))
   FastDiv divx, divd1;
   long long s1, s0, pi;
   float scale;
