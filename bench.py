@@ -49,7 +49,7 @@ METRIC = "batched 3D FFT transforms/s and % of HBM roofline at 64^3/128^3 (FP32 
 # The sources each default FP32 kernel is built from (its own file and the
 # headers it includes); their hash keys the recorded DRAM traffic.
 _COMMON_SOURCES = ["paper_2006_08435_gb300/csrc/persistent.cuh",
-                   "paper_2006_08435_gb300/csrc/pipelined.cuh",
+                   "paper_2006_08435_gb300/csrc/mbar.cuh",
                    "paper_2006_08435_gb300/csrc/rowfft.cuh",
                    "paper_2006_08435_gb300/csrc/codelets.cuh",
                    "paper_2006_08435_gb300/csrc/sizes.h"]

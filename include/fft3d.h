@@ -264,31 +264,32 @@ int fft3d_selftest_wait_timeout(int64_t timeout_ns);
 
 /*
  * The kernel variant a plan uses (written to *variant).  Single-edge FP32
- * plans: 0 plain persistent kernel, 1 the same with twice the threads per
- * block, 2 the TMA-fed warp-specialised kernel (64^3, 128^3), 3 the
- * cluster-fused single-pass kernel (16^3, 32^3, 64^3), 4 the double-buffered
- * persistent kernel (32^3 .. 96^3, except 128^3), 5 the warp-owned two-phase
- * kernel (64^3, 128^3), 6 the double-buffered TMA-fed kernel with producer
- * and signaller warps (64^3), 7 the thread-per-pencil kernel (each 1D FFT in
- * one thread's registers, items loaded by swizzled tensor TMA; 64^3), 8 the
- * same with two-plane items and a register split (64^3); for 128^3, 6 is the
- * split-y kernel (64 KB items: half-planes and quarter-slabs, 128-point
- * FFTs by thread pairs).  The tensor-TMA variants (64^3: 7, 8; 128^3: 6)
- * need packed, 16-byte aligned buffers of one batch (they encode tensor maps
- * of `in` and `out` at each execute).  Tensor-core precision plans (64^3,
- * 128^3): 0 the plain persistent kernel (mma.sync radix-16 stage), 8 the
- * two-plane tensor-TMA kernel with mma.sync products (64^3), 9 the
- * tensor-TMA items with tcgen05 products, operands and accumulators in
- * tensor memory (64^3 two-plane, 128^3 split-y; all of a multiprocessor's
- * tensor memory, one block per multiprocessor); 8 and 9 have the same buffer
- * requirements as the tensor-TMA FP32 variants.  10: the general path
- * (every plan that is not cubic with a fused edge; selectable for those
- * too): per chunk of grids that fits 40% of L2, three launches, the x pass
- * (in -> out) and the y and z passes in place on out, each a batched 1D
- * transform of the pencils of one axis in shared-memory tiles (mixed
- * radices 2, 3, 4, 5, 6, 8, 9, 10, 12, 15, 16; fft3d_axis_digit_map).
- * Mixed plans: 0 one launch of the mixed-edge kernel, 1 one launch per
- * distinct edge.
+ * plans (each variant the fastest for some edge and batch on the GB300):
+ * 0 plain persistent kernel, 1 the same with twice the threads per block
+ * (16^3 .. 96^3), 3 the cluster-fused single-pass kernel (16^3, 32^3), 4
+ * the double-buffered persistent kernel (32^3, 48^3, 80^3, 96^3), 5 the
+ * warp-owned two-phase kernel (64^3, 128^3), 7 the thread-per-pencil
+ * kernel (each 1D FFT in one thread's registers, items loaded by swizzled
+ * tensor TMA; 64^3), 8 the same with two-plane items and a register split
+ * (64^3); for 128^3, 6 is the split-y kernel (64 KB items: half-planes and
+ * quarter-slabs, 128-point FFTs by thread pairs).  The tensor-TMA variants
+ * (64^3: 7, 8; 128^3: 6) need packed, 16-byte aligned buffers of one batch
+ * (they encode tensor maps of `in` and `out` at each execute).
+ * Tensor-core precision plans (64^3, 128^3): 0 the plain persistent kernel
+ * (mma.sync radix-16 stage), 9 the tensor-TMA items with tcgen05 products,
+ * operands and accumulators in tensor memory (64^3 two-plane, 128^3
+ * split-y; all of a multiprocessor's tensor memory, one block per
+ * multiprocessor), with the buffer requirements of the tensor-TMA FP32
+ * variants; the block-floating-point and FP8 kinds exist on 9 only.  10:
+ * the general path (every plan that is not cubic with a fused edge;
+ * selectable for those too): per chunk of grids that fits 40% of L2, three
+ * launches, the x pass (in -> out) and the y and z passes in place on out,
+ * each a batched 1D transform of the pencils of one axis in shared-memory
+ * tiles (mixed radices 2, 3, 4, 5, 6, 8, 9, 10, 12, 15, 16;
+ * fft3d_axis_digit_map).  Mixed plans: 0 one launch of the mixed-edge
+ * kernel, 1 one launch per distinct edge (the default; an edge whose
+ * default is a tensor-TMA kernel takes variant 0 at 64^3 and 5 at 128^3,
+ * which address grids through the plan's map).
  * At create the variant comes from FFT3D_VARIANT / FFT3D_MIXED_VARIANT if
  * set, else from the tuning cache named by FFT3D_TUNE_CACHE (tuned on the
  * spot when FFT3D_TUNE=1 and the entry is missing), else a built-in default.

@@ -1,17 +1,9 @@
-// Single-size persistent kernels for 64^3 grids (forward and inverse),
-// in two block sizes: the default and twice as many threads per block
-// (more warps to hide latency, fewer registers per thread), plus the
-// warp-specialised TMA-fed kernel (variant 2) and the cluster-fused
-// single-pass kernel (variant 3).
-// Variant 4: the double-buffered (cp.async prefetch) persistent kernel.
-// Variant 5: warp-owned rows/columns inside the two-phase items.
-// Variant 6: double-buffered TMA-fed blocks with producer and signaller warps.
-// Variant 7: thread-per-pencil register FFTs fed by tensor TMA.
-// Variant 8: the same with two-plane items and a register split.
-#include "cluster.cuh"
-#include "dbuf.cuh"
-#include "prefetch.cuh"
-#include "pipelined.cuh"
+// Single-size kernels for 64^3 grids (forward and inverse): the plain
+// persistent kernel in two block sizes (variant 0, and 1 with twice the
+// threads per block: more warps to hide latency, fewer registers per
+// thread), the warp-owned two-phase kernel (5), the thread-per-pencil
+// kernel fed by tensor TMA (7) and the same with two-plane items and a
+// register split (8).  Each is the fastest for some batch on the GB300.
 #include "rowfft.cuh"
 #include "rowfft2.cuh"
 #include "warpown.cuh"
@@ -22,11 +14,7 @@ KernelInfo fused_kernel_info_n64(int dir, int variant) {
   constexpr int T = fused_threads(64);
   if (variant == 8) return dir < 0 ? rowk2::info<64, -1>() : rowk2::info<64, 1>();
   if (variant == 7) return dir < 0 ? rowk::info<64, -1>() : rowk::info<64, 1>();
-  if (variant == 6) return dir < 0 ? dbuf::info<64, -1>() : dbuf::info<64, 1>();
   if (variant == 5) return dir < 0 ? wown::info<64, -1>() : wown::info<64, 1>();
-  if (variant == 4) return dir < 0 ? pref::info<T, -1, 64>() : pref::info<T, 1, 64>();
-  if (variant == 3) return dir < 0 ? clus::info<64, -1>() : clus::info<64, 1>();
-  if (variant == 2) return dir < 0 ? piped::info<64, -1>() : piped::info<64, 1>();
   if (variant == 1 && 2 * T <= 1024)
     return dir < 0 ? make_fused_info<2 * T, -1, 64>() : make_fused_info<2 * T, 1, 64>();
   return dir < 0 ? make_fused_info<T, -1, 64>() : make_fused_info<T, 1, 64>();

@@ -1,17 +1,15 @@
 // Tensor-core (split FP16, split BF16, FP16; the block-floating-point and
 // FP8 kinds in inst_tc_n64_f4.cu) kernels for 64^3 grids: the
 // radix-16 step of each axis runs on the tensor cores.  Variant 0: the
-// plain persistent kernel; 8: the two-plane tensor-TMA kernel with mma.sync
-// (tcrow.cuh); 9: the same items with tcgen05 products (tcgen.cuh).
+// plain persistent kernel (mma.sync, the fastest below 16 grids); 9: the
+// two-plane tensor-TMA items with tcgen05 products (tcgen.cuh).
 #include "persistent.cuh"
 #include "tcgen.cuh"
-#include "tcrow.cuh"
 
 namespace fft3d {
 
 template <int DIR, int PREC>
 static KernelInfo tc_info_n64(int variant) {
-  if (variant == 8) return tcr::info<64, DIR, PREC>();
   if (variant == 9) return tg::info<64, DIR, PREC>();
   return make_fused_info_prec<fused_threads(64), DIR, PREC, 64>();
 }

@@ -165,7 +165,7 @@ extern "C" int fft3d_execute_noalloc(int n, int batch, int direction, int norm, 
     st.ready = true;
   }
 
-  const KernelInfo k = fused_kernel_info(n, direction, n == 128 ? 2 : 0);
+  const KernelInfo k = fused_kernel_info(n, direction, 0);
   const int di = direction < 0 ? 0 : 1, si = fused_slot(n);
   if (st.per_sm[di][si] == 0) {
     int per_sm = 0;

@@ -173,14 +173,15 @@ static void umma_b_table(int prec, uint16_t* out /* 8192 */) {
 
 static bool fused_size(int n) { return fused_slot(n) >= 0; }
 
-// Kernel variants of a single-size FP32 plan: 0 plain persistent kernel,
-// 1 the same with twice the threads, 2 the TMA-fed warp-specialised kernel
-// (64^3 and 128^3), 3 the cluster-fused single-pass kernel (16^3, 32^3,
-// 64^3), 4 the double-buffered persistent kernel (32^3 to 96^3), 5 the
-// warp-owned two-phase kernel (64^3, 128^3), 6 to 8 the tensor-TMA
-// thread-per-pencil kernels.  Tensor-core precisions: 0 the plain persistent
-// kernel, 8 (64^3) the two-plane tensor-TMA kernel with mma.sync, 9 the
-// tensor-TMA items with tcgen05 products (64^3 two-plane, 128^3 split-y).
+// Kernel variants of a single-size FP32 plan (each the fastest for some
+// edge and batch on the GB300): 0 plain persistent kernel, 1 the same with
+// twice the threads (16^3 to 96^3), 3 the cluster-fused single-pass kernel
+// (16^3, 32^3), 4 the double-buffered persistent kernel (32^3, 48^3, 80^3,
+// 96^3), 5 the warp-owned two-phase kernel (64^3, 128^3), 6 to 8 the
+// tensor-TMA thread-per-pencil kernels (128^3 split-y; 64^3 one-plane and
+// two-plane items).  Tensor-core precisions: 0 the plain persistent kernel,
+// 9 the tensor-TMA items with tcgen05 products (64^3 two-plane, 128^3
+// split-y).
 // Variant 10 (kGeneralVariant): the general path, one pencil pass per axis
 // (axis.cu), the only one for non-cubic grids and edges without a fused
 // kernel, selectable for the others.  Mixed plans: 0 one
@@ -190,37 +191,41 @@ std::vector<int> variant_candidates(bool mixed, int n, int precision) {
   if (mixed) return {0, 1};
   // the block-floating-point and FP8 kinds exist on the tcgen05 kernels only
   if (precision >= FFT3D_BFP16) return {9};
-  if (precision != FFT3D_FP32) return n == 64 ? std::vector<int>{0, 8, 9} : std::vector<int>{0, 9};
+  if (precision != FFT3D_FP32) return {0, 9};
   if (!fused_size(n)) return {kGeneralVariant};
   switch (n) {
     case 16: return {0, 1, 3, kGeneralVariant};
     case 32: return {0, 1, 3, 4, kGeneralVariant};
-    case 64: return {0, 1, 2, 3, 4, 5, 6, 7, 8, kGeneralVariant};
-    case 128: return {0, 1, 2, 5, 6, kGeneralVariant};
+    case 64: return {0, 1, 5, 7, 8, kGeneralVariant};
+    case 128: return {0, 5, 6, kGeneralVariant};
     default: return {0, 1, 4, kGeneralVariant};  // 48, 80, 96
   }
 }
 
-// Measured on GB300 (see profiles/): the TMA-fed kernel at 128^3, the
-// cluster-fused kernel for 16^3 and 32^3 batches of 64 grids or more, the
-// plain persistent kernel otherwise.
+// The fastest variant measured on the GB300 for each edge and batch
+// (back-to-back executes; one grid also with L2 flushed):
+//   16^3, 32^3: plain persistent below 64 grids, cluster-fused from 64;
+//   48^3, 96^3: plain persistent;  80^3: plain persistent for one grid,
+//     the double-buffered persistent kernel from 4 (0.67x the time at 256);
+//   64^3: warp-owned for one grid, the persistent kernel with twice the
+//     threads below 16, thread-per-pencil below 64, two-plane from 64;
+//   128^3: warp-owned for one grid, split-y from 2;
+//   tensor-core precisions: the plain persistent kernel (mma.sync) for few
+//     grids, the tcgen05 kernels from 16 (64^3) and 2 (128^3) grids.
 int builtin_default_variant(bool mixed, int n, int batch, int precision) {
   // mixed edges: one launch per distinct edge (the mixed workload of 64
   // grids: 0.41 ms against 0.48 ms for the one mixed-edge launch)
   if (mixed) return 1;
-  // tensor-core precisions: the tcgen05 kernels (measured 0.50 of the HBM
-  // roofline at 64^3 x 256 against 0.40 for mma.sync and 0.24 for the plain
-  // persistent kernel; 0.37 at 128^3 x 32 against 0.20)
   if (precision >= FFT3D_BFP16) return 9;
-  if (precision != FFT3D_FP32) return (n == 64 && batch >= 16) || (n == 128 && batch >= 4) ? 9 : 0;
-  // split-y from 2 grids (L2 flushed: 37.5 us for two, 43.7 us for three,
-  // the fastest); one grid: the plain persistent kernel (26.7 us against
-  // 32.4 us for the TMA-fed kernel, 34.4 us for split-y)
-  if (n == 128) return batch >= 2 ? 6 : 0;
-  if ((n == 16 || n == 32) && batch >= 64) return 3;
-  if (n == 64 && batch >= 128) return 8;  // two-plane items, measured faster from 128 grids
-  if (n == 64 && batch >= 16) return 7;   // thread-per-pencil, measured faster from 16 grids
-  return 0;
+  if (precision != FFT3D_FP32) return (n == 64 && batch >= 16) || (n == 128 && batch >= 2) ? 9 : 0;
+  switch (n) {
+    case 16:
+    case 32: return batch >= 64 ? 3 : 0;
+    case 64: return batch == 1 ? 5 : batch < 16 ? 1 : batch < 64 ? 7 : 8;
+    case 80: return batch >= 4 ? 4 : 0;
+    case 128: return batch == 1 ? 5 : 6;
+    default: return 0;  // 48, 96
+  }
 }
 
 }  // namespace fft3d
@@ -711,9 +716,9 @@ int create_mixed(int count, const int* dims, int direction, int norm, int varian
       // the edge's default kernel, unless it is one of the tensor-map kernels
       // (64^3: 7, 8; 128^3: 6), which need the unit's grids as one packed
       // batch; the unit addresses its grids through the plan's map, so those
-      // edges take the fastest kernel that does (64^3: 6, 128^3: 2)
+      // edges take the fastest kernel that does (64^3: 0, 128^3: 5)
       int v = builtin_default_variant(false, n, (int)u.grids.size(), FFT3D_FP32);
-      if ((n == 64 && (v == 7 || v == 8)) || (n == 128 && v == 6)) v = n == 64 ? 6 : 2;
+      if ((n == 64 && (v == 7 || v == 8)) || (n == 128 && v == 6)) v = n == 64 ? 0 : 5;
       u.kernel = fused_kernel_info(n, direction, v);
       p->units.push_back(u);
     }

@@ -36,17 +36,17 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
-#include "pipelined.cuh"
+#include "mbar.cuh"
 
 namespace fft3d {
 namespace rowk {
 
-using piped::mbar_arrive;
-using piped::mbar_arrive_tx;
-using piped::mbar_init;
-using piped::mbar_wait_bounded;
-using piped::saddr;
-using piped::warp_wait;
+using mb::mbar_arrive;
+using mb::mbar_arrive_tx;
+using mb::mbar_init;
+using mb::mbar_wait_bounded;
+using mb::saddr;
+using mb::warp_wait;
 
 template <int N>
 struct Cfg {

@@ -25,12 +25,12 @@
 namespace fft3d {
 namespace rowk2 {
 
-using piped::mbar_arrive;
-using piped::mbar_arrive_tx;
-using piped::mbar_init;
-using piped::mbar_wait_bounded;
-using piped::saddr;
-using piped::warp_wait;
+using mb::mbar_arrive;
+using mb::mbar_arrive_tx;
+using mb::mbar_init;
+using mb::mbar_wait_bounded;
+using mb::saddr;
+using mb::warp_wait;
 using rowk::bcast;
 using rowk::Desc;
 using rowk::spin_geq;

@@ -41,22 +41,22 @@
 
 #include <cuda_fp8.h>
 
-#include "tcrow.cuh"
+#include "tcops.cuh"
 
 namespace fft3d {
 namespace tg {
 
-using piped::mbar_arrive;
-using piped::mbar_init;
-using piped::saddr;
-using piped::warp_wait;
+using mb::mbar_arrive;
+using mb::mbar_init;
+using mb::saddr;
+using mb::warp_wait;
 using rowk::Desc;
 using rowk::policy_evict_last;
 using rowk2::boff;
 using rowk2::Cfg;
-using tcr::lds2;
-using tcr::max3;
-using tcr::sts4;
+using tco::lds2;
+using tco::max3;
+using tco::sts4;
 
 constexpr int kBBytes = 2 * 4 * 2048;  // B operands: term (hi, lo) x k1 x 32 x 32 halves
 constexpr int kTmemCols = 512;         // 2 groups x (A: 8 x 16, D: 4 x 32 columns)
@@ -151,7 +151,7 @@ template <int PREC>
 __device__ __forceinline__ void split_nhi(float2 x, float2 s, uint32_t& nhi, uint32_t& lo) {
   static_assert(!Kind<PREC>::fp8, "FP8 operands: split8");
   if constexpr (PREC == 3) {
-    tcr::split<3>(x, s, nhi, lo);
+    tco::split<3>(x, s, nhi, lo);
   } else {
     constexpr float C = PREC == 2 ? 1610612736.0f : 201326592.0f;
     const float2 c = make_float2(C, C);
@@ -298,7 +298,7 @@ __device__ __forceinline__ bool pass(float2 (&v)[64], const Pass& P, unsigned& p
 #pragma unroll
   for (int n2 = 0; n2 < 16; ++n2) {
     float2 q[4] = {v[n2], v[16 + n2], v[32 + n2], v[48 + n2]};
-    tcr::dft4<DIR>(q);
+    tco::dft4<DIR>(q);
     v[n2] = q[0];
     v[16 + n2] = q[1];
     v[32 + n2] = q[2];

@@ -14,10 +14,10 @@
 namespace fft3d {
 namespace tsy {
 
-using piped::mbar_arrive;
-using piped::mbar_init;
-using piped::saddr;
-using piped::warp_wait;
+using mb::mbar_arrive;
+using mb::mbar_init;
+using mb::saddr;
+using mb::warp_wait;
 using rowk::Desc;
 using rowk::policy_evict_last;
 using sy::Cfg;

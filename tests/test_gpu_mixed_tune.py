@@ -124,7 +124,7 @@ def test_autotune_records_and_plans_use_the_choice(cuda, tmp_path, monkeypatch):
     from paper_2006_08435_gb300 import Plan, MixedPlan, autotune, autotune_mixed
     cache = str(tmp_path / "tune.json")
     best = autotune(64, 16, cache_path=cache)
-    assert best in list(range(9)) + [10]  # the 64^3 candidates
+    assert best in (0, 1, 5, 7, 8, 10)  # the 64^3 candidates
     sizes = synth.mixed_sizes(16, seed=3)
     best_m = autotune_mixed(sizes, cache_path=cache)
     assert best_m in (0, 1)

@@ -76,11 +76,11 @@ def test_precision_unsupported_size_is_refused(cuda):
         Plan(48, 48, 48, 1, precision="split_fp16")
 
 
-@pytest.mark.parametrize("variant", [0, 8])
+@pytest.mark.parametrize("variant", [0, 9])
 @pytest.mark.parametrize("inverse", [False, True])
 def test_precision_kinds_per_variant_64(cuda, monkeypatch, variant, inverse):
-    """Each 64^3 tensor-core kernel (0 plain persistent, 8 two-plane
-    tensor-TMA) for every precision kind, three grids (a ragged tail of
+    """Each 64^3 tensor-core kernel (0 plain persistent, 9 two-plane
+    tcgen05) for every precision kind, three grids (a ragged tail of
     plane-pair items), forward and normalised inverse."""
     from paper_2006_08435_gb300 import Plan
     monkeypatch.setenv("FFT3D_VARIANT", str(variant))
@@ -105,13 +105,13 @@ def test_split_fp16_two_plane_in_place_many_grids(cuda, monkeypatch):
     """40 grids in place (every block goes several times round its tiles),
     each a multiple of the first, so one oracle transform checks three."""
     from paper_2006_08435_gb300 import Plan
-    monkeypatch.setenv("FFT3D_VARIANT", "8")
+    monkeypatch.setenv("FFT3D_VARIANT", "9")
     n, batch = 64, 40
     base = torch.from_numpy(synth.gaussian_sum_grids(n, 1, seed=5)).cuda()
     x = (base.repeat(batch, 1, 1, 1) *
          torch.arange(1, batch + 1, device="cuda", dtype=torch.float32).view(-1, 1, 1, 1)).contiguous()
     p = Plan(n, n, n, batch, precision="split_fp16")
-    assert p.variant == 8
+    assert p.variant == 9
     p.execute(x, x)
     assert p.device_status() == 0
     ref0 = oracle.dft3d(base[0].cpu().numpy().astype(np.complex128), -1)
@@ -120,11 +120,11 @@ def test_split_fp16_two_plane_in_place_many_grids(cuda, monkeypatch):
 
 
 def test_split_fp16_two_plane_closed_forms_and_range(cuda, monkeypatch):
-    """The two-plane tensor-core kernel on a delta (all-ones result), a
+    """The two-plane tcgen05 kernel on a delta (all-ones result), a
     constant (one bin), zero planes, and a round trip through values far
     above the FP16 range."""
     from paper_2006_08435_gb300 import fft3d
-    monkeypatch.setenv("FFT3D_VARIANT", "8")
+    monkeypatch.setenv("FFT3D_VARIANT", "9")
     n = 64
     d = torch.zeros((1, n, n, n), dtype=torch.complex64, device="cuda")
     d[0, 0, 0, 0] = 1.0

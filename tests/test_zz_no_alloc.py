@@ -36,8 +36,8 @@ def call_noalloc(lib, x, out, n, batch, direction, norm):
                                      torch.cuda.current_stream().cuda_stream)
 
 
-# (64, 3) and (48, 2): plain persistent kernel; (128, 2): the pipelined
-# kernel; (16, 300): 600 schedule blocks (several words of the phase bits
+# the plain persistent kernel at (64, 3), (128, 2), (48, 2); (16, 300): 600
+# schedule blocks (several words of the phase bits
 # the set-up kernel expands) with slab blocks interleaved among the planes
 @pytest.mark.parametrize("n,batch", [(64, 3), (128, 2), (48, 2), (16, 300)])
 def test_matches_planned_path_and_oracle_on_two_calls(cuda, n, batch):
