@@ -8,15 +8,17 @@ than L2, so no flush is needed between steps).  Roofline bytes per
 transform = 16 * N^3 (one read and one write of the grid).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload 128x32|64x256|128x16|64x64|64x128] [--no-cpu-baseline]
+                  [--workload 128x32|64x256|128x16|64x64|64x128|256x2] [--no-cpu-baseline]
                   [--no-e2e] [--no-split] [--no-real] [--no-64] [--no-mixed] [--no-batch1]
+                  [--no-general]
 
 The small workloads exist for profiler captures of the same kernels.  Beside
 the headline the line carries sub-objects: split_fp16 (the same batch in
 split FP16), tensor_core_kinds (split BF16, FP16, block floating point
 FP16, split FP8, FP8 on the same batch), real_r2c_fp32 (real grids), w64x256 (64^3 x 256 in FP32 and
 split FP16), mixed_c2 (64 mixed-edge grids, forward + inverse in one CUDA
-graph) and batch1 (one grid per launch, L2 flushed, the paper's setting).
+graph), general_path (256^3 and a non-cubic batch on the per-axis passes)
+and batch1 (one grid per launch, L2 flushed, the paper's setting).
 
 Under torchrun each rank transforms its own batch (weak scaling, no
 collective on the data path); rank 0 prints one JSON line.
@@ -44,6 +46,8 @@ WORKLOADS = {
     "128x16": (128, 16),
     "64x64": (64, 64),
     "64x128": (64, 128),
+    # the general path (edges without a fused kernel), for profiler captures
+    "256x2": (256, 2),
 }
 METRIC = "batched 3D FFT transforms/s and % of HBM roofline at 64^3/128^3 (FP32 vs split-FP16)"
 # The sources each default FP32 kernel is built from (its own file and the
@@ -55,7 +59,8 @@ _COMMON_SOURCES = ["paper_2006_08435_gb300/csrc/persistent.cuh",
                    "paper_2006_08435_gb300/csrc/sizes.h"]
 KERNEL_SOURCES = {128: ["paper_2006_08435_gb300/csrc/splity.cuh"] + _COMMON_SOURCES,
                   64: ["paper_2006_08435_gb300/csrc/rowfft2.cuh"] + _COMMON_SOURCES}
-KERNEL_NAMES = {128: "splity_fft3d_kernel<128,-1>", 64: "rowfft2_fft3d_kernel<64,-1>"}
+KERNEL_NAMES = {128: "splity_fft3d_kernel<128,-1>", 64: "rowfft2_fft3d_kernel<64,-1>",
+                256: "axis_pass_kernel<-1,2> (general path, three passes)"}
 
 
 def dist_env():
@@ -467,6 +472,32 @@ def run_ours(args, ws, rank, local):
                  "roofline_frac": 2 * 16.0 * pts / (msm / 1e3) / 1e9 / peak}
         del xm, ym, bm, graph, fwd, inv
 
+    # the general path (any edge up to 512, non-cubic grids): 256^3 x 4 and
+    # a non-cubic batch, one pencil pass per axis (three launches per chunk
+    # of grids); roofline fractions of the 16 n^3 bytes and of the passes'
+    # own traffic (three reads and writes of the grid, 48 n^3 bytes)
+    general = None
+    if not args.no_general:
+        general = {}
+        for shape, bg in (((256, 256, 256), 4), ((96, 128, 64), 64)):
+            nz_, ny_, nx_ = shape
+            xg = torch.randn((bg, nz_, ny_, nx_), dtype=torch.complex64, device=dev)
+            yg = torch.empty_like(xg)
+            pg = Plan(nx_, ny_, nz_, bg)
+            for _ in range(3):
+                pg.execute(xg, yg, stream)
+            barrier()
+            kg = max(1, args.steps // 4)
+            msg = max_over_ranks(timed_ms(lambda: pg.execute(xg, yg, stream), kg, stream), ws, dev)
+            assert pg.device_status() == 0
+            pts_g = nx_ * ny_ * nz_ * bg
+            general[f"{nz_}x{ny_}x{nx_}x{bg}"] = {
+                "value": whole_job_rate(ws, bg, 1, msg), "unit": "transforms/s", "steps": kg,
+                "ms_per_step": msg, "variant": pg.variant,
+                "roofline_frac": 16.0 * pts_g / (msg / 1e3) / 1e9 / peak,
+                "frac_of_pass_traffic": 48.0 * pts_g / (msg / 1e3) / 1e9 / peak}
+            del xg, yg, pg
+
     # the paper's setting: one grid per transform (Table 1), latency of
     # one execute with L2 flushed before each timed launch
     batch1 = None
@@ -541,6 +572,8 @@ def run_ours(args, ws, rank, local):
         line["w64x256"] = w64
     if mixed is not None:
         line["mixed_c2"] = mixed
+    if general is not None:
+        line["general_path"] = general
     if batch1 is not None:
         line["batch1"] = batch1
     if ws == 1 and not args.no_cpu_baseline:
@@ -565,6 +598,7 @@ def main():
     ap.add_argument("--no-64", action="store_true", help="skip the 64^3 x 256 sub-leg")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-edge graph sub-leg")
     ap.add_argument("--no-batch1", action="store_true", help="skip the batch-1 latency sub-leg")
+    ap.add_argument("--no-general", action="store_true", help="skip the general-path sub-leg")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":

@@ -47,6 +47,16 @@ __device__ __forceinline__ unsigned fdiv(unsigned n, FastDiv d) {
   return (unsigned)(((unsigned long long)__umulhi(n, d.mul) + n) >> d.shift);
 }
 
+// Tile slot of element i of pencil c.  In the x pass of a power-of-two
+// span S = L / R_0, the digit-reversed positions that consecutive outputs
+// read are S apart, so without a rotation every lane of a warp would hit
+// the same bank (16-way conflicts at L = 256); the pencil index is XORed
+// with bits of i / S (a permutation of each aligned group of 16 pencils, so
+// the butterflies, whose lanes share i, stay conflict-free).
+__device__ __forceinline__ int tix(const Args& a, int i, int c, int P) {
+  return i * P + (c ^ ((i >> a.swsh) & a.swmask));
+}
+
 template <int R, int DIR>
 __device__ __forceinline__ void stage(float2* tile, const float2* tw, const Args& a, int t, int P) {
   const int N = a.span[t], M = a.sub[t], stw = a.twst[t];
@@ -59,7 +69,7 @@ __device__ __forceinline__ void stage(float2* tile, const float2* tw, const Args
     const int i0 = (int)blk * N + j;
     float2 v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = tile[(i0 + r * M) * P + q];
+    for (int r = 0; r < R; ++r) v[r] = tile[tix(a, i0 + r * M, q, P)];
     DFT<R, DIR>::run(v);
     const int st = j * stw;  // W_N^(j k) = W_L^(j k L / N); j k L / N < L
     if (st) {
@@ -67,7 +77,7 @@ __device__ __forceinline__ void stage(float2* tile, const float2* tw, const Args
       for (int k = 1; k < R; ++k) v[k] = cmul_tw<DIR>(v[k], tw[k * st]);
     }
 #pragma unroll
-    for (int k = 0; k < R; ++k) tile[(i0 + k * M) * P + q] = v[k];
+    for (int k = 0; k < R; ++k) tile[tix(a, i0 + k * M, q, P)] = v[k];
   }
 }
 
@@ -123,7 +133,7 @@ __device__ __forceinline__ void load_tile(const Args& a, unsigned t, float2* buf
     const float2* src = a.in + r.base;
     for (int e = threadIdx.x; e < r.nv * a.L; e += kThreads) {
       const unsigned q = fdiv((unsigned)e, a.divL);
-      cp_async8(sb + 8u * (uint32_t)((e - (int)q * a.L) * P + (int)q), src + e);
+      cp_async8(sb + 8u * (uint32_t)tix(a, e - (int)q * a.L, (int)q, P), src + e);
     }
   } else {
     // W <= kThreads: a thread's pencil c is the same in every step
@@ -131,7 +141,7 @@ __device__ __forceinline__ void load_tile(const Args& a, unsigned t, float2* buf
     if (q < r.nvx && g < r.ng) {
       const float2* src = a.in + slice_base(a, r.o0 + g) + r.x0 + q;
       for (int i = threadIdx.x >> a.lw; i < a.L; i += kThreads >> a.lw)
-        cp_async8(sb + 8u * (uint32_t)(i * P + c), src + (long long)i * a.pi);
+        cp_async8(sb + 8u * (uint32_t)tix(a, i, c, P), src + (long long)i * a.pi);
     }
   }
 }
@@ -190,7 +200,7 @@ __global__ void __launch_bounds__(kThreads) axis_pass_kernel(const Args a) {
 #pragma unroll 4
       for (int e = threadIdx.x; e < r.nv * a.L; e += kThreads) {
         const unsigned q = fdiv((unsigned)e, a.divL);
-        dst[e] = cscale(tile[pos[e - (int)q * a.L] * P + (int)q], sc);
+        dst[e] = cscale(tile[tix(a, pos[e - (int)q * a.L], (int)q, P)], sc);
       }
     } else {
       const int c = threadIdx.x & (a.W - 1), q = c & 15, g = c >> 4;
@@ -198,7 +208,7 @@ __global__ void __launch_bounds__(kThreads) axis_pass_kernel(const Args a) {
         float2* dst = a.out + slice_base(a, r.o0 + g) + r.x0 + q;
 #pragma unroll 4
         for (int k = threadIdx.x >> a.lw; k < a.L; k += kThreads >> a.lw)
-          dst[(long long)k * a.pi] = cscale(tile[pos[k] * P + c], sc);
+          dst[(long long)k * a.pi] = cscale(tile[tix(a, pos[k], c, P)], sc);
       }
     }
     __syncthreads();  // this buffer is reloaded next
@@ -297,6 +307,17 @@ int prepare_axis_pass(const AxisTable& tab, int dir, const AxisGeom& g, int sms,
     span = a.sub[t];
   }
   a.divL = make_fastdiv((unsigned)tab.L);
+  // x pass: rotate pencils by bits of i / S for a power-of-two S = L / R_0
+  // of at least 8 (the rotation turns the copies' conflict-free writes
+  // into 2-way ones; it pays where the reads were 8- or 16-way: measured
+  // 256^3 0.160 -> 0.187, slower at S = 4)
+  a.swsh = 0;
+  a.swmask = 0;
+  const int S0 = tab.L / tab.radix[0];
+  if (g.contiguous && S0 >= 8 && (S0 & (S0 - 1)) == 0) {
+    while ((1 << a.swsh) < S0) ++a.swsh;
+    a.swmask = 15;
+  }
   long long ntiles;
   if (g.contiguous) {
     a.rows = g.rows;

@@ -117,6 +117,7 @@ struct AxisArgs {
   int radix[kAxisMaxStages], span[kAxisMaxStages], sub[kAxisMaxStages], twst[kAxisMaxStages];
   FastDiv divsub[kAxisMaxStages];  // division by sub[t], the span M of a stage's sub-blocks
   FastDiv divL;
+  int swsh, swmask;  // tile slot of (i, c): i * (W + 1) + (c ^ ((i >> swsh) & swmask))
   int contiguous;
   unsigned ntiles;
   long long rows;
