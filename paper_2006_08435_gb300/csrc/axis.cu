@@ -150,7 +150,7 @@ __device__ __forceinline__ void load_tile(const Args& a, unsigned t, float2* buf
 // transformed (two tile buffers); NBUF = 1: one buffer, the copies of a
 // tile all in flight at once, other blocks on the multiprocessor overlap.
 template <int DIR, int NBUF>
-__global__ void __launch_bounds__(kThreads) axis_pass_kernel(const Args a) {
+__global__ void __launch_bounds__(kThreads, NBUF == 2 ? 3 : 2) axis_pass_kernel(const Args a) {
   extern __shared__ __align__(16) float2 sm[];
   const int P = a.W + 1;
   const size_t bstride = (size_t)a.L * P;  // buffer b at sm + b * bstride
@@ -212,6 +212,109 @@ __global__ void __launch_bounds__(kThreads) axis_pass_kernel(const Args a) {
       }
     }
     __syncthreads();  // this buffer is reloaded next
+  }
+}
+
+// ------------------------------------------------------------ plane pass
+constexpr int kPlaneThreads = 256;
+
+// One stage over `np` pencils of the plane (pencil c fastest across the
+// threads), element i of pencil c at addr(c, i).
+template <int R, int DIR, class Addr>
+__device__ __forceinline__ void plane_stage(float2* pl, const float2* tw, const AxisStages& st,
+                                            int t, int np, FastDiv divnp, Addr addr) {
+  const int N = st.span[t], M = st.sub[t], stw = st.twst[t];
+  const int nb = (st.L / R) * np;
+  for (int b = threadIdx.x; b < nb; b += kPlaneThreads) {
+    const unsigned jb = fdiv((unsigned)b, divnp);
+    const int c = b - (int)jb * np;
+    const unsigned blk = fdiv(jb, st.divsub[t]);
+    const int j = (int)(jb - blk * (unsigned)M);
+    const int i0 = (int)blk * N + j;
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = pl[addr(c, i0 + r * M)];
+    DFT<R, DIR>::run(v);
+    const int sk = j * stw;
+    if (sk) {
+#pragma unroll
+      for (int k = 1; k < R; ++k) v[k] = cmul_tw<DIR>(v[k], tw[k * sk]);
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k) pl[addr(c, i0 + k * M)] = v[k];
+  }
+}
+
+template <int DIR, class Addr>
+__device__ __forceinline__ void plane_axis(float2* pl, const float2* tw, const AxisStages& st,
+                                           int np, FastDiv divnp, Addr addr) {
+  for (int s = 0; s < st.nst; ++s) {
+    switch (st.radix[s]) {
+      case 16: plane_stage<16, DIR>(pl, tw, st, s, np, divnp, addr); break;
+      case 15: plane_stage<15, DIR>(pl, tw, st, s, np, divnp, addr); break;
+      case 12: plane_stage<12, DIR>(pl, tw, st, s, np, divnp, addr); break;
+      case 10: plane_stage<10, DIR>(pl, tw, st, s, np, divnp, addr); break;
+      case 9: plane_stage<9, DIR>(pl, tw, st, s, np, divnp, addr); break;
+      case 8: plane_stage<8, DIR>(pl, tw, st, s, np, divnp, addr); break;
+      case 6: plane_stage<6, DIR>(pl, tw, st, s, np, divnp, addr); break;
+      case 5: plane_stage<5, DIR>(pl, tw, st, s, np, divnp, addr); break;
+      case 4: plane_stage<4, DIR>(pl, tw, st, s, np, divnp, addr); break;
+      case 3: plane_stage<3, DIR>(pl, tw, st, s, np, divnp, addr); break;
+      default: plane_stage<2, DIR>(pl, tw, st, s, np, divnp, addr); break;
+    }
+    __syncthreads();
+  }
+}
+
+// Planes of nx x ny points (rows of nx contiguous in memory), one per block
+// at a time: the plane is copied in (cp.async, rows contiguous), the x
+// stages run over its ny rows, the y stages over its nx columns, and the
+// stores read the digit-reversed result of both axes in natural order.
+// Shared layout: element (x, y) at y * px + rot(x), px odd (the x stages'
+// lanes are rows: stride px; the y stages' lanes are columns: consecutive),
+// rot(x) = x ^ ((x >> rsh) & rmask) a permutation of each aligned group of
+// 16 that keeps the stores' digit-reversed reads (consecutive outputs S =
+// nx / R_0 apart) off a single bank.
+template <int DIR>
+__global__ void __launch_bounds__(kPlaneThreads, 2) plane_pass_kernel(const PlaneArgs a) {
+  extern __shared__ __align__(16) float2 sm[];
+  const int nx = a.nx, ny = a.ny, px = a.px;
+  float2* pl = sm;
+  float2* twx = pl + (size_t)ny * px;
+  float2* twy = twx + nx;
+  unsigned short* posx = reinterpret_cast<unsigned short*>(twy + ny);
+  unsigned short* posy = posx + nx;
+  for (int i = threadIdx.x; i < nx; i += kPlaneThreads) {
+    twx[i] = a.twx[i];
+    posx[i] = a.posx[i];
+  }
+  for (int i = threadIdx.x; i < ny; i += kPlaneThreads) {
+    twy[i] = a.twy[i];
+    posy[i] = a.posy[i];
+  }
+  auto rot = [&](int x) { return x ^ ((x >> a.rsh) & a.rmask); };
+  const uint32_t sb = (uint32_t)__cvta_generic_to_shared(pl);
+  const int pts = nx * ny;
+  for (unsigned p = blockIdx.x; p < a.nplanes; p += gridDim.x) {
+    const float2* src = a.in + (size_t)p * pts;
+    for (int e = threadIdx.x; e < pts; e += kPlaneThreads) {
+      const int y = (int)fdiv((unsigned)e, a.divnx), x = e - y * nx;
+      cp_async8(sb + 8u * (uint32_t)(y * px + rot(x)), src + e);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    // x: pencils are the rows (c = y), elements x
+    plane_axis<DIR>(pl, twx, a.sx, ny, a.divny, [&](int c, int i) { return c * px + rot(i); });
+    // y: pencils are the columns (c = x), elements y
+    plane_axis<DIR>(pl, twy, a.sy, nx, a.divnx, [&](int c, int i) { return i * px + rot(c); });
+    float2* dst = a.out + (size_t)p * pts;
+#pragma unroll 4
+    for (int e = threadIdx.x; e < pts; e += kPlaneThreads) {
+      const int ky = (int)fdiv((unsigned)e, a.divnx), kx = e - ky * nx;
+      dst[e] = pl[posy[ky] * px + rot(posx[kx])];
+    }
+    __syncthreads();  // the plane is reloaded next
   }
 }
 
@@ -378,6 +481,87 @@ cudaError_t launch_axis_pass(const AxisLaunch& l, const float2* in, float2* out,
     else
       ax::axis_pass_kernel<1, 1><<<l.grid, ax::kThreads, l.smem, stream>>>(a);
   }
+  return cudaGetLastError();
+}
+
+}  // namespace fft3d
+
+namespace fft3d {
+
+static void fill_stages(const AxisTable& tab, AxisStages& st) {
+  st.L = tab.L;
+  st.nst = tab.nst;
+  int span = tab.L;
+  for (int t = 0; t < tab.nst; ++t) {
+    st.radix[t] = tab.radix[t];
+    st.span[t] = span;
+    st.sub[t] = span / tab.radix[t];
+    st.twst[t] = tab.L / span;
+    st.divsub[t] = make_fastdiv((unsigned)st.sub[t]);
+    span = st.sub[t];
+  }
+}
+
+// One block per multiprocessor at most when the plane uses more than half
+// of the shared memory; planes above 200 KB take the separate passes.
+size_t plane_pass_smem(int nx, int ny) {
+  const int px = nx | 1;
+  const size_t b = ((size_t)ny * px + nx + ny) * sizeof(float2) + (size_t)(nx + ny) * sizeof(unsigned short);
+  return b <= 200 * 1024 ? b : 0;
+}
+
+int prepare_plane_pass(const AxisTable& tx, const AxisTable& ty, int dir, long long planes, int sms,
+                       PlaneLaunch* out) {
+  const size_t smem = plane_pass_smem(tx.L, ty.L);
+  if (!smem || planes <= 0 || planes >= (1ll << 31)) return FFT3D_ERR_INVALID_ARG;
+  PlaneArgs a{};
+  a.twx = tx.d_tw;
+  a.posx = tx.d_pos;
+  a.twy = ty.d_tw;
+  a.posy = ty.d_pos;
+  fill_stages(tx, a.sx);
+  fill_stages(ty, a.sy);
+  a.nx = tx.L;
+  a.ny = ty.L;
+  a.px = tx.L | 1;
+  // rotation: S = nx / R_0 a power of two, nx a multiple of 16
+  const int S0 = tx.L / tx.radix[0];
+  a.rsh = 0;
+  a.rmask = 0;
+  if (tx.L % 16 == 0 && S0 >= 2 && (S0 & (S0 - 1)) == 0) {
+    while ((1 << a.rsh) < S0) ++a.rsh;
+    a.rmask = 15;
+  }
+  a.divnx = make_fastdiv((unsigned)tx.L);
+  a.divny = make_fastdiv((unsigned)ty.L);
+  a.nplanes = (unsigned)planes;
+  const void* fn = dir < 0 ? (const void*)&ax::plane_pass_kernel<-1> : (const void*)&ax::plane_pass_kernel<1>;
+  int per_sm = 0;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, ax::kPlaneThreads, smem) !=
+          cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    return FFT3D_ERR_CUDA;
+  }
+  out->args = a;
+  out->dir = dir;
+  out->smem = smem;
+  out->threads = ax::kPlaneThreads;
+  out->grid = (int)std::min<long long>(planes, (long long)per_sm * sms);
+  return FFT3D_SUCCESS;
+}
+
+cudaError_t launch_plane_pass(const PlaneLaunch& l, const float2* in, float2* out,
+                              cudaStream_t stream) {
+  PlaneArgs a = l.args;
+  a.in = in;
+  a.out = out;
+  if (l.dir < 0)
+    ax::plane_pass_kernel<-1><<<l.grid, ax::kPlaneThreads, l.smem, stream>>>(a);
+  else
+    ax::plane_pass_kernel<1><<<l.grid, ax::kPlaneThreads, l.smem, stream>>>(a);
   return cudaGetLastError();
 }
 

@@ -128,6 +128,38 @@ struct AxisArgs {
   float scale;
   int do_scale;
 };
+// The x and y passes fused for planes that fit shared memory (axis.cu):
+// one nx x ny plane per block at a time, x stages over its rows, y stages
+// over its columns, one read and one write of the plane.
+struct AxisStages {
+  int L, nst;
+  int radix[kAxisMaxStages], span[kAxisMaxStages], sub[kAxisMaxStages], twst[kAxisMaxStages];
+  FastDiv divsub[kAxisMaxStages];
+};
+struct PlaneArgs {
+  const float2* in;
+  float2* out;
+  const float2 *twx, *twy;
+  const unsigned short *posx, *posy;
+  AxisStages sx, sy;
+  int nx, ny, px;      // row pitch px: odd, >= nx
+  int rsh, rmask;      // element x of a row sits at x ^ ((x >> rsh) & rmask)
+  FastDiv divnx, divny;
+  unsigned nplanes;
+};
+struct PlaneLaunch {
+  PlaneArgs args{};
+  int dir = -1;
+  int grid = 0, threads = 0;
+  size_t smem = 0;
+};
+// Shared memory a plane pass of an nx x ny plane needs (0 if it does not fit).
+size_t plane_pass_smem(int nx, int ny);
+int prepare_plane_pass(const AxisTable& tx, const AxisTable& ty, int dir, long long planes, int sms,
+                       PlaneLaunch* out);
+cudaError_t launch_plane_pass(const PlaneLaunch& l, const float2* in, float2* out,
+                              cudaStream_t stream);
+
 struct AxisLaunch {
   AxisArgs args{};
   int dir = -1;
