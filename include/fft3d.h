@@ -282,11 +282,12 @@ int fft3d_selftest_wait_timeout(int64_t timeout_ns);
  * multiprocessor), with the buffer requirements of the tensor-TMA FP32
  * variants; the block-floating-point and FP8 kinds exist on 9 only.  10:
  * the general path (every plan that is not cubic with a fused edge;
- * selectable for those too): per chunk of grids that fits 40% of L2, three
- * launches, the x pass (in -> out) and the y and z passes in place on out,
- * each a batched 1D transform of the pencils of one axis in shared-memory
- * tiles (mixed radices 2, 3, 4, 5, 6, 8, 9, 10, 12, 15, 16;
- * fft3d_axis_digit_map).  Mixed plans: 0 one launch of the mixed-edge
+ * selectable for those too): per chunk of grids that fits 40% of L2, the x
+ * pass (in -> out) and the y and z passes in place on out, each a batched
+ * 1D transform of the pencils of one axis in shared-memory tiles (mixed
+ * radices 2, 3, 4, 5, 6, 8, 9, 10, 12, 15, 16; fft3d_axis_digit_map);
+ * where a plane of at least 4096 points fits shared memory, x and y run as
+ * one plane pass (two launches per chunk instead of three).  Mixed plans: 0 one launch of the mixed-edge
  * kernel, 1 one launch per distinct edge (the default; an edge whose
  * default is a tensor-TMA kernel takes variant 0 at 64^3 and 5 at 128^3,
  * which address grids through the plan's map).
