@@ -365,6 +365,25 @@ int fft3d_hartree_energy(const void* rhohat, int n, int batch, double L,
 int fft3d_hartree_seed(const void* rhohat, int n, int batch, double L,
                        const double* grad_energy, void* seed, void* stream);
 
+/*
+ * The same two steps on HALF spectra, for real densities (n even): rhohat_half
+ * and seed_half are the half spectra kx = 0 .. n/2 of fft3d_real_execute's
+ * layout (batch * n * n * (n/2 + 1) complex64 points, index
+ * (kz*n + ky)*(n/2 + 1) + kx).  Since F(rho)(-k) = conj F(rho)(k) for a
+ * real rho, the energy counts every point with 0 < kx < n/2 twice (its
+ * mirror is not stored) and the points kx = 0, n/2 once: the same E_H as
+ * fft3d_hartree_energy on the full spectrum, from about half the reads.
+ * The seed is Hermitian as well, so the real inverse transform of
+ * seed_half (fft3d_real_execute, FFT3D_INVERSE, unnormalised) is
+ * grad_energy[b] * dE_H/drho.  workspace: as for fft3d_hartree_energy (its
+ * size covers both).  FFT3D_ERR_INVALID_ARG for odd n.
+ */
+int fft3d_hartree_energy_half(const void* rhohat_half, int n, int batch, double L,
+                              double* energy, void* workspace, size_t workspace_bytes,
+                              void* stream);
+int fft3d_hartree_seed_half(const void* rhohat_half, int n, int batch, double L,
+                            const double* grad_energy, void* seed_half, void* stream);
+
 /* out[i] = (re[i], 0) for i < count (device float -> complex64). */
 int fft3d_real_to_complex(const float* re, void* out, int64_t count, void* stream);
 

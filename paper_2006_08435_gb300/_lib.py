@@ -51,6 +51,8 @@ _SIGS = {
     "fft3d_hartree_workspace_bytes": (ctypes.c_size_t, [_I, _I]),
     "fft3d_hartree_energy": (_I, [_VP, _I, _I, ctypes.c_double, _VP, _VP, ctypes.c_size_t, _VP]),
     "fft3d_hartree_seed": (_I, [_VP, _I, _I, ctypes.c_double, _VP, _VP, _VP]),
+    "fft3d_hartree_energy_half": (_I, [_VP, _I, _I, ctypes.c_double, _VP, _VP, ctypes.c_size_t, _VP]),
+    "fft3d_hartree_seed_half": (_I, [_VP, _I, _I, ctypes.c_double, _VP, _VP, _VP]),
     "fft3d_real_to_complex": (_I, [_VP, _VP, ctypes.c_int64, _VP]),
     "fft3d_plan_variant": (_I, [_VP, ctypes.POINTER(_I)]),
     "fft3d_plan_host_io": (_I, [_VP, _I]),

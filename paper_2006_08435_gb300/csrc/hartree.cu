@@ -35,9 +35,17 @@ __host__ __device__ inline int energy_blocks(long long npts) {
 
 __device__ __forceinline__ int signed_index(int k, int n) { return k < (n + 1) / 2 ? k : k - n; }
 
-__device__ __forceinline__ int m_squared(long long i, int n) {
-  const int kx = (int)(i % n), ky = (int)((i / n) % n), kz = (int)(i / ((long long)n * n));
+// |m|^2 of point i of a full spectrum (HALF false: rows of n) or of a half
+// spectrum (HALF true: rows of n / 2 + 1, kx = 0 .. n / 2), and in *w the
+// number of points of the full spectrum the point stands for: a real
+// grid's spectrum has |F(-k)| = |F(k)|, so a half-spectrum point with
+// 0 < kx < n / 2 counts twice (its mirror kx -> n - kx is not stored).
+template <bool HALF>
+__device__ __forceinline__ int m_squared(long long i, int n, int* w = nullptr) {
+  const int h = HALF ? n / 2 + 1 : n;
+  const int kx = (int)(i % h), ky = (int)((i / h) % n), kz = (int)(i / ((long long)h * n));
   const int mx = signed_index(kx, n), my = signed_index(ky, n), mz = signed_index(kz, n);
+  if (w) *w = HALF && kx != 0 && 2 * kx != n ? 2 : 1;
   return mx * mx + my * my + mz * mz;
 }
 
@@ -48,7 +56,9 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // One row of blocks per grid (blockIdx.y).  partials: [batch][gridDim.x];
-// counters: [batch], zero on entry, left at zero by the last block.
+// counters: [batch], zero on entry, left at zero by the last block.  npts:
+// points per grid of the (full or half) spectrum.
+template <bool HALF>
 __global__ void __launch_bounds__(kRedThreads) hartree_energy_kernel(
     const float2* __restrict__ f, int n, long long npts, double half_s,
     double* __restrict__ partials, unsigned* __restrict__ counters, double* __restrict__ energy) {
@@ -57,7 +67,8 @@ __global__ void __launch_bounds__(kRedThreads) hartree_energy_kernel(
   double acc = 0.0;
   for (long long i = (long long)blockIdx.x * kRedThreads + threadIdx.x; i < npts;
        i += (long long)gridDim.x * kRedThreads) {
-    const int m2 = m_squared(i, n);
+    int w = 1;
+    const int m2 = m_squared<HALF>(i, n, &w);
     if (m2 != 0) {
       const float2 v = fb[i];
       // 1/m2 in FP64: the correctly rounded FP32 reciprocal (relative error
@@ -66,7 +77,7 @@ __global__ void __launch_bounds__(kRedThreads) hartree_energy_kernel(
       // division on the FP64 units)
       const double r0 = (double)(1.0f / (float)m2);
       const double inv = fma(r0, fma(-(double)m2, r0, 1.0), r0);
-      acc += ((double)v.x * v.x + (double)v.y * v.y) * inv;
+      acc += ((double)v.x * v.x + (double)v.y * v.y) * (inv * (double)w);
     }
   }
   __shared__ double warp_part[kRedThreads / 32];
@@ -92,6 +103,7 @@ __global__ void __launch_bounds__(kRedThreads) hartree_energy_kernel(
   }
 }
 
+template <bool HALF>
 __global__ void hartree_seed_kernel(const float2* __restrict__ f, int n, long long npts, double s,
                                     const double* __restrict__ grad_e, float2* __restrict__ seed) {
   const int b = blockIdx.y;
@@ -100,7 +112,7 @@ __global__ void hartree_seed_kernel(const float2* __restrict__ f, int n, long lo
   float2* sb = seed + (long long)b * npts;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < npts;
        i += (long long)gridDim.x * blockDim.x) {
-    const int m2 = m_squared(i, n);
+    const int m2 = m_squared<HALF>(i, n);
     float2 o = make_float2(0.0f, 0.0f);
     if (m2 != 0) {
       const float2 v = fb[i];
@@ -154,14 +166,19 @@ size_t fft3d_hartree_workspace_bytes(int n, int batch) {
   return ((partials + 255) & ~size_t(255)) + sizeof(unsigned) * (size_t)batch;
 }
 
-int fft3d_hartree_energy(const void* rhohat, int n, int batch, double L, double* energy,
-                         void* workspace, size_t workspace_bytes, void* stream) {
+}  // extern "C"
+
+namespace {
+
+template <bool HALF>
+int energy_impl(const void* rhohat, int n, int batch, double L, double* energy, void* workspace,
+                size_t workspace_bytes, void* stream) {
   if (!rhohat || !energy || !workspace) return FFT3D_ERR_NULL_PTR;
-  if (!valid_grid(n, batch, L)) return FFT3D_ERR_INVALID_ARG;
+  if (!valid_grid(n, batch, L) || (HALF && (n & 1))) return FFT3D_ERR_INVALID_ARG;
   if (workspace_bytes < fft3d_hartree_workspace_bytes(n, batch)) return FFT3D_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(rhohat) & 7u || reinterpret_cast<uintptr_t>(workspace) & 7u)
     return FFT3D_ERR_MISALIGNED;
-  const long long npts = (long long)n * n * n;
+  const long long npts = (long long)n * n * (HALF ? n / 2 + 1 : n);
   const int blocks = energy_blocks(npts);
   const size_t partial_bytes = sizeof(double) * (size_t)batch * (size_t)blocks;
   unsigned char* ws = static_cast<unsigned char*>(workspace);
@@ -171,26 +188,51 @@ int fft3d_hartree_energy(const void* rhohat, int n, int batch, double L, double*
     cudaGetLastError();
     return FFT3D_ERR_CUDA;
   }
-  hartree_energy_kernel<<<dim3(blocks, batch), kRedThreads, 0, s>>>(
+  hartree_energy_kernel<HALF><<<dim3(blocks, batch), kRedThreads, 0, s>>>(
       static_cast<const float2*>(rhohat), n, npts, 0.5 * hartree_s(n, L),
       reinterpret_cast<double*>(ws), counters, energy);
   if (cudaGetLastError() != cudaSuccess) return FFT3D_ERR_CUDA;
   return FFT3D_SUCCESS;
 }
 
-int fft3d_hartree_seed(const void* rhohat, int n, int batch, double L, const double* grad_energy,
-                       void* seed, void* stream) {
+template <bool HALF>
+int seed_impl(const void* rhohat, int n, int batch, double L, const double* grad_energy,
+              void* seed, void* stream) {
   if (!rhohat || !grad_energy || !seed) return FFT3D_ERR_NULL_PTR;
-  if (!valid_grid(n, batch, L)) return FFT3D_ERR_INVALID_ARG;
+  if (!valid_grid(n, batch, L) || (HALF && (n & 1))) return FFT3D_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(rhohat) & 7u || reinterpret_cast<uintptr_t>(seed) & 7u)
     return FFT3D_ERR_MISALIGNED;
-  const long long npts = (long long)n * n * n;
+  const long long npts = (long long)n * n * (HALF ? n / 2 + 1 : n);
   const int bx = grid_for(npts, 256) / batch + 1;
-  hartree_seed_kernel<<<dim3(bx, batch), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+  hartree_seed_kernel<HALF><<<dim3(bx, batch), 256, 0, static_cast<cudaStream_t>(stream)>>>(
       static_cast<const float2*>(rhohat), n, npts, hartree_s(n, L), grad_energy,
       static_cast<float2*>(seed));
   if (cudaGetLastError() != cudaSuccess) return FFT3D_ERR_CUDA;
   return FFT3D_SUCCESS;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fft3d_hartree_energy(const void* rhohat, int n, int batch, double L, double* energy,
+                         void* workspace, size_t workspace_bytes, void* stream) {
+  return energy_impl<false>(rhohat, n, batch, L, energy, workspace, workspace_bytes, stream);
+}
+
+int fft3d_hartree_energy_half(const void* rhohat_half, int n, int batch, double L, double* energy,
+                              void* workspace, size_t workspace_bytes, void* stream) {
+  return energy_impl<true>(rhohat_half, n, batch, L, energy, workspace, workspace_bytes, stream);
+}
+
+int fft3d_hartree_seed(const void* rhohat, int n, int batch, double L, const double* grad_energy,
+                       void* seed, void* stream) {
+  return seed_impl<false>(rhohat, n, batch, L, grad_energy, seed, stream);
+}
+
+int fft3d_hartree_seed_half(const void* rhohat_half, int n, int batch, double L,
+                            const double* grad_energy, void* seed_half, void* stream) {
+  return seed_impl<true>(rhohat_half, n, batch, L, grad_energy, seed_half, stream);
 }
 
 int fft3d_real_to_complex(const float* re, void* out, int64_t count, void* stream) {

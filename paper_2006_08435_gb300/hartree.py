@@ -4,15 +4,19 @@ E_H(rho) = (Omega/2) sum_{G != 0} 4 pi |rho_hat(G)|^2 / |G|^2 with
 rho_hat = F(rho) / n^3 for a periodic cubic cell of side L (bohr); the
 gradient dE_H/drho = (Omega/n^3) V_H is the adjoint (inverse, unnormalised)
 transform of the seed s F(rho) / |m|^2.  Every step runs in the library's
-kernels: real->complex, forward FFT, FP64 energy reduction; seed, inverse
-FFT, complex->real.
+kernels.  For even n (the usual grids) the density being real, the path
+works on half spectra: real-grid forward transform, FP64 energy reduction
+over the half spectrum (mirrored points counted twice); seed on the half
+spectrum, real-grid inverse transform.  For odd n: real->complex, complex
+forward transform, full-spectrum reduction; seed, complex inverse,
+complex->real.
 """
 from __future__ import annotations
 
 import torch
 
 from . import _lib as L
-from .fft import _stream_handle, fft3d
+from .fft import _stream_handle, fft3d, irfft3d, rfft3d
 
 _ws_cache: dict = {}
 
@@ -62,6 +66,34 @@ def energy_from_spectrum(rhohat: torch.Tensor, cell: float) -> torch.Tensor:
     return e.reshape(rhohat.shape[:-3])
 
 
+def energy_from_half_spectrum(rhohat_half: torch.Tensor, cell: float) -> torch.Tensor:
+    """E_H per grid from the half spectrum rfft3d(rho) (complex64,
+    (..., n, n, n // 2 + 1), n even); FP64."""
+    n = rhohat_half.shape[-2]
+    batch = rhohat_half.numel() // (n * n * (n // 2 + 1))
+    rhohat_half = rhohat_half.contiguous()
+    e = torch.empty(batch, dtype=torch.float64, device=rhohat_half.device)
+    ws = _workspace(n, batch, rhohat_half.device)
+    L.check(L.lib().fft3d_hartree_energy_half(rhohat_half.data_ptr(), n, batch, float(cell),
+                                              e.data_ptr(), ws.data_ptr(), ws.numel(),
+                                              _stream_handle(None)), "fft3d_hartree_energy_half")
+    return e.reshape(rhohat_half.shape[:-3])
+
+
+def seed_from_half_spectrum(rhohat_half: torch.Tensor, cell: float,
+                            grad_e: torch.Tensor) -> torch.Tensor:
+    n = rhohat_half.shape[-2]
+    batch = rhohat_half.numel() // (n * n * (n // 2 + 1))
+    g = grad_e.to(torch.float64).contiguous().reshape(-1)
+    if g.numel() != batch:
+        raise ValueError("one gradient per grid")
+    seed = torch.empty_like(rhohat_half)
+    L.check(L.lib().fft3d_hartree_seed_half(rhohat_half.data_ptr(), n, batch, float(cell),
+                                            g.data_ptr(), seed.data_ptr(), _stream_handle(None)),
+            "fft3d_hartree_seed_half")
+    return seed
+
+
 def seed_from_spectrum(rhohat: torch.Tensor, cell: float, grad_e: torch.Tensor) -> torch.Tensor:
     n = rhohat.shape[-1]
     batch = rhohat.numel() // n ** 3
@@ -82,14 +114,22 @@ class HartreeEnergy(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, rho, cell):
+        ctx.cell = float(cell)
+        ctx.half = rho.shape[-1] % 2 == 0
+        if ctx.half:
+            rhohat = rfft3d(rho.contiguous())
+            ctx.save_for_backward(rhohat)
+            return energy_from_half_spectrum(rhohat, cell)
         rhohat = fft3d(real_to_complex(rho))
         ctx.save_for_backward(rhohat)
-        ctx.cell = float(cell)
         return energy_from_spectrum(rhohat, cell)
 
     @staticmethod
     def backward(ctx, grad_e):
         (rhohat,) = ctx.saved_tensors
+        if ctx.half:
+            seed = seed_from_half_spectrum(rhohat, ctx.cell, grad_e)
+            return irfft3d(seed), None
         seed = seed_from_spectrum(rhohat, ctx.cell, grad_e)
         return complex_to_real(fft3d(seed, inverse=True)), None
 
