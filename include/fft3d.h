@@ -266,7 +266,9 @@ int fft3d_selftest_wait_timeout(int64_t timeout_ns);
  * The kernel variant a plan uses (written to *variant).  Single-edge FP32
  * plans (each variant the fastest for some edge and batch on the GB300):
  * 0 plain persistent kernel, 1 the same with twice the threads per block
- * (16^3 .. 96^3), 3 the cluster-fused single-pass kernel (16^3, 32^3), 4
+ * (16^3 .. 96^3), 3 the cluster-fused single-pass kernel (16^3, 32^3), 12
+ * a whole 16^3 grid per block (three passes of thread-per-pencil 16-point
+ * DFTs in shared memory, no work counters), 4
  * the double-buffered persistent kernel (32^3, 48^3, 80^3, 96^3), 5 the
  * warp-owned two-phase kernel (64^3, 128^3), 7 the thread-per-pencil
  * kernel (each 1D FFT in one thread's registers, items loaded by swizzled

@@ -65,6 +65,7 @@ struct KernelInfo {
   int tw_l1 = 0;                // twiddle table split n = l1 * (n / l1); 0: item_l1(n, prec)
   int phase_items = 0;          // work items per phase of a grid; 0: the grid's edge
   int umma_b = 0;               // mma_frag holds the tcgen05 B table (tcgen.cuh), not mma.sync fragments
+  int uses_work = 1;            // 0: no ticket counters (nothing to clear before a launch)
 };
 
 // ---------------------------------------------------------------- general path

@@ -176,7 +176,7 @@ static bool fused_size(int n) { return fused_slot(n) >= 0; }
 // Kernel variants of a single-size FP32 plan (each the fastest for some
 // edge and batch on the GB300): 0 plain persistent kernel, 1 the same with
 // twice the threads (16^3 to 96^3), 3 the cluster-fused single-pass kernel
-// (16^3, 32^3), 4 the double-buffered persistent kernel (32^3, 48^3, 80^3,
+// (16^3, 32^3), 12 a whole 16^3 grid per block, 4 the double-buffered persistent kernel (32^3, 48^3, 80^3,
 // 96^3), 5 the warp-owned two-phase kernel (64^3, 128^3), 6 to 8 the
 // tensor-TMA thread-per-pencil kernels (128^3 split-y; 64^3 one-plane and
 // two-plane items).  Tensor-core precisions: 0 the plain persistent kernel,
@@ -194,7 +194,7 @@ std::vector<int> variant_candidates(bool mixed, int n, int precision) {
   if (precision != FFT3D_FP32) return {0, 9};
   if (!fused_size(n)) return {kGeneralVariant};
   switch (n) {
-    case 16: return {0, 1, 3, kGeneralVariant};
+    case 16: return {0, 1, 3, kGeneralVariant, 12};
     case 32: return {0, 1, 3, 4, kGeneralVariant};
     case 64: return {0, 1, 5, 7, 8, kGeneralVariant};
     case 128: return {0, 5, 6, kGeneralVariant};
@@ -204,7 +204,8 @@ std::vector<int> variant_candidates(bool mixed, int n, int precision) {
 
 // The fastest variant measured on the GB300 for each edge and batch
 // (back-to-back executes; one grid also with L2 flushed):
-//   16^3, 32^3: plain persistent below 64 grids, cluster-fused from 64;
+//   16^3: plain persistent for one grid, whole grid per block from 2;
+//   32^3: plain persistent below 64 grids, cluster-fused from 64;
 //   48^3, 96^3: plain persistent;  80^3: plain persistent for one grid,
 //     the double-buffered persistent kernel from 4 (0.67x the time at 256);
 //   64^3: warp-owned for one grid, the persistent kernel with twice the
@@ -219,7 +220,11 @@ int builtin_default_variant(bool mixed, int n, int batch, int precision) {
   if (precision >= FFT3D_BFP16) return 9;
   if (precision != FFT3D_FP32) return (n == 64 && batch >= 16) || (n == 128 && batch >= 2) ? 9 : 0;
   switch (n) {
-    case 16:
+    // 16^3: the whole-grid kernel from 2 grids (x 4096: 74 us against 111 us
+    // for the cluster kernel; 0.53 of the roofline); one grid: the
+    // persistent kernel (L2 flushed: 11.9 us against 15.0 us, its grid
+    // spread over 32 blocks instead of one)
+    case 16: return batch >= 2 ? 12 : 0;
     case 32: return batch >= 64 ? 3 : 0;
     case 64: return batch == 1 ? 5 : batch < 16 ? 1 : batch < 64 ? 7 : 8;
     case 80: return batch >= 4 ? 4 : 0;
@@ -503,8 +508,10 @@ int launch(fft3d_plan p, const float2* in, float2* out, const float2* const* in_
            float2* const* out_ptrs, cudaStream_t stream) {
   if (p->general) return launch_general(p, in, out, stream);
   for (const Unit& u : p->units) {
-    // ticket kernels start from zeroed counters; cluster kernels use none
-    if (u.kernel.cluster == 0 && cudaMemsetAsync(u.d_work, 0, u.work_bytes, stream) != cudaSuccess) {
+    // ticket kernels start from zeroed counters; cluster and whole-grid
+    // kernels use none
+    if (u.kernel.cluster == 0 && u.kernel.uses_work &&
+        cudaMemsetAsync(u.d_work, 0, u.work_bytes, stream) != cudaSuccess) {
       cudaGetLastError();
       return FFT3D_ERR_CUDA;
     }
