@@ -410,9 +410,14 @@ int fft3d_complex_to_real(const void* in, float* re, int64_t count, void* stream
  * and for any other input the imaginary parts of the self-mirrored bins
  * (kx, ky, kz each 0 or n/2) drop out.  `in` is not modified.
  *
- * Two grids of the batch share one complex transform (c = a + i b; the pair
- * is separated with the symmetry above), so a grid's rounding error is
- * relative to the larger of its pair.  Cost per pair: a packing pass, one
+ * At n = 128 in FP32 the transforms run as dedicated kernels: each real row
+ * of n points is transformed as n/2 complex points and split into its half
+ * spectrum (the even and odd samples' transforms, X[k] = E[k] + W_n^k O[k]),
+ * so the y and z transforms run on n/2 (+ 1) columns; one pass over the real
+ * grids and one over the half spectra, each grid's error relative to itself.
+ * Elsewhere two grids of the batch share one complex transform (c = a + i b;
+ * the pair is separated with the symmetry above), so a grid's rounding error
+ * is relative to the larger of its pair; cost per pair: a packing pass, one
  * complex transform of the plan's precision, a separating pass.
  * ---------------------------------------------------------------------------
  */
@@ -427,9 +432,12 @@ typedef struct fft3d_real_plan_s* fft3d_real_plan;
  *   direction : FFT3D_FORWARD (real -> half spectrum) or FFT3D_INVERSE
  *               (half spectrum -> real).
  *   norm      : fft3d_norm (1/n^3 or 1/sqrt(n^3) on the output).
- * Validates its arguments before touching the GPU.  Owns a complex plan of
- * ceil(batch/2) grids and a device workspace of ceil(batch/2) * n^3 complex64
- * points, both allocated here and freed by fft3d_real_plan_destroy.
+ * Validates its arguments before touching the GPU.  Owns its device memory,
+ * allocated here and freed by fft3d_real_plan_destroy: at n = 128 in FP32 a
+ * schedule, counters and (forward) batch * n * n/2 complex64 points of
+ * workspace; elsewhere a complex plan of ceil(batch/2) grids and a workspace
+ * of ceil(batch/2) * n^3 complex64 points.  The environment variable
+ * FFT3D_REAL_PATH=pairs selects the pair scheme everywhere (for testing).
  */
 int fft3d_real_plan_create(int n, int batch, int precision, int direction, int norm,
                            fft3d_real_plan* out_plan);
@@ -438,8 +446,10 @@ int fft3d_real_plan_create(int n, int batch, int precision, int direction, int n
  * Transform every grid of the plan.  `in` and `out` are DEVICE pointers,
  * 16-byte aligned, not overlapping (forward: in = real grids, out = half
  * spectra; inverse: the other way round).  Asynchronous on `stream`,
- * allocates nothing, capturable in a CUDA graph (a packing or rebuilding
- * kernel, the complex plan's launch, a separating or splitting kernel).  A plan may run on one stream at a time.
+ * allocates nothing, capturable in a CUDA graph (a counter reset and one
+ * kernel at n = 128 in FP32; elsewhere a packing or rebuilding kernel, the
+ * complex plan's launch, a separating or splitting kernel).  A plan may run
+ * on one stream at a time.
  */
 int fft3d_real_execute(fft3d_real_plan plan, const void* in, void* out, void* stream);
 

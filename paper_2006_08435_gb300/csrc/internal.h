@@ -47,6 +47,7 @@ struct FusedArgs {
   long long timeout_ns;
   const uint32_t* mma_frag;     // tensor-core B fragments (split precisions), or null
   int ngrids;                   // grids of the launch unit
+  float2* aux;                  // a kernel's own workspace (real grids: Nyquist columns), or null
 };
 
 using LaunchFn = cudaError_t (*)(const FusedArgs&, int grid, cudaStream_t);
@@ -175,6 +176,7 @@ cudaError_t launch_axis_pass(const AxisLaunch& l, const float2* in, float2* out,
 KernelInfo fused_kernel_info(int n, int dir, int variant);   // single-size kernel
 KernelInfo mixed_kernel_info(int dir);          // all fused sizes
 KernelInfo tc_kernel_info(int n, int dir, int prec, int variant);  // tensor-core kinds
+KernelInfo real_kernel_info(int n, int dir);    // real grids (rgrid.cuh); launch null: none
 cudaError_t launch_wait_selftest(unsigned* flag, unsigned* status, long long timeout_ns,
                                  cudaStream_t stream);
 

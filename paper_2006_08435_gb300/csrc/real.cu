@@ -17,20 +17,42 @@
 // spectra A, B are rebuilt as one full spectrum H(A) + i H(B), transformed
 // once, and the real and imaginary parts of the result are the two grids.
 //
-// The kernels here move data only (pack, separate, rebuild, split); the
-// transforms are the library's complex plans.  Packing two grids into one
-// makes each grid's rounding error relative to the larger of the pair.
+// At 128^3 in FP32 the transforms run instead as dedicated two-phase
+// kernels (rgrid.cuh: half-length row transforms, one pass over the real
+// grid and one over the half spectrum, a workspace of n^2/2 complex per
+// grid for the Nyquist column of the forward transform); everywhere else the
+// pair scheme above, whose kernels here move data only (pack, separate,
+// rebuild, split) and whose transforms are the library's complex plans.
+// Packing two grids into one makes each grid's rounding error relative to
+// the larger of the pair.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
+#include <cstdlib>
+#include <cstring>
 #include <new>
+#include <vector>
 
 #include "fft3d.h"
+#include "internal.h"
+#include "schedule.h"
 
 struct fft3d_real_plan_s {
   int n = 0, batch = 0, pairs = 0, direction = FFT3D_FORWARD;
+  // pair scheme
   fft3d_plan inner = nullptr;  // complex plan of `pairs` n^3 grids
   float2* d_work = nullptr;    // pairs * n^3 complex points
+  // dedicated kernels (rgrid.cuh)
+  bool fused = false;
+  fft3d::KernelInfo kern;
+  fft3d::SchedBlock* d_blocks = nullptr;
+  unsigned* d_count = nullptr;   // [0] ticket, [1 + g] phase-0 items of grid g done
+  unsigned* d_status = nullptr;
+  float2* d_aux = nullptr;       // forward: n * n/2 complex per grid (Nyquist pencils)
+  int nblocks = 0, total_items = 0, grid = 0;
+  float scale = 1.0f;
+  int do_scale = 0;
 };
 
 namespace fft3d {
@@ -155,7 +177,114 @@ __global__ void rebuild_pairs_kernel(const float2* __restrict__ x, float2* __res
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+void free_fused(fft3d_real_plan p) {
+  cudaFree(p->d_aux);
+  cudaFree(p->d_blocks);
+  cudaFree(p->d_count);
+  cudaFree(p->d_status);
+}
+
 }  // namespace
+
+// Plan of the dedicated kernels: phase 0 has n items per grid (forward:
+// planes; inverse: z rows), phase 1 n items (forward: z rows, plus the
+// Nyquist column; inverse: planes).  The schedule's L2 budget counts 8 n^3
+// bytes of intermediate per grid (a complex grid); a real grid's is about
+// half of that, so the budget passed is scaled by the ratio.
+int create_fused_real(int n, int batch, int direction, int norm, const KernelInfo& k,
+                      fft3d_real_plan* out_plan) {
+  int dev = -1, sms = 0, l2 = 0, major = 0, minor = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return FFT3D_ERR_NO_DEVICE;
+  }
+  if (major != 10 || minor != 3) return FFT3D_ERR_NO_DEVICE;
+  if (cudaFuncSetAttribute(k.func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return FFT3D_ERR_CUDA;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.func, k.threads, k.smem) !=
+          cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    return FFT3D_ERR_CUDA;
+  }
+  const int resident = per_sm * sms;
+  const int forward = direction == FFT3D_FORWARD;
+  const double n3 = (double)n * n * n;
+  const double inter = forward ? (double)n * n * (n / 2 + 1) * 8.0 : 4.0 * n3;
+  std::vector<int> dims(batch, n), order(batch), plane_end(batch);
+  for (int g = 0; g < batch; ++g) order[g] = g;
+  std::vector<SchedBlock> blocks(2 * (size_t)batch);
+  int total = 0;
+  const int nb = schedule_blocks(batch, dims.data(), order.data(), resident * k.items_in_flight,
+                                 0.4 * (double)l2 * (8.0 * n3 / inter), 0, plane_end.data(),
+                                 blocks.data(), &total, forward ? 1 : 0);
+  auto* p = new (std::nothrow) fft3d_real_plan_s();
+  if (!p) return FFT3D_ERR_ALLOC;
+  p->n = n;
+  p->batch = batch;
+  p->direction = direction;
+  p->fused = true;
+  p->kern = k;
+  p->nblocks = nb;
+  p->total_items = total;
+  p->grid = total < resident ? total : resident;
+  if (norm == FFT3D_NORM_BY_N) {
+    p->scale = (float)(1.0 / n3);
+    p->do_scale = 1;
+  } else if (norm == FFT3D_NORM_ORTHO) {
+    p->scale = (float)(1.0 / std::sqrt(n3));
+    p->do_scale = 1;
+  }
+  if (cudaMalloc(&p->d_blocks, sizeof(SchedBlock) * (size_t)nb) != cudaSuccess ||
+      cudaMalloc(&p->d_count, sizeof(unsigned) * (size_t)(batch + 1)) != cudaSuccess ||
+      cudaMalloc(&p->d_status, sizeof(unsigned)) != cudaSuccess ||
+      cudaMemcpy(p->d_blocks, blocks.data(), sizeof(SchedBlock) * (size_t)nb,
+                 cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(p->d_status, 0, sizeof(unsigned)) != cudaSuccess ||
+      (forward && cudaMalloc(&p->d_aux, sizeof(float2) * (size_t)batch * n * (n / 2)) !=
+                      cudaSuccess)) {
+    cudaGetLastError();
+    free_fused(p);
+    delete p;
+    return FFT3D_ERR_ALLOC;
+  }
+  *out_plan = p;
+  return FFT3D_SUCCESS;
+}
+
+int execute_fused_real(fft3d_real_plan p, const void* in, void* out, cudaStream_t s) {
+  if (cudaMemsetAsync(p->d_count, 0, sizeof(unsigned) * (size_t)(p->batch + 1), s) != cudaSuccess) {
+    cudaGetLastError();
+    return FFT3D_ERR_CUDA;
+  }
+  FusedArgs a{};
+  a.in = static_cast<const float2*>(in);
+  a.out = static_cast<float2*>(out);
+  a.blocks = p->d_blocks;
+  a.nblocks = p->nblocks;
+  a.total_items = p->total_items;
+  a.work = p->d_count;
+  a.status = p->d_status;
+  a.scale = p->scale;
+  a.do_scale = p->do_scale;
+  a.timeout_ns = kDefaultWaitNs;
+  a.ngrids = p->batch;
+  a.aux = p->d_aux;
+  if (p->kern.launch(a, p->grid, s) != cudaSuccess) {
+    cudaGetLastError();
+    return FFT3D_ERR_CUDA;
+  }
+  return FFT3D_SUCCESS;
+}
+
 }  // namespace fft3d
 
 extern "C" {
@@ -166,6 +295,14 @@ int fft3d_real_plan_create(int n, int batch, int precision, int direction, int n
   *out_plan = nullptr;
   if (batch < 1 || batch > (1 << 24)) return FFT3D_ERR_INVALID_ARG;
   if (n < 2 || (n & 1) || !fft3d_size_supported(n)) return FFT3D_ERR_UNSUPPORTED_SIZE;
+  if (direction != FFT3D_FORWARD && direction != FFT3D_INVERSE) return FFT3D_ERR_INVALID_ARG;
+  if (norm < FFT3D_NORM_NONE || norm > FFT3D_NORM_ORTHO) return FFT3D_ERR_INVALID_ARG;
+  const char* path = std::getenv("FFT3D_REAL_PATH");  // "pairs": the pair scheme everywhere
+  const bool pairs_only = path && std::strcmp(path, "pairs") == 0;
+  if (precision == FFT3D_FP32 && !pairs_only) {
+    const fft3d::KernelInfo k = fft3d::real_kernel_info(n, direction == FFT3D_FORWARD ? -1 : 1);
+    if (k.launch) return fft3d::create_fused_real(n, batch, direction, norm, k, out_plan);
+  }
   const int pairs = (batch + 1) / 2;
   fft3d_plan inner = nullptr;
   int rc = fft3d_plan_create(n, n, n, pairs, precision, direction, norm, &inner);
@@ -196,6 +333,7 @@ int fft3d_real_execute(fft3d_real_plan plan, const void* in, void* out, void* st
   if (!plan || !in || !out) return FFT3D_ERR_NULL_PTR;
   if (!aligned16(in) || !aligned16(out)) return FFT3D_ERR_MISALIGNED;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (plan->fused) return execute_fused_real(plan, in, out, s);
   const int n = plan->n, batch = plan->batch, pairs = plan->pairs;
   const int q = n * n * n / 4, h = n / 2 + 1;
   if (plan->direction == FFT3D_FORWARD) {
@@ -221,11 +359,25 @@ int fft3d_real_execute(fft3d_real_plan plan, const void* in, void* out, void* st
 
 int fft3d_real_get_device_status(fft3d_real_plan plan, void* stream) {
   if (!plan) return FFT3D_ERR_NULL_PTR;
-  return fft3d_get_device_status(plan->inner, stream);
+  if (!plan->fused) return fft3d_get_device_status(plan->inner, stream);
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+    cudaGetLastError();
+    return FFT3D_ERR_CUDA;
+  }
+  unsigned st = 0;
+  if (cudaMemcpy(&st, plan->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemset(plan->d_status, 0, sizeof(unsigned)) != cudaSuccess)
+    return FFT3D_ERR_CUDA;
+  return st == fft3d::kStatusOk ? FFT3D_SUCCESS : FFT3D_ERR_DEVICE_TIMEOUT;
 }
 
 int fft3d_real_plan_destroy(fft3d_real_plan plan) {
   if (!plan) return FFT3D_SUCCESS;
+  if (plan->fused) {
+    fft3d::free_fused(plan);
+    delete plan;
+    return FFT3D_SUCCESS;
+  }
   cudaFree(plan->d_work);
   const int rc = fft3d_plan_destroy(plan->inner);
   delete plan;

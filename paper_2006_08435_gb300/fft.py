@@ -186,7 +186,8 @@ class RealPlan:
     complex64 (batch, n, n, n // 2 + 1), the half spectrum of Eq. 1.
     Inverse (``inverse=True``): x is the half spectrum and out the float32
     grids, the real part of the inverse transform of the Hermitian extension.
-    Two grids share one complex transform inside the library."""
+    At 128^3 in FP32 the library runs dedicated real-grid kernels; elsewhere
+    two grids share one complex transform."""
 
     def __init__(self, n: int, batch: int = 1, precision: str = "fp32", inverse: bool = False,
                  norm: str = "none"):
@@ -276,8 +277,8 @@ def fft3d(x: torch.Tensor, inverse: bool = False, norm: str = "none", precision:
         return plan.execute(x, out, stream)
 
 
-# Real plans own a workspace of ceil(batch/2) n^3 complex points (268 MB at
-# 128^3 x 32), so only the most recently used few are kept.  An evicted plan
+# Real plans of the pair scheme own a workspace of ceil(batch/2) n^3 complex
+# points (268 MB at 128^3 x 32), so only the most recently used few are kept.  An evicted plan
 # is only dropped from the cache, not closed: a caller in another thread may
 # still be executing it, and its memory is released (plan destroy, whose
 # cudaFree waits for work still using it) once the last reference to it
