@@ -256,7 +256,7 @@ __device__ __forceinline__ void producer(const FusedArgs& a, const CUtensorMap* 
                                          unsigned long long* done, int* pubq,
                                          volatile int* pub_done, Desc* desc, const int2* sched) {
   using K = Cfg<N>;
-  constexpr int NT = K::NTILE, DQ = K::DQ, G = K::GROUPS, HC = K::HC, H = K::H;
+  constexpr int NT = K::NTILE, DQ = K::DQ, G = K::GROUPS, H = K::H;
   const int lane = threadIdx.x & 31;
   const bool local = a.nblocks <= K::SCHED;
   auto start_of = [&](int b) { return local ? sched[b].x : a.blocks[b].start; };
@@ -492,45 +492,117 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
     unsigned char* t = base + (size_t)s * K::TILE;
     const long long gg = d.grid;
     float2 v[H];
-    if constexpr (DIR < 0) {
-      float2* og = const_cast<float2*>(a.out) + gg * N * N * HC;  // half spectra of grid g
-      if (d.phase == 0) {
-        // x: row y = gt, 16-byte chunks of reals = pairs of complex z[m]
-#pragma unroll
-        for (int j = 0; j < H / 2; ++j) {
-          const float4 q = *reinterpret_cast<const float4*>(t + swz<N>(gt, j));
-          v[2 * j] = make_float2(q.x, q.y);
-          v[2 * j + 1] = make_float2(q.z, q.w);
-        }
-        DFT<H, DIR>::run(v);
-        real_split<H, DIR>(v);
-#pragma unroll
-        for (int j = 0; j < H / 2; ++j)
-          *reinterpret_cast<float4*>(t + swz<N>(gt, j)) =
-              make_float4(v[2 * j].x, v[2 * j].y, v[2 * j + 1].x, v[2 * j + 1].y);
+    // The item's passes share one DFT in a loop (one copy of its code for the
+    // instruction cache): forward 0 plane x, 1 plane y, 2 z, 3 Nyquist;
+    // inverse 0 z, 1 plane y, 2 plane x.
+    int pass;
+    if constexpr (DIR < 0) pass = d.phase == 0 ? 0 : (d.idx < N ? 2 : 3);
+    else pass = d.phase;
+    const int off = 8 * (d.idx & 1);  // z items: column 0 in the tile row
+    bool fail = false;
+    if constexpr (DIR > 0) {
+      if (pass == 0) {
+        // rows (kz, ky = idx) of the input: columns 0 and H -> their
+        // Hermitian parts, packed into column 0 (thread gt = kz)
+        unsigned char* rk = t + gt * P + off;
+        const float2 T0 = *reinterpret_cast<const float2*>(rk);
+        const float2 Th = *reinterpret_cast<const float2*>(rk + 8 * H);
+        // mirror row (-kz, -ky): its columns 0 and h from the mirror boxes
+        const int mz = (N - gt) % N, mo = 16 * mz + 8 * (((N - d.idx) % N) & 1);
+        const float2 M0 = *reinterpret_cast<const float2*>(t + K::MAIN + mo);
+        const float2 Mh = *reinterpret_cast<const float2*>(t + K::MAIN + N * 16 + mo);
+        const float2 A = make_float2(0.5f * (T0.x + M0.x), 0.5f * (T0.y - M0.y));
+        const float2 B = make_float2(0.5f * (Th.x + Mh.x), 0.5f * (Th.y - Mh.y));
+        *reinterpret_cast<float2*>(rk) = make_float2(A.x - B.y, A.y + B.x);  // A + i B
         if (!group_sync()) break;
-        // y: column c (chunk c/2 of every row, half c & 1), outputs ky = 2k +
-        // h, straight to out (kept in L2)
-        {
+      }
+    }
+#pragma unroll 1
+    for (;;) {
+      // ---------------------------------------------------------- in
+      if constexpr (DIR < 0) {
+        if (pass == 0) {
+          // x: row y = gt, 16-byte chunks of reals = pairs of complex z[m]
+#pragma unroll
+          for (int j = 0; j < H / 2; ++j) {
+            const float4 q = *reinterpret_cast<const float4*>(t + swz<N>(gt, j));
+            v[2 * j] = make_float2(q.x, q.y);
+            v[2 * j + 1] = make_float2(q.z, q.w);
+          }
+        } else if (pass == 1) {
+          // y: column c (chunk c/2 of every row, half c & 1)
           const unsigned char* tc = t + (c & 1) * 8;
           auto at = [&](int r) { return reinterpret_cast<const float2*>(tc + swz<N>(r, c >> 1)); };
           if (h == 0) load_dif<N, DIR, 0>(at, v);
           else load_dif<N, DIR, 1>(at, v);
-        }
-        release(s);
-        DFT<H, DIR>::run(v);
-        float2* dst = og + (long long)d.idx * N * HC;  // plane z = idx
-        const unsigned long long keep = rowk::policy_evict_last();
-        float2* scr = scratch + g * N;
-        if (c != 0) {
-#pragma unroll
-          for (int kk = 0; kk < H; ++kk) st_keep(dst + (2 * kk + h) * HC + c, v[kk], keep);
+          release(s);
+        } else if (pass == 2) {
+          // z: column c of the rows (z, ky = idx)
+          load_dif_rows<N, DIR, P>(t, off + 8 * c, h, v);
+          release(s);
         } else {
-#pragma unroll
-          for (int kk = 0; kk < H; ++kk) scr[2 * kk + h] = v[kk];
+          // Nyquist column: pencil p = c of the workspace tile (dense rows z)
+          load_dif_rows<N, DIR, H * 8>(t, 8 * c, h, v);
+          release(s);
         }
-        if (!group_sync()) break;
-        {
+      } else {
+        if (pass == 0) {
+          // z: column c of the rows (kz, ky = idx)
+          load_dif_rows<N, DIR, P>(t, off + 8 * c, h, v);
+          release(s);
+        } else if (pass == 1) {
+          // y: column c of plane z = idx (dense rows of H complex)
+          load_dif_rows<N, DIR, H * 8>(t, 8 * c, h, v);
+          if (!group_sync()) {  // every column read before any row is written
+            fail = true;
+            break;
+          }
+        } else {
+          // x: row y = gt (half spectrum, X[0] + i X[h] in column 0)
+          const unsigned char* row = t + gt * P;
+#pragma unroll
+          for (int j = 0; j < H / 2; ++j) {
+            const float4 q = *reinterpret_cast<const float4*>(row + 16 * j);
+            v[2 * j] = make_float2(q.x, q.y);
+            v[2 * j + 1] = make_float2(q.z, q.w);
+          }
+          real_merge<H, DIR>(v);
+        }
+      }
+      DFT<H, DIR>::run(v);
+      // --------------------------------------------------------- out
+      if constexpr (DIR < 0) {
+        float2* og = const_cast<float2*>(a.out) + gg * N * N * HC;  // half spectra of grid g
+        if (pass == 0) {
+          real_split<H, DIR>(v);
+#pragma unroll
+          for (int j = 0; j < H / 2; ++j)
+            *reinterpret_cast<float4*>(t + swz<N>(gt, j)) =
+                make_float4(v[2 * j].x, v[2 * j].y, v[2 * j + 1].x, v[2 * j + 1].y);
+          if (!group_sync()) {
+            fail = true;
+            break;
+          }
+          pass = 1;
+          continue;
+        }
+        if (pass == 1) {
+          // outputs ky = 2k + h straight to out (kept in L2); column 0
+          // through the group's scratch
+          float2* dst = og + (long long)d.idx * N * HC;  // plane z = idx
+          const unsigned long long keep = rowk::policy_evict_last();
+          float2* scr = scratch + g * N;
+          if (c != 0) {
+#pragma unroll
+            for (int kk = 0; kk < H; ++kk) st_keep(dst + (2 * kk + h) * HC + c, v[kk], keep);
+          } else {
+#pragma unroll
+            for (int kk = 0; kk < H; ++kk) scr[2 * kk + h] = v[kk];
+          }
+          if (!group_sync()) {
+            fail = true;
+            break;
+          }
           // column 0 (C = Y0 + i Yh, each Hermitian), separated by thread
           // ky = gt: Y0 to column 0, Yh (real at ky = 0 and h) to the
           // Nyquist workspace
@@ -542,22 +614,14 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
           if (gt == 0) st_keep_f(&nq[0].x, B.x, keep);
           else if (gt == H) st_keep_f(&nq[0].y, B.x, keep);
           else if (gt < H) st_keep(nq + gt, B, keep);
-        }
-      } else if (d.idx < N) {
-        // z: column c of the rows (z, ky = idx), outputs kz = 2k + h
-        load_dif_rows<N, DIR, P>(t, 8 * (c + (d.idx & 1)), h, v);
-        release(s);
-        DFT<H, DIR>::run(v);
-        float2* dst = og + (long long)d.idx * HC + c;
+        } else if (pass == 2) {
+          // outputs kz = 2k + h, scaled
+          float2* dst = og + (long long)d.idx * HC + c;
 #pragma unroll
-        for (int kk = 0; kk < H; ++kk)
-          st_stream(dst + (long long)(2 * kk + h) * N * HC, cscale(v[kk], sc));
-      } else {
-        // Nyquist column: pencil p = c of the workspace tile (dense rows z)
-        load_dif_rows<N, DIR, H * 8>(t, 8 * c, h, v);
-        release(s);
-        DFT<H, DIR>::run(v);
-        if (c != 0) {
+          for (int kk = 0; kk < H; ++kk)
+            st_stream(dst + (long long)(2 * kk + h) * N * HC, cscale(v[kk], sc));
+        } else if (c != 0) {
+          // Nyquist pencil ky = c and its mirror -ky (conjugate, at -kz)
 #pragma unroll
           for (int kk = 0; kk < H; ++kk) {
             const int kz = 2 * kk + h, mz = (N - kz) % N;
@@ -566,6 +630,7 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
             st_stream(og + ((long long)mz * N + (N - c)) * HC + H, conjf2(o));
           }
         } else {
+          // the packed pencil: ky = 0 and ky = h
           auto put = [&](int kz, float2 A, float2 B) {
             st_stream(og + ((long long)kz * N) * HC + H, cscale(A, sc));
             st_stream(og + ((long long)kz * N + H) * HC + H, cscale(B, sc));
@@ -573,65 +638,43 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
           if (h == 0) herm_unpack<H, 0>(v, put);
           else herm_unpack<H, 1>(v, put);
         }
-      }
-    } else {
-      if (d.phase == 0) {
-        // rows (kz, ky = idx) of the input: columns 0 and H -> their
-        // Hermitian parts, packed into column 0 (thread gt = kz)
-        const int off = 8 * (d.idx & 1);
-        {
-          unsigned char* rk = t + gt * P + off;
-          const float2 T0 = *reinterpret_cast<const float2*>(rk);
-          const float2 Th = *reinterpret_cast<const float2*>(rk + 8 * H);
-          // mirror row (-kz, -ky): its columns 0 and h from the mirror boxes
-          const int mz = (N - gt) % N, mo = 16 * mz + 8 * (((N - d.idx) % N) & 1);
-          const float2 M0 = *reinterpret_cast<const float2*>(t + K::MAIN + mo);
-          const float2 Mh = *reinterpret_cast<const float2*>(t + K::MAIN + N * 16 + mo);
-          const float2 A = make_float2(0.5f * (T0.x + M0.x), 0.5f * (T0.y - M0.y));
-          const float2 B = make_float2(0.5f * (Th.x + Mh.x), 0.5f * (Th.y - Mh.y));
-          *reinterpret_cast<float2*>(rk) = make_float2(A.x - B.y, A.y + B.x);  // A + i B
-        }
-        if (!group_sync()) break;
-        // z: column c, outputs z = 2k + h, into the intermediate (kept in L2)
-        load_dif_rows<N, DIR, P>(t, off + 8 * c, h, v);
-        release(s);
-        DFT<H, DIR>::run(v);
-        float2* dst = const_cast<float2*>(a.out) + gg * N * N * H + (long long)d.idx * H + c;
-        const unsigned long long keep = rowk::policy_evict_last();
-#pragma unroll
-        for (int kk = 0; kk < H; ++kk) st_keep(dst + (long long)(2 * kk + h) * N * H, v[kk], keep);
       } else {
-        // y: column c of plane z = idx (dense rows of H complex), back into
-        // the tile as row y = 2k + h (padded rows)
-        load_dif_rows<N, DIR, H * 8>(t, 8 * c, h, v);
-        if (!group_sync()) break;  // every column read before any row is written
-        DFT<H, DIR>::run(v);
+        if (pass == 0) {
+          // outputs z = 2k + h into the intermediate (kept in L2)
+          float2* dst = const_cast<float2*>(a.out) + gg * N * N * H + (long long)d.idx * H + c;
+          const unsigned long long keep = rowk::policy_evict_last();
 #pragma unroll
-        for (int kk = 0; kk < H; ++kk)
-          *reinterpret_cast<float2*>(t + (2 * kk + h) * P + 8 * c) = v[kk];
-        if (!group_sync()) break;
-        // x: row y = gt -> n reals, scaled, back to the row and out
-        unsigned char* row = t + gt * P;
+          for (int kk = 0; kk < H; ++kk)
+            st_keep(dst + (long long)(2 * kk + h) * N * H, v[kk], keep);
+        } else if (pass == 1) {
+          // back into the tile as row y = 2k + h (padded rows)
 #pragma unroll
-        for (int j = 0; j < H / 2; ++j) {
-          const float4 q = *reinterpret_cast<const float4*>(row + 16 * j);
-          v[2 * j] = make_float2(q.x, q.y);
-          v[2 * j + 1] = make_float2(q.z, q.w);
+          for (int kk = 0; kk < H; ++kk)
+            *reinterpret_cast<float2*>(t + (2 * kk + h) * P + 8 * c) = v[kk];
+          if (!group_sync()) {
+            fail = true;
+            break;
+          }
+          pass = 2;
+          continue;
+        } else {
+          // n reals of row y = gt, scaled, back to the row and out
+          unsigned char* row = t + gt * P;
+#pragma unroll
+          for (int j = 0; j < H / 2; ++j)
+            *reinterpret_cast<float4*>(row + 16 * j) = make_float4(
+                sc * v[2 * j].x, sc * v[2 * j].y, sc * v[2 * j + 1].x, sc * v[2 * j + 1].y);
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          float* og = reinterpret_cast<float*>(const_cast<float2*>(a.out)) + gg * N * N * N;
+          bulk_store_row(og + ((long long)d.idx * N + gt) * N, saddr(row), N * 4);
+          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+          asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+          release(s);
         }
-        real_merge<H, DIR>(v);
-        DFT<H, DIR>::run(v);
-#pragma unroll
-        for (int j = 0; j < H / 2; ++j)
-          *reinterpret_cast<float4*>(row + 16 * j) =
-              make_float4(sc * v[2 * j].x, sc * v[2 * j].y, sc * v[2 * j + 1].x, sc * v[2 * j + 1].y);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        float* og = reinterpret_cast<float*>(const_cast<float2*>(a.out)) + gg * N * N * N;
-        bulk_store_row(og + ((long long)d.idx * N + gt) * N, saddr(row), N * 4);
-        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-        release(s);
       }
+      break;
     }
+    if (fail) break;
     __syncwarp();
     if (lane == 0) mbar_arrive(&done[k % K::DQ]);  // the stores are issued, for the publisher
   }
