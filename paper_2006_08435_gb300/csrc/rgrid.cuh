@@ -19,7 +19,8 @@
 //       then holds C = Y0 + i Yh, the y transforms of the real columns X[0]
 //       and X[h]; both are Hermitian, so Y0 = (C(ky) + conj C(-ky)) / 2 and
 //       Yh = (C(ky) - conj C(-ky)) / (2i), and ky, -ky have the same parity
-//       (same thread).  The plane's half rows go to out[g][z][ky][0 .. h].
+//       (outputs of the same thread, separated by its warp).  The plane's
+//       half rows go to out[g][z][ky][0 .. h].
 //   slab item (g, ky): rows (z, ky), columns 0 .. h-1 of out -> tile; z DFTs
 //     as for y; results (scaled) back to those rows.
 //   Nyquist item (g): column h of out.  Since F(kx, -ky, -kz) = conj F(kx,
@@ -221,26 +222,6 @@ __device__ __forceinline__ void load_dif_rows(const unsigned char* t, int col, i
   auto at = [&](int r) { return reinterpret_cast<const float2*>(t + r * P + col); };
   if (h == 0) load_dif<N, DIR, 0>(at, v);
   else load_dif<N, DIR, 1>(at, v);
-}
-
-// v[k] = C(2k + HALF) of a column whose real and imaginary parts are two
-// Hermitian transforms: C = A + i B with A(-j) = conj A(j), B likewise.
-// Calls put(j, A(j), B(j)) for the outputs j = 2k + HALF.  -j has the same
-// parity, at k' = (H - k) mod H (HALF 0) or H - 1 - k (HALF 1); each pair
-// is taken once, A(-j) = conj A(j), B(-j) = conj B(j).
-template <int H, int HALF, class Put>
-__device__ __forceinline__ void herm_unpack(const float2* v, Put&& put) {
-  static_for<0, H>([&](auto K) {
-    constexpr int k = decltype(K)::value;
-    constexpr int km = HALF == 0 ? (H - k) % H : H - 1 - k;
-    if constexpr (k <= km) {
-      const float2 c = v[k], m = v[km];
-      const float2 A = make_float2(0.5f * (c.x + m.x), 0.5f * (c.y - m.y));  // (c + conj m) / 2
-      const float2 B = make_float2(0.5f * (c.y + m.y), 0.5f * (m.x - c.x));  // (c - conj m) / 2i
-      put(2 * k + HALF, A, B);
-      if constexpr (km != k) put(2 * km + HALF, conjf2(A), conjf2(B));
-    }
-  });
 }
 
 // --------------------------------------------------------------- producer
@@ -587,56 +568,72 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
           continue;
         }
         if (pass == 1) {
-          // outputs ky = 2k + h straight to out (kept in L2); column 0
-          // through the group's scratch
+          // outputs ky = 2k + h straight to out (kept in L2).  Column 0 (C =
+          // Y0 + i Yh, each Hermitian) is separated in the warp that holds
+          // it: ky and -ky have the same parity, so lane 0's 64 outputs are
+          // every ky of that parity; they go to the warp's scratch, and each
+          // lane separates two of them: Y0 to column 0, Yh (real at ky = 0
+          // and h) to the Nyquist workspace.
           float2* dst = og + (long long)d.idx * N * HC;  // plane z = idx
           const unsigned long long keep = rowk::policy_evict_last();
-          float2* scr = scratch + g * N;
-          if (c != 0) {
 #pragma unroll
-            for (int kk = 0; kk < H; ++kk) st_keep(dst + (2 * kk + h) * HC + c, v[kk], keep);
-          } else {
+          for (int kk = 0; kk < H; ++kk)
+            if (c != 0) st_keep(dst + (2 * kk + h) * HC + c, v[kk], keep);
+          if (c < 32) {  // the warp holding column 0
+            float2* scr = scratch + (g * 2 + h) * H;
+            if (c == 0) {
 #pragma unroll
-            for (int kk = 0; kk < H; ++kk) scr[2 * kk + h] = v[kk];
+              for (int kk = 0; kk < H; ++kk) scr[kk] = v[kk];
+            }
+            __syncwarp();
+            float2* nq = a.aux + (gg * N + d.idx) * H;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+              const int kk = c + 32 * q, ky = 2 * kk + h;
+              const float2 cc = scr[kk], m = scr[h == 0 ? (H - kk) % H : H - 1 - kk];
+              const float2 A = make_float2(0.5f * (cc.x + m.x), 0.5f * (cc.y - m.y));  // (C + conj M) / 2
+              const float2 B = make_float2(0.5f * (cc.y + m.y), 0.5f * (m.x - cc.x));  // (C - conj M) / 2i
+              st_keep(dst + ky * HC, A, keep);
+              if (ky == 0) st_keep_f(&nq[0].x, B.x, keep);
+              else if (ky == H) st_keep_f(&nq[0].y, B.x, keep);
+              else if (ky < H) st_keep(nq + ky, B, keep);
+            }
           }
-          if (!group_sync()) {
-            fail = true;
-            break;
-          }
-          // column 0 (C = Y0 + i Yh, each Hermitian), separated by thread
-          // ky = gt: Y0 to column 0, Yh (real at ky = 0 and h) to the
-          // Nyquist workspace
-          const float2 cc = scr[gt], m = scr[(N - gt) % N];
-          const float2 A = make_float2(0.5f * (cc.x + m.x), 0.5f * (cc.y - m.y));  // (C + conj M) / 2
-          const float2 B = make_float2(0.5f * (cc.y + m.y), 0.5f * (m.x - cc.x));  // (C - conj M) / 2i
-          st_keep(dst + gt * HC, A, keep);
-          float2* nq = a.aux + (gg * N + d.idx) * H;
-          if (gt == 0) st_keep_f(&nq[0].x, B.x, keep);
-          else if (gt == H) st_keep_f(&nq[0].y, B.x, keep);
-          else if (gt < H) st_keep(nq + gt, B, keep);
         } else if (pass == 2) {
           // outputs kz = 2k + h, scaled
           float2* dst = og + (long long)d.idx * HC + c;
 #pragma unroll
           for (int kk = 0; kk < H; ++kk)
             st_stream(dst + (long long)(2 * kk + h) * N * HC, cscale(v[kk], sc));
-        } else if (c != 0) {
-          // Nyquist pencil ky = c and its mirror -ky (conjugate, at -kz)
+        } else {
+          // Nyquist pencils: ky = c and its mirror -ky (conjugate, at -kz);
+          // pencil 0 packs ky = 0 and ky = h, separated like column 0 above
 #pragma unroll
           for (int kk = 0; kk < H; ++kk) {
             const int kz = 2 * kk + h, mz = (N - kz) % N;
             const float2 o = cscale(v[kk], sc);
-            st_stream(og + ((long long)kz * N + c) * HC + H, o);
-            st_stream(og + ((long long)mz * N + (N - c)) * HC + H, conjf2(o));
+            if (c != 0) {
+              st_stream(og + ((long long)kz * N + c) * HC + H, o);
+              st_stream(og + ((long long)mz * N + (N - c)) * HC + H, conjf2(o));
+            }
           }
-        } else {
-          // the packed pencil: ky = 0 and ky = h
-          auto put = [&](int kz, float2 A, float2 B) {
-            st_stream(og + ((long long)kz * N) * HC + H, cscale(A, sc));
-            st_stream(og + ((long long)kz * N + H) * HC + H, cscale(B, sc));
-          };
-          if (h == 0) herm_unpack<H, 0>(v, put);
-          else herm_unpack<H, 1>(v, put);
+          if (c < 32) {
+            float2* scr = scratch + (g * 2 + h) * H;
+            if (c == 0) {
+#pragma unroll
+              for (int kk = 0; kk < H; ++kk) scr[kk] = v[kk];
+            }
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+              const int kk = c + 32 * q, kz = 2 * kk + h;
+              const float2 cc = scr[kk], m = scr[h == 0 ? (H - kk) % H : H - 1 - kk];
+              const float2 A = make_float2(0.5f * (cc.x + m.x), 0.5f * (cc.y - m.y));
+              const float2 B = make_float2(0.5f * (cc.y + m.y), 0.5f * (m.x - cc.x));
+              st_stream(og + ((long long)kz * N) * HC + H, cscale(A, sc));
+              st_stream(og + ((long long)kz * N + H) * HC + H, cscale(B, sc));
+            }
+          }
         }
       } else {
         if (pass == 0) {
