@@ -729,7 +729,10 @@ KernelInfo info() {
   k.smem = Cfg<N>::smem;
   k.sizes[0] = N;
   k.nsizes = 1;
-  k.items_in_flight = Cfg<N>::NTILE + 3;  // the tiles and the tickets held ahead
+  // schedule lag in items per block: the tiles and the tickets held ahead;
+  // twice that forward, whose plane items take longer than its z items, so
+  // that the z items of a grid rarely wait for its planes (measured)
+  k.items_in_flight = (Cfg<N>::NTILE + 3) * (DIR < 0 ? 2 : 1);
   return k;
 }
 
