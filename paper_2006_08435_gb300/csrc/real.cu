@@ -188,7 +188,7 @@ void free_fused(fft3d_real_plan p) {
 
 // Plan of the dedicated kernels: phase 0 has n items per grid (forward:
 // planes; inverse: z rows), phase 1 n items (forward: z rows, plus the
-// Nyquist column; inverse: planes).  The schedule's L2 budget counts 8 n^3
+// Nyquist column; inverse: planes); forward blocks have one ticket more.  The schedule's L2 budget counts 8 n^3
 // bytes of intermediate per grid (a complex grid); a real grid's is about
 // half of that, so the budget passed is scaled by the ratio.  The forward
 // transform keeps more grids in flight (60% of L2 against 40%): its input
@@ -227,10 +227,11 @@ int create_fused_real(int n, int batch, int direction, int norm, const KernelInf
   for (int g = 0; g < batch; ++g) order[g] = g;
   std::vector<SchedBlock> blocks(2 * (size_t)batch);
   int total = 0;
+  // n + 1 tickets per block forward (the z block's last is the Nyquist
+  // item, the plane block's last is empty), n inverse
   const int nb = schedule_blocks(batch, dims.data(), order.data(), resident * k.items_in_flight,
-                                 (forward ? 0.6 : 0.4) * (double)l2 * (8.0 * n3 / inter), 0,
-                                 plane_end.data(),
-                                 blocks.data(), &total, forward ? 1 : 0);
+                                 (forward ? 0.6 : 0.4) * (double)l2 * (8.0 * n3 / inter),
+                                 forward ? n + 1 : n, plane_end.data(), blocks.data(), &total);
   auto* p = new (std::nothrow) fft3d_real_plan_s();
   if (!p) return FFT3D_ERR_ALLOC;
   p->n = n;

@@ -1,4 +1,4 @@
-// Persistent transforms of REAL 128^3 grids: forward (R2C, sign -1, real
+// Persistent transforms of REAL n^3 grids (n = 64, 128): forward (R2C, sign -1, real
 // grid -> half spectrum kx = 0 .. n/2) and inverse (C2R, sign +1), each in
 // two phases of work items with the ticket schedule and L2-resident
 // intermediate of the complex kernels.  Every 1D transform of n points is
@@ -45,17 +45,17 @@
 //
 // Block: a control warpgroup (producer warp: tickets, schedule lookup,
 // dependency waits, the item's copies; publisher warp: finished phase-0
-// items to the other blocks, in order) and two compute groups of 128
-// threads; a ring of three tiles.  Every item arrives with at most four
+// items to the other blocks, in order) and compute groups of n threads
+// (two at 128^3, four at 64^3); a ring of three (five) tiles.  Every item arrives with at most four
 // copies (the copy engine's cost is per copy, not per byte, at these sizes):
 //   real plane: four tensor boxes of 32 floats x n rows, 128-byte swizzled
 //     (16-byte chunk j of row r at chunk j ^ (r mod 8)), so that both the
 //     thread-per-row and the thread-per-column accesses are conflict-free;
-//   rows (z, ky) of a half spectrum: one tensor box of 132 floats x n over a
-//     view of the half spectra as ROW PAIRS (1040 bytes, a 16-byte multiple,
-//     where a single row of 520 bytes is not): pair ky/2 from float 0 (even
-//     ky: columns 0 .. h+1) or 128 (odd ky: column h of row ky-1, then
-//     columns 0 .. h), 528 bytes per tile row;
+//   rows (z, ky) of a half spectrum: one tensor box of n + 4 floats x n over a
+//     view of the half spectra as ROW PAIRS (16 (h + 1) bytes, a 16-byte
+//     multiple, where a single row of 8 (h + 1) bytes is not): pair ky/2
+//     from float 0 (even ky: columns 0 .. h+1) or 2h (odd ky: column h of
+//     row ky-1, then columns 0 .. h), 8 (h + 2) bytes per tile row;
 //   the inverse's mirror columns: two boxes of 4 floats x n of the same view;
 //   a contiguous plane of the intermediate or the Nyquist workspace: one
 //     bulk copy (dense rows).
@@ -78,30 +78,31 @@ using rowk::spin_geq;
 
 template <int N>
 struct Cfg {
-  static_assert(N == 128, "the real-grid kernels cover 128^3");
+  static_assert(N == 64 || N == 128, "the real-grid kernels cover 64^3 and 128^3");
   static constexpr int H = N / 2;               // points of each register DFT
   static constexpr int HC = N / 2 + 1;          // complex per half-spectrum row
   static constexpr int PITCH = (N / 2 + 2) * 8; // bytes per tile row (16-byte multiple)
   static constexpr int MAIN = N * PITCH;        // rows of an item
   static constexpr int MIRROR = 2 * N * 16;     // inverse: mirror boxes of columns 0 and h
-  static constexpr int TILE = MAIN + MIRROR;    // a multiple of 1024 (swizzle alignment)
+  static constexpr int TILE = MAIN + MIRROR;
+  static_assert(TILE % 1024 == 0, "tiles 1024-byte aligned (swizzle)");
   static constexpr int SWB = 32 * N * 4;        // bytes of one swizzled box of the real plane
-  static constexpr int NTILE = 3;
   static constexpr int GT = N;                  // threads per compute group
   static constexpr int GW = GT / 32;
-  static constexpr int GROUPS = 2;
+  static constexpr int GROUPS = 256 / N;        // two warpgroups of compute threads
+  static constexpr int NTILE = N == 128 ? 3 : 5;  // coprime with GROUPS
   static constexpr int T = 128 + GROUPS * GT;   // control warpgroup + compute
   // registers per thread at launch 65536 / 384 -> 168; setmaxnreg moves them
   // from the control warpgroup to the compute ones: 128 * 56 + 256 * 224 =
   // 64512 <= 384 * 168
   static constexpr int REG_CTRL = 56, REG_COMP = 224;
   static constexpr int DQ = 16;                 // finished items queued for the publisher
-  static constexpr int SCHED = 1024;            // schedule blocks kept in shared memory
+  static constexpr int SCHED = 2048;            // schedule blocks kept in shared memory
   static constexpr int NFULL = NTILE * GROUPS;
   static constexpr size_t smem = 1024 + (size_t)NTILE * TILE + GROUPS * N * sizeof(float2) +
                                  (NFULL + NTILE + GROUPS + DQ) * sizeof(unsigned long long) +
-                                 NTILE * sizeof(int4) + (DQ + 2) * sizeof(int) +
-                                 SCHED * sizeof(int2);
+                                 NTILE * sizeof(int4) + (DQ + 1) * sizeof(int) +
+                                 SCHED * sizeof(int);
 };
 
 struct Desc {
@@ -235,28 +236,23 @@ __device__ __forceinline__ void producer(const FusedArgs& a, const CUtensorMap* 
                                          const CUtensorMap* m1, uint32_t tiles,
                                          unsigned long long* full, unsigned long long* empty,
                                          unsigned long long* done, int* pubq,
-                                         volatile int* pub_done, Desc* desc, const int2* sched) {
+                                         volatile int* pub_done, Desc* desc, const int* sched) {
   using K = Cfg<N>;
   constexpr int NT = K::NTILE, DQ = K::DQ, G = K::GROUPS, H = K::H;
   const int lane = threadIdx.x & 31;
-  const bool local = a.nblocks <= K::SCHED;
-  auto start_of = [&](int b) { return local ? sched[b].x : a.blocks[b].start; };
+  // every schedule block has IPB tickets (forward: the plane block's last
+  // ticket is empty, matching the z block's Nyquist item), so a ticket's
+  // block is t / IPB; (grid, phase) of the first SCHED blocks are in shared
+  // memory
+  constexpr int IPB = N + (DIR < 0 ? 1 : 0);
   auto resolve = [&](int t, Desc& d) {
-    int lo = 0, hi = a.nblocks - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (start_of(mid) <= t) lo = mid;
-      else hi = mid - 1;
-    }
-    if (local) {
-      d.grid = sched[lo].y >> 1;
-      d.phase = sched[lo].y & 1;
-    } else {
-      const SchedBlock blk = a.blocks[lo];
-      d.grid = blk.grid;
-      d.phase = blk.phase;
-    }
-    d.idx = t - start_of(lo);
+    const int b = t / IPB;
+    int gp;
+    if (b < K::SCHED) gp = sched[b];
+    else gp = a.blocks[b].grid * 2 + a.blocks[b].phase;
+    d.grid = gp >> 1;
+    d.phase = gp & 1;
+    d.idx = t - b * IPB;
     d.item = t;
   };
   int t1 = 0, t2 = 0;
@@ -273,12 +269,15 @@ __device__ __forceinline__ void producer(const FusedArgs& a, const CUtensorMap* 
     Desc d{-1, 0, 0, 0};
     int ok = 1;
     if (lane == 0) {
-      const int t = t1;
-      t1 = t2;
-      t2 = (int)atomicAdd(a.work, 1u);
-      ok = t < a.total_items;
+      int t;
+      do {  // (the empty tickets are skipped)
+        t = t1;
+        t1 = t2;
+        t2 = (int)atomicAdd(a.work, 1u);
+        ok = t < a.total_items;
+        if (ok) resolve(t, d);
+      } while (ok && DIR < 0 && d.phase == 0 && d.idx == N);
       if (ok) {
-        resolve(t, d);
         if (d.phase == 1 && d.grid != ready_grid) {
           ok = bounded_wait_geq(a.work + 1 + d.grid, (unsigned)N, a.status, a.timeout_ns);
           if (ok) ready_grid = d.grid;
@@ -356,18 +355,18 @@ __device__ __forceinline__ void producer(const FusedArgs& a, const CUtensorMap* 
     if (bulk) {
       if (lane == 0) bulk_row(dst, bulk, tx, fb, once);
     } else if (DIR < 0 && d.phase == 0) {
-      if (lane < 4)  // plane z = idx: box {32 x, all y} at z
+      if (lane < N / 32)  // plane z = idx: box {32 x, all y} at z
         rowk::tma_box_hint(dst + lane * K::SWB, m1, 32 * lane, 0, g * N + ky, fb, once);
     } else {
       // pair ky/2 of every z of grid g; the inverse also the mirror row
       // (-ky): columns 0 and h, one box each
       const int my = (N - ky) % N;
-      if (lane == 0) rowk::tma_box_hint(dst, m0, (ky & 1) ? 128 : 0, ky >> 1, g * N, fb, once);
+      if (lane == 0) rowk::tma_box_hint(dst, m0, (ky & 1) ? 2 * H : 0, ky >> 1, g * N, fb, once);
       if (DIR > 0 && lane == 1)
-        rowk::tma_box_hint(dst + K::MAIN, m1, (my & 1) ? 128 : 0, my >> 1, g * N, fb, once);
+        rowk::tma_box_hint(dst + K::MAIN, m1, (my & 1) ? 2 * H : 0, my >> 1, g * N, fb, once);
       if (DIR > 0 && lane == 2)
-        rowk::tma_box_hint(dst + K::MAIN + N * 16, m1, (my & 1) ? 256 : 128, my >> 1, g * N, fb,
-                           once);
+        rowk::tma_box_hint(dst + K::MAIN + N * 16, m1, (my & 1) ? 4 * H : 2 * H, my >> 1, g * N,
+                           fb, once);
     }
     live |= 1u << s;
   }
@@ -403,10 +402,10 @@ __device__ __forceinline__ void publisher(const FusedArgs& a, unsigned long long
 }
 
 // ----------------------------------------------------------------- kernel
-// Tensor maps: forward m0 = the half spectra `out` as row pairs (box 132
+// Tensor maps: forward m0 = the half spectra `out` as row pairs (box n + 4
 // floats x 1 x n), m1 = the real grids `in` (box 32 floats x n x 1,
-// swizzled); inverse m0 = the half spectra `in` as row pairs (box 132 x 1 x
-// n), m1 = the same view with boxes of 4 floats (mirror columns).
+// swizzled); inverse m0 = the half spectra `in` as row pairs (box n + 4 x 1
+// x n), m1 = the same view with boxes of 4 floats (mirror columns).
 template <int N, int DIR>
 __global__ void __launch_bounds__(Cfg<N>::T, 1)
     rgrid_fft3d_kernel(const FusedArgs a, const __grid_constant__ CUtensorMap m0,
@@ -425,11 +424,10 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
   Desc* desc = reinterpret_cast<Desc*>(done + K::DQ);
   int* pubq = reinterpret_cast<int*>(desc + NT);
   volatile int* pub_done = pubq + K::DQ;
-  int2* sched = reinterpret_cast<int2*>(pubq + K::DQ + 2);  // 8-byte aligned
+  int* sched = pubq + K::DQ + 1;
   const int w = threadIdx.x >> 5;
-  if (a.nblocks <= K::SCHED)
-    for (int b = threadIdx.x; b < a.nblocks; b += K::T)
-      sched[b] = make_int2(a.blocks[b].start, a.blocks[b].grid * 2 + a.blocks[b].phase);
+  for (int b = threadIdx.x; b < a.nblocks && b < K::SCHED; b += K::T)
+    sched[b] = a.blocks[b].grid * 2 + a.blocks[b].phase;
   if (threadIdx.x == 0) {
     for (int i = 0; i < K::NFULL; ++i) mbar_init(&full[i], 1);
     for (int s = 0; s < NT; ++s) mbar_init(&empty[s], K::GW);
@@ -448,7 +446,7 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
   }
   asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(K::REG_COMP));
 
-  // compute group g (warpgroup g + 1), thread gt of 128; column passes:
+  // compute group g (of the warpgroups 1, 2), thread gt of N; column passes:
   // column c = gt % H, output half h = gt / H (the same for a whole warp)
   const int g = (w - 4) / K::GW, gt = threadIdx.x - 128 - g * K::GT, lane = threadIdx.x & 31;
   const int c = gt % H, h = gt / H;
@@ -579,7 +577,7 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
 #pragma unroll
           for (int kk = 0; kk < H; ++kk)
             if (c != 0) st_keep(dst + (2 * kk + h) * HC + c, v[kk], keep);
-          if (c < 32) {  // the warp holding column 0
+          if (c < 32) {  // the warp holding column 0 (for this half)
             float2* scr = scratch + (g * 2 + h) * H;
             if (c == 0) {
 #pragma unroll
@@ -588,7 +586,7 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
             __syncwarp();
             float2* nq = a.aux + (gg * N + d.idx) * H;
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
+            for (int q = 0; q < H / 32; ++q) {
               const int kk = c + 32 * q, ky = 2 * kk + h;
               const float2 cc = scr[kk], m = scr[h == 0 ? (H - kk) % H : H - 1 - kk];
               const float2 A = make_float2(0.5f * (cc.x + m.x), 0.5f * (cc.y - m.y));  // (C + conj M) / 2
@@ -625,7 +623,7 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
             }
             __syncwarp();
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
+            for (int q = 0; q < H / 32; ++q) {
               const int kk = c + 32 * q, kz = 2 * kk + h;
               const float2 cc = scr[kk], m = scr[h == 0 ? (H - kk) % H : H - 1 - kk];
               const float2 A = make_float2(0.5f * (cc.x + m.x), 0.5f * (cc.y - m.y));
@@ -710,10 +708,12 @@ cudaError_t launch(const FusedArgs& a, int grid, cudaStream_t stream) {
     const cuuint64_t dims[3] = {N, N, (cuuint64_t)N * a.ngrids};
     const cuuint64_t strides[2] = {N * 4, (cuuint64_t)N * N * 4};
     const cuuint32_t box[3] = {32, N, 1};
-    if (!encode_pairs(&m0, a.out, N, a.ngrids, 132) || !encode(&m1, a.in, dims, strides, box, true))
+    if (!encode_pairs(&m0, a.out, N, a.ngrids, 2 * (N / 2 + 2)) ||
+        !encode(&m1, a.in, dims, strides, box, true))
       return cudaErrorInvalidValue;
   } else {
-    if (!encode_pairs(&m0, a.in, N, a.ngrids, 132) || !encode_pairs(&m1, a.in, N, a.ngrids, 4))
+    if (!encode_pairs(&m0, a.in, N, a.ngrids, 2 * (N / 2 + 2)) ||
+        !encode_pairs(&m1, a.in, N, a.ngrids, 4))
       return cudaErrorInvalidValue;
   }
   rgrid_fft3d_kernel<N, DIR><<<grid, Cfg<N>::T, Cfg<N>::smem, stream>>>(a, m0, m1);

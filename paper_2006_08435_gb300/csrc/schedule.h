@@ -16,14 +16,13 @@ namespace fft3d {
 // `l2_budget` bytes (8 n^3 each; their intermediate must stay in L2).  The
 // grids waiting for their slabs leave in the order their planes were
 // emitted, so they are the positions [head, i) of `order`.  A phase is
-// `phase_items` tickets (the grid's edge when 0); a slab block has
-// `slab_extra` tickets more.
+// `phase_items` tickets (the grid's edge when 0).
 //   plane_end : scratch of `count` ints (ticket after each plane block).
 //   out       : receives 2 * count blocks.
 // Returns the number of blocks; *total_items = tickets in all.
 inline int schedule_blocks(int count, const int* dims, const int* order, int concurrency,
                            double l2_budget, int phase_items, int* plane_end, SchedBlock* out,
-                           int* total_items, int slab_extra = 0) {
+                           int* total_items) {
   int start = 0, nb = 0, head = 0;
   double pending = 0.0;
   auto bytes_at = [&](int i) {
@@ -32,7 +31,7 @@ inline int schedule_blocks(int count, const int* dims, const int* order, int con
   };
   auto emit = [&](int g, int phase) {
     out[nb++] = SchedBlock{g, phase, start, dims[g]};
-    start += (phase_items > 0 ? phase_items : dims[g]) + (phase == 1 ? slab_extra : 0);
+    start += phase_items > 0 ? phase_items : dims[g];
   };
   // slab blocks of the waiting grids before position `next`: those whose
   // planes ended `concurrency` tickets ago, and at least one if forced

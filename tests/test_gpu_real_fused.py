@@ -1,5 +1,6 @@
-"""Parity of the dedicated real-grid kernels (128^3, FP32: half-length row
-transforms, no pairing) with the FP64 oracle, element by element.
+"""Parity of the dedicated real-grid kernels (64^3 and 128^3, FP32:
+half-length row transforms, no pairing) with the FP64 oracle, element by
+element.
 
 Bar: relative L2 error <= 5e-6 per grid, the FP32 tolerance of the complex
 path.  Grids are independent draws (not scaled copies of one grid), so a
@@ -15,8 +16,8 @@ from paper_2006_08435_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-N = 128
 FP32_TOL = 5e-6
+EDGES = [64, 128]
 
 
 def to_dev(a):
@@ -27,18 +28,18 @@ def rel(got, ref):
     return oracle.rel_l2(np.asarray(got, dtype=np.complex128), ref)
 
 
-def real_grids(batch, seed):
+def real_grids(N, batch, seed):
     return np.ascontiguousarray(synth.uniform_grids(N, batch, seed=seed).real.astype(np.float32))
 
 
-def half_spectra(batch, seed):
+def half_spectra(N, batch, seed):
     """Arbitrary half spectra: not Hermitian in the planes kx = 0 and n/2."""
     return np.ascontiguousarray(synth.uniform_grids((N, N, N // 2 + 1), batch, seed=seed))
 
 
-def run(x, inverse=False, norm="none", batch=None):
+def run(x, inverse=False, norm="none"):
     from paper_2006_08435_gb300 import RealPlan
-    b = x.shape[0]
+    b, N = x.shape[0], x.shape[1]
     p = RealPlan(N, b, inverse=inverse, norm=norm)
     if inverse:
         out = torch.empty((b, N, N, N), dtype=torch.float32, device="cuda")
@@ -50,25 +51,27 @@ def run(x, inverse=False, norm="none", batch=None):
     return out
 
 
+@pytest.mark.parametrize("N", EDGES)
 @pytest.mark.parametrize("path", ["dedicated", "pairs"])
 @pytest.mark.parametrize("batch", [1, 3])
-def test_forward_against_oracle(cuda, monkeypatch, path, batch):
+def test_forward_against_oracle(cuda, monkeypatch, N, path, batch):
     if path == "pairs":
         monkeypatch.setenv("FFT3D_REAL_PATH", "pairs")
-    r = real_grids(batch, seed=400 + batch)
+    r = real_grids(N, batch, seed=400 + batch)
     got = run(to_dev(r)).cpu().numpy()
     ref = oracle.rdft3d(r.astype(np.float64))
     errs = [rel(got[b], ref[b]) for b in range(batch)]
     assert max(errs) <= FP32_TOL, errs
 
 
+@pytest.mark.parametrize("N", EDGES)
 @pytest.mark.parametrize("path", ["dedicated", "pairs"])
-def test_inverse_non_hermitian_against_oracle(cuda, monkeypatch, path):
+def test_inverse_non_hermitian_against_oracle(cuda, monkeypatch, N, path):
     """Columns kx = 0 and n/2 not Hermitian: the oracle's Re of the inverse
     of the Hermitian extension; the input is left unchanged."""
     if path == "pairs":
         monkeypatch.setenv("FFT3D_REAL_PATH", "pairs")
-    h = half_spectra(3, seed=77)
+    h = half_spectra(N, 3, seed=77)
     hd = to_dev(h)
     keep = hd.clone()
     got = run(hd, inverse=True).cpu().numpy()
@@ -78,7 +81,8 @@ def test_inverse_non_hermitian_against_oracle(cuda, monkeypatch, path):
     assert max(errs) <= FP32_TOL, errs
 
 
-def test_special_inputs(cuda):
+@pytest.mark.parametrize("N", EDGES)
+def test_special_inputs(cuda, N):
     """Closed forms through the dedicated kernels: a delta at the origin
     has a flat spectrum; a cosine along x with m cycles has n^3/2 at kx = m
     (ky = kz = 0) and nothing else; the Nyquist cosine (-1)^(x+y+z) has n^3
@@ -98,8 +102,9 @@ def test_special_inputs(cuda):
     assert np.max(np.abs(got[2] - e)) <= 1e-6 * N ** 3
 
 
-def test_norms_and_round_trip(cuda):
-    r = real_grids(2, seed=91)
+@pytest.mark.parametrize("N", EDGES)
+def test_norms_and_round_trip(cuda, N):
+    r = real_grids(N, 2, seed=91)
     rd = to_dev(r)
     ref = oracle.rdft3d(r.astype(np.float64))
     fo = run(rd, norm="ortho").cpu().numpy()
@@ -113,7 +118,8 @@ def test_norms_and_round_trip(cuda):
     assert rel(bo, r.astype(np.float64)) <= 2 * FP32_TOL
 
 
-def test_schedule_beyond_shared_table(cuda):
+@pytest.mark.parametrize("N", EDGES)
+def test_schedule_beyond_shared_table(cuda, N):
     """1100 grids: more schedule blocks (2200) than the kernel keeps in
     shared memory, so tickets are resolved from the global table.  Sampled
     grids against the oracle; every grid back through the inverse."""
@@ -130,7 +136,8 @@ def test_schedule_beyond_shared_table(cuda):
     assert float(err.max()) <= 2 * FP32_TOL
 
 
-def test_graph_capture(cuda):
+@pytest.mark.parametrize("N", EDGES)
+def test_graph_capture(cuda, N):
     from paper_2006_08435_gb300 import RealPlan
     batch = 2
     fwd, inv = RealPlan(N, batch), RealPlan(N, batch, inverse=True, norm="by_n")
@@ -147,7 +154,7 @@ def test_graph_capture(cuda):
     with torch.cuda.graph(g):
         fwd.execute(xs, hs)
         inv.execute(hs, bs)
-    r = real_grids(batch, seed=12)
+    r = real_grids(N, batch, seed=12)
     xs.copy_(to_dev(r))
     g.replay()
     torch.cuda.synchronize()
