@@ -15,7 +15,7 @@ transform = 16 * N^3 (one read and one write of the grid).
 The small workloads exist for profiler captures of the same kernels.  Beside
 the headline the line carries sub-objects: split_fp16 (the same batch in
 split FP16), tensor_core_kinds (split BF16, FP16, block floating point
-FP16, split FP8, FP8 on the same batch), real_r2c_fp32 (real grids), w64x256 (64^3 x 256 in FP32 and
+FP16, split FP8, FP8 on the same batch), real_r2c_fp32 / real_c2r_fp32 (real grids), w64x256 (64^3 x 256 in FP32 and
 split FP16), mixed_c2 (64 mixed-edge grids, forward + inverse in one CUDA
 graph), general_path (256^3 and a non-cubic batch on the per-axis passes)
 and batch1 (one grid per launch, L2 flushed, the paper's setting).
@@ -383,30 +383,35 @@ def run_ours(args, ws, rank, local):
             del pk
 
     # real grids (the real parts of the same batch): forward R2C to half
-    # spectra, two grids per complex transform (pack, transform, separate)
+    # spectra and inverse C2R back, each one kernel of the real-grid path
+    # after a counter reset (128^3 FP32)
     real = None
     if not args.no_real:
         from paper_2006_08435_gb300 import RealPlan
         xr = x.real.contiguous()
         yr = torch.empty((batch, n, n, n // 2 + 1), dtype=torch.complex64, device=dev)
-        rplan = RealPlan(n, batch)
-        for _ in range(3):
-            rplan.execute(xr, yr, stream)
-        barrier()
-        kr = max(1, args.steps // 8)
-        r0 = torch.cuda.Event(enable_timing=True)
-        r1 = torch.cuda.Event(enable_timing=True)
-        r0.record(stream)
-        for _ in range(kr):
-            rplan.execute(xr, yr, stream)
-        r1.record(stream)
-        barrier()
-        msr = max_over_ranks(r0.elapsed_time(r1) / kr, ws, dev)
-        assert rplan.device_status() == 0
-        real = {"value": whole_job_rate(ws, batch, 1, msr), "unit": "transforms/s", "steps": kr,
-                "ms_per_step": msr, "launches_per_step": 3,
-                "bytes_per_transform": 4 * n ** 3 + 8 * n * n * (n // 2 + 1)}
-        del xr, yr, rplan
+        br = torch.empty_like(xr)
+        real = {}
+        for name, rplan, src, dst in (("r2c", RealPlan(n, batch), xr, yr),
+                                      ("c2r", RealPlan(n, batch, inverse=True), yr, br)):
+            for _ in range(3):
+                rplan.execute(src, dst, stream)
+            barrier()
+            kr = max(1, args.steps // 8)
+            r0 = torch.cuda.Event(enable_timing=True)
+            r1 = torch.cuda.Event(enable_timing=True)
+            r0.record(stream)
+            for _ in range(kr):
+                rplan.execute(src, dst, stream)
+            r1.record(stream)
+            barrier()
+            msr = max_over_ranks(r0.elapsed_time(r1) / kr, ws, dev)
+            assert rplan.device_status() == 0
+            real[name] = {"value": whole_job_rate(ws, batch, 1, msr), "unit": "transforms/s",
+                          "steps": kr, "ms_per_step": msr, "launches_per_step": 1,
+                          "bytes_per_transform": 4 * n ** 3 + 8 * n * n * (n // 2 + 1)}
+            del rplan
+        del xr, yr, br
 
     peak, peak_kind = measured_peaks()
 
@@ -565,9 +570,10 @@ def run_ours(args, ws, rank, local):
             v["roofline_frac"] = 16.0 * n ** 3 * batch / (v["ms_per_step"] / 1e3) / 1e9 / peak
         line["tensor_core_kinds"] = kinds
     if real is not None:
-        real["roofline_frac"] = (real["bytes_per_transform"] * batch / (real["ms_per_step"] / 1e3)
-                                 / 1e9 / peak)
-        line["real_r2c_fp32"] = real
+        for name, r in real.items():
+            r["roofline_frac"] = (r["bytes_per_transform"] * batch / (r["ms_per_step"] / 1e3)
+                                  / 1e9 / peak)
+            line[f"real_{name}_fp32"] = r
     if w64 is not None:
         line["w64x256"] = w64
     if mixed is not None:
