@@ -186,9 +186,10 @@ void free_fused(fft3d_real_plan p) {
 
 }  // namespace
 
-// Plan of the dedicated kernels: phase 0 has n items per grid (forward:
-// planes; inverse: z rows), phase 1 n items (forward: z rows, plus the
-// Nyquist column; inverse: planes); forward blocks have one ticket more.  The schedule's L2 budget counts 8 n^3
+// Plan of the dedicated kernels: per grid, phase 0 has n/P items (forward:
+// P planes each; inverse: P rows ky of every z), phase 1 n/P items (forward:
+// rows, plus the Nyquist column; inverse: planes); forward blocks have one
+// ticket more.  (P = 128/n: every item has 128 rows.)  The schedule's L2 budget counts 8 n^3
 // bytes of intermediate per grid (a complex grid); a real grid's is about
 // half of that, so the budget passed is scaled by the ratio.  The forward
 // transform keeps more grids in flight (60% of L2 against 40%): its input
@@ -227,11 +228,11 @@ int create_fused_real(int n, int batch, int direction, int norm, const KernelInf
   for (int g = 0; g < batch; ++g) order[g] = g;
   std::vector<SchedBlock> blocks(2 * (size_t)batch);
   int total = 0;
-  // n + 1 tickets per block forward (the z block's last is the Nyquist
-  // item, the plane block's last is empty), n inverse
+  // the kernel's tickets per block (forward: the z block's last is the
+  // Nyquist item, the plane block's last is empty)
   const int nb = schedule_blocks(batch, dims.data(), order.data(), resident * k.items_in_flight,
                                  (forward ? 0.6 : 0.4) * (double)l2 * (8.0 * n3 / inter),
-                                 forward ? n + 1 : n, plane_end.data(), blocks.data(), &total);
+                                 k.phase_items, plane_end.data(), blocks.data(), &total);
   auto* p = new (std::nothrow) fft3d_real_plan_s();
   if (!p) return FFT3D_ERR_ALLOC;
   p->n = n;

@@ -46,7 +46,7 @@
 // Block: a control warpgroup (producer warp: tickets, schedule lookup,
 // dependency waits, the item's copies; publisher warp: finished phase-0
 // items to the other blocks, in order) and compute groups of n threads
-// (two at 128^3, four at 64^3); a ring of three (five) tiles.  Every item arrives with at most four
+// (two at 128^3, six at 64^3); a ring of three (seven) tiles.  Every item arrives with at most four
 // copies (the copy engine's cost is per copy, not per byte, at these sizes):
 //   real plane: four tensor boxes of 32 floats x n rows, 128-byte swizzled
 //     (16-byte chunk j of row r at chunk j ^ (r mod 8)), so that both the
@@ -81,25 +81,34 @@ struct Cfg {
   static_assert(N == 64 || N == 128, "the real-grid kernels cover 64^3 and 128^3");
   static constexpr int H = N / 2;               // points of each register DFT
   static constexpr int HC = N / 2 + 1;          // complex per half-spectrum row
-  static constexpr int PITCH = (N / 2 + 2) * 8; // bytes per tile row (16-byte multiple)
-  static constexpr int MAIN = N * PITCH;        // rows of an item
-  static constexpr int MIRROR = 2 * N * 16;     // inverse: mirror boxes of columns 0 and h
+  // an item is P planes (or P rows ky of every z), 128 rows in all
+  static constexpr int P = 128 / N;
+  static constexpr int ROWS = P * N;
+  // z items: bytes per tile row (one row ky from float 0 or 2h of its pair,
+  // or, with P = 2, the whole pair); 16-byte multiples
+  static constexpr int PITCH = P == 1 ? (H + 2) * 8 : 16 * HC;
+  static constexpr int XP = (H + 2) * 8;        // padded row of a plane (thread-per-row passes)
+  static constexpr int MAIN = N * PITCH > ROWS * XP ? N * PITCH : ROWS * XP;
+  static constexpr int MIRROR = 2 * P * N * 16; // inverse: mirror boxes of columns 0 and h
   static constexpr int TILE = MAIN + MIRROR;
   static_assert(TILE % 1024 == 0, "tiles 1024-byte aligned (swizzle)");
-  static constexpr int SWB = 32 * N * 4;        // bytes of one swizzled box of the real plane
-  static constexpr int GT = N;                  // threads per compute group
+  static constexpr int SWB = 32 * ROWS * 4;     // bytes of one swizzled box of the real planes
+  static constexpr int GT = ROWS;               // threads per compute group (128)
   static constexpr int GW = GT / 32;
-  static constexpr int GROUPS = 256 / N;        // two warpgroups of compute threads
-  static constexpr int NTILE = N == 128 ? 3 : 5;  // coprime with GROUPS
+  // compute groups: two warpgroups at 128^3 (64-point DFTs, 224 registers),
+  // three at 64^3 (32-point DFTs, 152 registers)
+  static constexpr int GROUPS = N == 128 ? 2 : 3;
+  static constexpr int NTILE = N == 128 ? 3 : 4;  // coprime with GROUPS
   static constexpr int T = 128 + GROUPS * GT;   // control warpgroup + compute
-  // registers per thread at launch 65536 / 384 -> 168; setmaxnreg moves them
-  // from the control warpgroup to the compute ones: 128 * 56 + 256 * 224 =
-  // 64512 <= 384 * 168
-  static constexpr int REG_CTRL = 56, REG_COMP = 224;
+  // registers: 65536 / T at launch (168 at 128^3, 128 at 64^3); setmaxnreg
+  // moves them from the control warpgroup to the compute ones:
+  // 128 * 56 + 256 * 224 = 64512 <= 384 * 168, 128 * 56 + 384 * 152 = 65536
+  static constexpr int REG_CTRL = 56, REG_COMP = N == 128 ? 224 : 152;
+  static constexpr int IPP = N / P;             // items per phase of a grid
   static constexpr int DQ = 16;                 // finished items queued for the publisher
   static constexpr int SCHED = 2048;            // schedule blocks kept in shared memory
   static constexpr int NFULL = NTILE * GROUPS;
-  static constexpr size_t smem = 1024 + (size_t)NTILE * TILE + GROUPS * N * sizeof(float2) +
+  static constexpr size_t smem = 1024 + (size_t)NTILE * TILE + GROUPS * GT * sizeof(float2) +
                                  (NFULL + NTILE + GROUPS + DQ) * sizeof(unsigned long long) +
                                  NTILE * sizeof(int4) + (DQ + 1) * sizeof(int) +
                                  SCHED * sizeof(int);
@@ -238,13 +247,13 @@ __device__ __forceinline__ void producer(const FusedArgs& a, const CUtensorMap* 
                                          unsigned long long* done, int* pubq,
                                          volatile int* pub_done, Desc* desc, const int* sched) {
   using K = Cfg<N>;
-  constexpr int NT = K::NTILE, DQ = K::DQ, G = K::GROUPS, H = K::H;
+  constexpr int NT = K::NTILE, DQ = K::DQ, G = K::GROUPS, H = K::H, P = K::P, IPP = K::IPP;
   const int lane = threadIdx.x & 31;
   // every schedule block has IPB tickets (forward: the plane block's last
   // ticket is empty, matching the z block's Nyquist item), so a ticket's
   // block is t / IPB; (grid, phase) of the first SCHED blocks are in shared
   // memory
-  constexpr int IPB = N + (DIR < 0 ? 1 : 0);
+  constexpr int IPB = IPP + (DIR < 0 ? 1 : 0);
   auto resolve = [&](int t, Desc& d) {
     const int b = t / IPB;
     int gp;
@@ -276,10 +285,10 @@ __device__ __forceinline__ void producer(const FusedArgs& a, const CUtensorMap* 
         t2 = (int)atomicAdd(a.work, 1u);
         ok = t < a.total_items;
         if (ok) resolve(t, d);
-      } while (ok && DIR < 0 && d.phase == 0 && d.idx == N);
+      } while (ok && DIR < 0 && d.phase == 0 && d.idx == IPP);
       if (ok) {
         if (d.phase == 1 && d.grid != ready_grid) {
-          ok = bounded_wait_geq(a.work + 1 + d.grid, (unsigned)N, a.status, a.timeout_ns);
+          ok = bounded_wait_geq(a.work + 1 + d.grid, (unsigned)IPP, a.status, a.timeout_ns);
           if (ok) ready_grid = d.grid;
         }
       }
@@ -322,22 +331,23 @@ __device__ __forceinline__ void producer(const FusedArgs& a, const CUtensorMap* 
     if (!__shfl_sync(0xffffffffu, fr, 0)) break;
     live &= ~(1u << s);
     unsigned long long* fb = &full[full_idx<NT, G>(k)];
-    // the item's copies: tensor boxes (lanes 0 .. 3) or one bulk copy
-    const int g = d.grid, ky = d.idx;
+    // the item's copies: tensor boxes or one bulk copy.  Item idx covers
+    // planes (or rows ky) P idx .. P idx + P - 1.
+    const int g = d.grid, i0 = P * d.idx;
     unsigned tx = 0;
     const char* bulk = nullptr;
     if (DIR < 0) {
-      if (d.phase == 0) tx = N * N * 4;                // real plane: 4 swizzled boxes
-      else if (ky < N) tx = K::MAIN;                   // rows (z, ky): one pair-view box
+      if (d.phase == 0) tx = P * N * N * 4;            // real planes: N/32 swizzled boxes
+      else if (d.idx < IPP) tx = N * K::PITCH;         // rows (z, ky): one pair-view box
       else {                                           // Nyquist workspace
         bulk = reinterpret_cast<const char*>(a.aux) + (long long)g * N * H * 8;
         tx = N * H * 8;
       }
     } else {
-      if (d.phase == 0) tx = K::MAIN + K::MIRROR;      // rows (kz, ky) and the mirror columns
-      else {                                           // a plane of the intermediate
-        bulk = reinterpret_cast<const char*>(a.out) + ((long long)g * N + ky) * N * H * 8;
-        tx = N * H * 8;
+      if (d.phase == 0) tx = N * K::PITCH + K::MIRROR; // rows (kz, ky) and the mirror columns
+      else {                                           // planes of the intermediate
+        bulk = reinterpret_cast<const char*>(a.out) + ((long long)g * N + i0) * N * H * 8;
+        tx = P * N * H * 8;
       }
     }
     if (lane == 0) {
@@ -355,18 +365,20 @@ __device__ __forceinline__ void producer(const FusedArgs& a, const CUtensorMap* 
     if (bulk) {
       if (lane == 0) bulk_row(dst, bulk, tx, fb, once);
     } else if (DIR < 0 && d.phase == 0) {
-      if (lane < N / 32)  // plane z = idx: box {32 x, all y} at z
-        rowk::tma_box_hint(dst + lane * K::SWB, m1, 32 * lane, 0, g * N + ky, fb, once);
+      if (lane < N / 32)  // planes i0 ..: box {32 x, all y, P planes}
+        rowk::tma_box_hint(dst + lane * K::SWB, m1, 32 * lane, 0, g * N + i0, fb, once);
     } else {
-      // pair ky/2 of every z of grid g; the inverse also the mirror row
-      // (-ky): columns 0 and h, one box each
-      const int my = (N - ky) % N;
-      if (lane == 0) rowk::tma_box_hint(dst, m0, (ky & 1) ? 2 * H : 0, ky >> 1, g * N, fb, once);
-      if (DIR > 0 && lane == 1)
-        rowk::tma_box_hint(dst + K::MAIN, m1, (my & 1) ? 2 * H : 0, my >> 1, g * N, fb, once);
-      if (DIR > 0 && lane == 2)
-        rowk::tma_box_hint(dst + K::MAIN + N * 16, m1, (my & 1) ? 4 * H : 2 * H, my >> 1, g * N,
-                           fb, once);
+      // rows i0 .. of every z of grid g (pair i0/2; with P = 1 from float 0
+      // or 2h by parity); the inverse also the mirror rows -ky: columns 0
+      // and h, one box each
+      if (lane == 0)
+        rowk::tma_box_hint(dst, m0, (P == 1 && (i0 & 1)) ? 2 * H : 0, i0 >> 1, g * N, fb, once);
+      if (DIR > 0 && lane >= 1 && lane <= 2 * P) {
+        const int r = (lane - 1) >> 1, col = (lane - 1) & 1;
+        const int my = (N - i0 - r) % N;
+        const int x = col == 0 ? ((my & 1) ? 2 * H : 0) : ((my & 1) ? 4 * H : 2 * H);
+        rowk::tma_box_hint(dst + K::MAIN + (lane - 1) * N * 16, m1, x, my >> 1, g * N, fb, once);
+      }
     }
     live |= 1u << s;
   }
@@ -411,13 +423,13 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
     rgrid_fft3d_kernel(const FusedArgs a, const __grid_constant__ CUtensorMap m0,
                        const __grid_constant__ CUtensorMap m1) {
   using K = Cfg<N>;
-  constexpr int NT = K::NTILE, G = K::GROUPS, H = K::H, HC = K::HC, P = K::PITCH;
+  constexpr int NT = K::NTILE, G = K::GROUPS, H = K::H, HC = K::HC, P = K::P, IPP = K::IPP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // tiles 1024-byte aligned (the swizzle pattern follows address bits 7..9)
   unsigned char* base = smem_raw + ((1024 - (saddr(smem_raw) & 1023)) & 1023);
   const uint32_t tiles = saddr(base);
-  float2* scratch = reinterpret_cast<float2*>(base + (size_t)NT * K::TILE);  // per group: N
-  unsigned long long* full = reinterpret_cast<unsigned long long*>(scratch + G * N);
+  float2* scratch = reinterpret_cast<float2*>(base + (size_t)NT * K::TILE);  // per group: GT
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(scratch + G * K::GT);
   unsigned long long* empty = full + K::NFULL;
   unsigned long long* tr = empty + NT;  // per group: its steps inside an item
   unsigned long long* done = tr + G;    // items finished, for the publisher
@@ -446,10 +458,12 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
   }
   asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(K::REG_COMP));
 
-  // compute group g (of the warpgroups 1, 2), thread gt of N; column passes:
-  // column c = gt % H, output half h = gt / H (the same for a whole warp)
+  // compute group g (of the warpgroups 1 ..), thread gt of ROWS = P N.
+  // Row passes: row gt of the item (plane gt / N).  Column passes: plane or
+  // row r = gt / N of the item, column c = gt % H, output half h = (gt / H)
+  // mod 2 (the same for a whole warp).
   const int g = (w - 4) / K::GW, gt = threadIdx.x - 128 - g * K::GT, lane = threadIdx.x & 31;
-  const int c = gt % H, h = gt / H;
+  const int c = gt % H, h = (gt / H) & 1, r = gt / N;
   unsigned steps = 0;  // group barriers passed (parity of tr[g])
   auto group_sync = [&]() -> bool {
     __syncwarp();
@@ -470,26 +484,32 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
     if (d.item < 0) break;
     unsigned char* t = base + (size_t)s * K::TILE;
     const long long gg = d.grid;
+    const int i0 = P * d.idx;  // first plane (or row ky) of the item
     float2 v[H];
     // The item's passes share one DFT in a loop (one copy of its code for the
     // instruction cache): forward 0 plane x, 1 plane y, 2 z, 3 Nyquist;
     // inverse 0 z, 1 plane y, 2 plane x.
     int pass;
-    if constexpr (DIR < 0) pass = d.phase == 0 ? 0 : (d.idx < N ? 2 : 3);
+    if constexpr (DIR < 0) pass = d.phase == 0 ? 0 : (d.idx < IPP ? 2 : 3);
     else pass = d.phase;
-    const int off = 8 * (d.idx & 1);  // z items: column 0 in the tile row
+    // z items: column 0 of row i0 + r in the tile row
+    const int off = P == 1 ? 8 * (i0 & 1) : 8 * HC * r;
+    // the forward Nyquist item uses the threads of row 0 only
+    const bool idle = DIR < 0 && pass == 3 && r != 0;
     bool fail = false;
     if constexpr (DIR > 0) {
       if (pass == 0) {
-        // rows (kz, ky = idx) of the input: columns 0 and H -> their
-        // Hermitian parts, packed into column 0 (thread gt = kz)
-        unsigned char* rk = t + gt * P + off;
+        // rows (kz, ky = i0 + r) of the input: columns 0 and H -> their
+        // Hermitian parts, packed into column 0 (thread (r, kz = gt % N))
+        const int kz = gt % N;
+        unsigned char* rk = t + kz * K::PITCH + off;
         const float2 T0 = *reinterpret_cast<const float2*>(rk);
         const float2 Th = *reinterpret_cast<const float2*>(rk + 8 * H);
         // mirror row (-kz, -ky): its columns 0 and h from the mirror boxes
-        const int mz = (N - gt) % N, mo = 16 * mz + 8 * (((N - d.idx) % N) & 1);
-        const float2 M0 = *reinterpret_cast<const float2*>(t + K::MAIN + mo);
-        const float2 Mh = *reinterpret_cast<const float2*>(t + K::MAIN + N * 16 + mo);
+        const int mz = (N - kz) % N, mo = 16 * mz + 8 * (((N - i0 - r) % N) & 1);
+        const float2 M0 = *reinterpret_cast<const float2*>(t + K::MAIN + 2 * r * N * 16 + mo);
+        const float2 Mh =
+            *reinterpret_cast<const float2*>(t + K::MAIN + (2 * r + 1) * N * 16 + mo);
         const float2 A = make_float2(0.5f * (T0.x + M0.x), 0.5f * (T0.y - M0.y));
         const float2 B = make_float2(0.5f * (Th.x + Mh.x), 0.5f * (Th.y - Mh.y));
         *reinterpret_cast<float2*>(rk) = make_float2(A.x - B.y, A.y + B.x);  // A + i B
@@ -501,7 +521,7 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
       // ---------------------------------------------------------- in
       if constexpr (DIR < 0) {
         if (pass == 0) {
-          // x: row y = gt, 16-byte chunks of reals = pairs of complex z[m]
+          // x: row gt, 16-byte chunks of reals = pairs of complex z[m]
 #pragma unroll
           for (int j = 0; j < H / 2; ++j) {
             const float4 q = *reinterpret_cast<const float4*>(t + swz<N>(gt, j));
@@ -509,36 +529,38 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
             v[2 * j + 1] = make_float2(q.z, q.w);
           }
         } else if (pass == 1) {
-          // y: column c (chunk c/2 of every row, half c & 1)
+          // y: column c of plane r (chunk c/2 of its rows, half c & 1)
           const unsigned char* tc = t + (c & 1) * 8;
-          auto at = [&](int r) { return reinterpret_cast<const float2*>(tc + swz<N>(r, c >> 1)); };
+          auto at = [&](int y) {
+            return reinterpret_cast<const float2*>(tc + swz<N>(r * N + y, c >> 1));
+          };
           if (h == 0) load_dif<N, DIR, 0>(at, v);
           else load_dif<N, DIR, 1>(at, v);
           release(s);
         } else if (pass == 2) {
-          // z: column c of the rows (z, ky = idx)
-          load_dif_rows<N, DIR, P>(t, off + 8 * c, h, v);
+          // z: column c of the rows (z, ky = i0 + r)
+          load_dif_rows<N, DIR, K::PITCH>(t, off + 8 * c, h, v);
           release(s);
         } else {
           // Nyquist column: pencil p = c of the workspace tile (dense rows z)
-          load_dif_rows<N, DIR, H * 8>(t, 8 * c, h, v);
+          if (!idle) load_dif_rows<N, DIR, H * 8>(t, 8 * c, h, v);
           release(s);
         }
       } else {
         if (pass == 0) {
-          // z: column c of the rows (kz, ky = idx)
-          load_dif_rows<N, DIR, P>(t, off + 8 * c, h, v);
+          // z: column c of the rows (kz, ky = i0 + r)
+          load_dif_rows<N, DIR, K::PITCH>(t, off + 8 * c, h, v);
           release(s);
         } else if (pass == 1) {
-          // y: column c of plane z = idx (dense rows of H complex)
-          load_dif_rows<N, DIR, H * 8>(t, 8 * c, h, v);
+          // y: column c of plane i0 + r (dense rows of H complex)
+          load_dif_rows<N, DIR, H * 8>(t + r * N * H * 8, 8 * c, h, v);
           if (!group_sync()) {  // every column read before any row is written
             fail = true;
             break;
           }
         } else {
-          // x: row y = gt (half spectrum, X[0] + i X[h] in column 0)
-          const unsigned char* row = t + gt * P;
+          // x: row gt (half spectrum, X[0] + i X[h] in column 0)
+          const unsigned char* row = t + gt * K::XP;
 #pragma unroll
           for (int j = 0; j < H / 2; ++j) {
             const float4 q = *reinterpret_cast<const float4*>(row + 16 * j);
@@ -568,23 +590,24 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
         if (pass == 1) {
           // outputs ky = 2k + h straight to out (kept in L2).  Column 0 (C =
           // Y0 + i Yh, each Hermitian) is separated in the warp that holds
-          // it: ky and -ky have the same parity, so lane 0's 64 outputs are
+          // it: ky and -ky have the same parity, so lane 0's outputs are
           // every ky of that parity; they go to the warp's scratch, and each
-          // lane separates two of them: Y0 to column 0, Yh (real at ky = 0
+          // lane separates some of them: Y0 to column 0, Yh (real at ky = 0
           // and h) to the Nyquist workspace.
-          float2* dst = og + (long long)d.idx * N * HC;  // plane z = idx
+          const int z = i0 + r;
+          float2* dst = og + (long long)z * N * HC;
           const unsigned long long keep = rowk::policy_evict_last();
 #pragma unroll
           for (int kk = 0; kk < H; ++kk)
             if (c != 0) st_keep(dst + (2 * kk + h) * HC + c, v[kk], keep);
-          if (c < 32) {  // the warp holding column 0 (for this half)
-            float2* scr = scratch + (g * 2 + h) * H;
+          if (c < 32) {  // the warp holding column 0 (of this plane and half)
+            float2* scr = scratch + ((g * P + r) * 2 + h) * H;
             if (c == 0) {
 #pragma unroll
               for (int kk = 0; kk < H; ++kk) scr[kk] = v[kk];
             }
             __syncwarp();
-            float2* nq = a.aux + (gg * N + d.idx) * H;
+            float2* nq = a.aux + (gg * N + z) * H;
 #pragma unroll
             for (int q = 0; q < H / 32; ++q) {
               const int kk = c + 32 * q, ky = 2 * kk + h;
@@ -599,11 +622,11 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
           }
         } else if (pass == 2) {
           // outputs kz = 2k + h, scaled
-          float2* dst = og + (long long)d.idx * HC + c;
+          float2* dst = og + (long long)(i0 + r) * HC + c;
 #pragma unroll
           for (int kk = 0; kk < H; ++kk)
             st_stream(dst + (long long)(2 * kk + h) * N * HC, cscale(v[kk], sc));
-        } else {
+        } else if (!idle) {
           // Nyquist pencils: ky = c and its mirror -ky (conjugate, at -kz);
           // pencil 0 packs ky = 0 and ky = h, separated like column 0 above
 #pragma unroll
@@ -616,7 +639,7 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
             }
           }
           if (c < 32) {
-            float2* scr = scratch + (g * 2 + h) * H;
+            float2* scr = scratch + ((g * P + r) * 2 + h) * H;
             if (c == 0) {
 #pragma unroll
               for (int kk = 0; kk < H; ++kk) scr[kk] = v[kk];
@@ -636,16 +659,17 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
       } else {
         if (pass == 0) {
           // outputs z = 2k + h into the intermediate (kept in L2)
-          float2* dst = const_cast<float2*>(a.out) + gg * N * N * H + (long long)d.idx * H + c;
+          float2* dst =
+              const_cast<float2*>(a.out) + gg * N * N * H + (long long)(i0 + r) * H + c;
           const unsigned long long keep = rowk::policy_evict_last();
 #pragma unroll
           for (int kk = 0; kk < H; ++kk)
             st_keep(dst + (long long)(2 * kk + h) * N * H, v[kk], keep);
         } else if (pass == 1) {
-          // back into the tile as row y = 2k + h (padded rows)
+          // back into the tile as row y = 2k + h of plane r (padded rows)
 #pragma unroll
           for (int kk = 0; kk < H; ++kk)
-            *reinterpret_cast<float2*>(t + (2 * kk + h) * P + 8 * c) = v[kk];
+            *reinterpret_cast<float2*>(t + (r * N + 2 * kk + h) * K::XP + 8 * c) = v[kk];
           if (!group_sync()) {
             fail = true;
             break;
@@ -653,15 +677,15 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
           pass = 2;
           continue;
         } else {
-          // n reals of row y = gt, scaled, back to the row and out
-          unsigned char* row = t + gt * P;
+          // n reals of row gt, scaled, back to the row and out
+          unsigned char* row = t + gt * K::XP;
 #pragma unroll
           for (int j = 0; j < H / 2; ++j)
             *reinterpret_cast<float4*>(row + 16 * j) = make_float4(
                 sc * v[2 * j].x, sc * v[2 * j].y, sc * v[2 * j + 1].x, sc * v[2 * j + 1].y);
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           float* og = reinterpret_cast<float*>(const_cast<float2*>(a.out)) + gg * N * N * N;
-          bulk_store_row(og + ((long long)d.idx * N + gt) * N, saddr(row), N * 4);
+          bulk_store_row(og + ((long long)i0 * N + gt) * N, saddr(row), N * 4);
           asm volatile("cp.async.bulk.commit_group;" ::: "memory");
           asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
           release(s);
@@ -707,12 +731,12 @@ cudaError_t launch(const FusedArgs& a, int grid, cudaStream_t stream) {
   if (DIR < 0) {
     const cuuint64_t dims[3] = {N, N, (cuuint64_t)N * a.ngrids};
     const cuuint64_t strides[2] = {N * 4, (cuuint64_t)N * N * 4};
-    const cuuint32_t box[3] = {32, N, 1};
-    if (!encode_pairs(&m0, a.out, N, a.ngrids, 2 * (N / 2 + 2)) ||
+    const cuuint32_t box[3] = {32, N, Cfg<N>::P};
+    if (!encode_pairs(&m0, a.out, N, a.ngrids, Cfg<N>::PITCH / 4) ||
         !encode(&m1, a.in, dims, strides, box, true))
       return cudaErrorInvalidValue;
   } else {
-    if (!encode_pairs(&m0, a.in, N, a.ngrids, 2 * (N / 2 + 2)) ||
+    if (!encode_pairs(&m0, a.in, N, a.ngrids, Cfg<N>::PITCH / 4) ||
         !encode_pairs(&m1, a.in, N, a.ngrids, 4))
       return cudaErrorInvalidValue;
   }
@@ -733,6 +757,9 @@ KernelInfo info() {
   // twice that forward, whose plane items take longer than its z items, so
   // that the z items of a grid rarely wait for its planes (measured)
   k.items_in_flight = (Cfg<N>::NTILE + 3) * (DIR < 0 ? 2 : 1);
+  // tickets per schedule block: n/P items, plus (forward) the Nyquist item
+  // of a z block and an empty ticket of a plane block
+  k.phase_items = Cfg<N>::IPP + (DIR < 0 ? 1 : 0);
   return k;
 }
 
