@@ -43,21 +43,29 @@
 //     conj X[h-k]) W_n^k, DFTs it, and z[m] = r[2m] + i r[2m+1] is the row
 //     (scaled), written back with bulk copies.
 //
+// Every item has 128 rows: at 128^3 one plane (or one row ky of every z),
+// at 64^3 two (P = 128/n), so the per-item costs (ticket, barriers,
+// copies) are spread over as much data at both edges.
+//
 // Block: a control warpgroup (producer warp: tickets, schedule lookup,
 // dependency waits, the item's copies; publisher warp: finished phase-0
-// items to the other blocks, in order) and compute groups of n threads
-// (two at 128^3, six at 64^3); a ring of three (seven) tiles.  Every item arrives with at most four
-// copies (the copy engine's cost is per copy, not per byte, at these sizes):
-//   real plane: four tensor boxes of 32 floats x n rows, 128-byte swizzled
-//     (16-byte chunk j of row r at chunk j ^ (r mod 8)), so that both the
-//     thread-per-row and the thread-per-column accesses are conflict-free;
-//   rows (z, ky) of a half spectrum: one tensor box of n + 4 floats x n over a
-//     view of the half spectra as ROW PAIRS (16 (h + 1) bytes, a 16-byte
-//     multiple, where a single row of 8 (h + 1) bytes is not): pair ky/2
-//     from float 0 (even ky: columns 0 .. h+1) or 2h (odd ky: column h of
-//     row ky-1, then columns 0 .. h), 8 (h + 2) bytes per tile row;
-//   the inverse's mirror columns: two boxes of 4 floats x n of the same view;
-//   a contiguous plane of the intermediate or the Nyquist workspace: one
+// items to the other blocks, in order) and compute groups of 128 threads
+// (two at 128^3, three at 64^3); a ring of three (four) tiles.  Every item
+// arrives with at most five copies (the copy engine's cost is per copy,
+// not per byte, at these sizes):
+//   real planes: n/32 tensor boxes of 32 floats x n rows x P planes,
+//     128-byte swizzled (16-byte chunk j of row r at chunk j ^ (r mod 8)),
+//     so that both the thread-per-row and the thread-per-column accesses
+//     are conflict-free;
+//   rows (z, ky) of a half spectrum: one tensor box over a view of the half
+//     spectra as ROW PAIRS (16 (h + 1) bytes, a 16-byte multiple, where a
+//     single row of 8 (h + 1) bytes is not): at P = 1 pair ky/2 from float
+//     0 (even ky: columns 0 .. h+1) or 2h (odd ky: column h of row ky-1,
+//     then columns 0 .. h), 8 (h + 2) bytes per tile row; at P = 2 the
+//     whole pair;
+//   the inverse's mirror columns: two boxes of 4 floats x n per row ky, of
+//     the same view;
+//   contiguous planes of the intermediate or the Nyquist workspace: one
 //     bulk copy (dense rows).
 // A tile goes back to the producer as soon as its group has read it.
 // Waits are bounded in time and report through the status word.
