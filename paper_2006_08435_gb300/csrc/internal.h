@@ -51,6 +51,12 @@ struct FusedArgs {
 };
 
 using LaunchFn = cudaError_t (*)(const FusedArgs&, int grid, cudaStream_t);
+// Launch of a unit of a mixed-edge plan on packed buffers with per-grid
+// tensor maps (at most kMixMaps grids, passed with the launch): host_off[l]
+// = element offset of the unit's grid l.
+constexpr int kMixMaps = 32;
+using LaunchMapsFn = cudaError_t (*)(const FusedArgs&, const long long* host_off, int grid,
+                                     cudaStream_t);
 
 struct KernelInfo {
   LaunchFn launch = nullptr;
@@ -67,6 +73,8 @@ struct KernelInfo {
   int phase_items = 0;          // work items per phase of a grid; 0: the grid's edge
   int umma_b = 0;               // mma_frag holds the tcgen05 B table (tcgen.cuh), not mma.sync fragments
   int uses_work = 1;            // 0: no ticket counters (nothing to clear before a launch)
+  LaunchMapsFn launch_maps = nullptr;  // mixed-edge units on packed buffers (tensor-map kernels)
+  const void* func_maps = nullptr;     // its kernel
 };
 
 // ---------------------------------------------------------------- general path

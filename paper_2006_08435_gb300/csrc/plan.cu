@@ -251,6 +251,10 @@ struct Unit {
   unsigned* d_work = nullptr;
   size_t work_bytes = 0;
   int* d_map = nullptr;
+  // mixed-edge plans on packed buffers: the kernel's per-grid tensor maps
+  // (KernelInfo::launch_maps) over these element offsets of the unit's grids
+  bool use_maps = false;
+  std::vector<long long> host_off;
 };
 
 struct HostIO;
@@ -269,6 +273,10 @@ struct fft3d_plan_s {
   int do_scale = 0;
   long long timeout_ns = kDefaultWaitNs;
   std::vector<Unit> units;
+  // mixed-edge plans whose units use per-grid tensor maps on packed buffers:
+  // the units for calls with pointer arrays (the same edges, kernels that
+  // address grids through pointers)
+  std::vector<Unit> units_ptr;
   // device buffers shared by the units (owned)
   long long* d_off = nullptr;
   unsigned* d_status = nullptr;
@@ -289,7 +297,8 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 
 void free_plan_buffers(fft3d_plan p) {
   if (!p) return;
-  for (Unit& u : p->units) {
+  for (std::vector<Unit>* list : {&p->units, &p->units_ptr})
+  for (Unit& u : *list) {
     cudaFree(u.d_tw);
     cudaFree(u.d_frag);
     cudaFree(u.d_blocks);
@@ -370,6 +379,9 @@ int upload(T** dst, const T* src, size_t count) {
 int finish_unit(fft3d_plan p, Unit& u, bool identity) {
   cudaError_t e = cudaFuncSetAttribute(u.kernel.func, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)u.kernel.smem);
+  if (e == cudaSuccess && u.use_maps)
+    e = cudaFuncSetAttribute(u.kernel.func_maps, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)u.kernel.smem);
   if (e != cudaSuccess) return FFT3D_ERR_CUDA;
   int per_sm = 0, sms = 0, l2_bytes = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, u.kernel.func, u.kernel.threads,
@@ -461,6 +473,8 @@ int finish_plan(fft3d_plan p) {
   const bool identity = p->units.size() == 1;
   for (Unit& u : p->units)
     if ((rc = finish_unit(p, u, identity))) return rc;
+  for (Unit& u : p->units_ptr)
+    if ((rc = finish_unit(p, u, identity))) return rc;
   return FFT3D_SUCCESS;
 }
 
@@ -507,7 +521,8 @@ int launch_general(fft3d_plan p, const float2* in, float2* out, cudaStream_t str
 int launch(fft3d_plan p, const float2* in, float2* out, const float2* const* in_ptrs,
            float2* const* out_ptrs, cudaStream_t stream) {
   if (p->general) return launch_general(p, in, out, stream);
-  for (const Unit& u : p->units) {
+  const std::vector<Unit>& units = in_ptrs && !p->units_ptr.empty() ? p->units_ptr : p->units;
+  for (const Unit& u : units) {
     // ticket kernels start from zeroed counters; cluster and whole-grid
     // kernels use none
     if (u.kernel.cluster == 0 && u.kernel.uses_work &&
@@ -533,7 +548,10 @@ int launch(fft3d_plan p, const float2* in, float2* out, const float2* const* in_
     a.timeout_ns = p->timeout_ns;
     a.mma_frag = u.d_frag;
     a.ngrids = (int)u.grids.size();
-    if (u.kernel.launch(a, u.grid, stream) != cudaSuccess) {
+    const cudaError_t e = u.use_maps && !in_ptrs
+                              ? u.kernel.launch_maps(a, u.host_off.data(), u.grid, stream)
+                              : u.kernel.launch(a, u.grid, stream);
+    if (e != cudaSuccess) {
       cudaGetLastError();
       return FFT3D_ERR_CUDA;
     }
@@ -727,6 +745,8 @@ int create_mixed(int count, const int* dims, int direction, int norm, int varian
     p->units.push_back(u);
   } else {
     // one unit per distinct edge, largest edges first
+    bool any_maps = false;
+    std::vector<Unit> ptr_units;
     std::vector<int> edges(p->dims);
     std::sort(edges.begin(), edges.end(), std::greater<int>());
     edges.erase(std::unique(edges.begin(), edges.end()), edges.end());
@@ -734,15 +754,27 @@ int create_mixed(int count, const int* dims, int direction, int norm, int varian
       Unit u;
       for (int g = 0; g < count; ++g)
         if (p->dims[g] == n) u.grids.push_back(g);
-      // the edge's default kernel, unless it is one of the tensor-map kernels
-      // (64^3: 7, 8; 128^3: 6), which need the unit's grids as one packed
-      // batch; the unit addresses its grids through the plan's map, so those
-      // edges take the fastest kernel that does (64^3: 0, 128^3: 5)
+      // the edge's default kernel.  The tensor-map kernels read a packed
+      // batch: at 128^3 the split-y kernel (6) takes one pair of tensor maps
+      // per grid with the launch (up to kMixMaps grids) on packed buffers,
+      // and calls with pointer arrays use the warp-owned kernel (5) in a
+      // unit of their own; at 64^3 (7, 8) the plain persistent kernel (0),
+      // as fast at the grid counts of a mixed batch
       int v = builtin_default_variant(false, n, (int)u.grids.size(), FFT3D_FP32);
-      if ((n == 64 && (v == 7 || v == 8)) || (n == 128 && v == 6)) v = n == 64 ? 0 : 5;
+      const bool maps = n == 128 && v == 6 && (int)u.grids.size() <= kMixMaps;
+      if ((n == 64 && (v == 7 || v == 8)) || (n == 128 && v == 6 && !maps)) v = n == 64 ? 0 : 5;
       u.kernel = fused_kernel_info(n, direction, v);
+      Unit w = u;
+      if (maps) {
+        u.use_maps = true;
+        for (int g : u.grids) u.host_off.push_back(p->offsets[g]);
+        w.kernel = fused_kernel_info(n, direction, 5);
+        any_maps = true;
+      }
       p->units.push_back(u);
+      ptr_units.push_back(w);
     }
+    if (any_maps) p->units_ptr = ptr_units;
   }
   rc = finish_plan(p);
   if (rc) {

@@ -130,6 +130,14 @@ struct Desc {
   int item, grid, phase, idx;
 };
 
+// Tensor maps passed with a launch (kernel parameter space): NM = 1 for a
+// packed uniform batch, kMixMaps for the grids of a mixed-edge unit.
+template <int NM>
+struct TensorMaps {
+  CUtensorMap in[NM];
+  CUtensorMap out[NM];
+};
+
 __device__ __forceinline__ Desc bcast(Desc d) {
   d.item = __shfl_sync(0xffffffffu, d.item, 0);
   d.grid = __shfl_sync(0xffffffffu, d.grid, 0);

@@ -168,9 +168,12 @@ __device__ __forceinline__ bool partner_loaded(int k, const Desc& d, unsigned lo
 // ------------------------------------------------------------- producer
 // Lanes 0..7 issue the tensor boxes; lane 0 takes and resolves tickets
 // (pairs, one pair ahead).  Tensors are [N * batch][N][2N] floats.
-template <int N>
-__device__ __forceinline__ void producer(const FusedArgs& a, const CUtensorMap* tin,
-                                         const CUtensorMap* tout, uint32_t tiles,
+// Tensor maps: one pair for a packed uniform batch (planes of grid g at z =
+// g N + ...), or one pair per grid (PER_GRID: a unit of a mixed-edge plan,
+// whose grids sit at arbitrary offsets; z within the grid).
+template <int N, bool PER_GRID>
+__device__ __forceinline__ void producer(const FusedArgs& a, const CUtensorMap* tins,
+                                         const CUtensorMap* touts, uint32_t tiles,
                                          unsigned long long* full, unsigned long long* freed,
                                          Desc* desc, const unsigned short* sched) {
   using K = Cfg<N>;
@@ -260,15 +263,19 @@ __device__ __forceinline__ void producer(const FusedArgs& a, const CUtensorMap* 
     if (d.phase == 0 && lane < 8) {
       // half-plane: plane z = idx / 2, rows y = parity + 2 m, 16 columns per box
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      tma_box_hint(dst + lane * 8192, tin, 32 * lane, d.idx & 1, d.grid * N + (d.idx >> 1), fb,
+      const CUtensorMap* tin = PER_GRID ? tins + d.grid : tins;
+      const int zb = PER_GRID ? 0 : d.grid * N;
+      tma_box_hint(dst + lane * 8192, tin, 32 * lane, d.idx & 1, zb + (d.idx >> 1), fb,
                    once);
     } else if (d.phase == 1 && lane < 4) {
       // slab: rows y = k2 + 64 r, columns 32 q + 16 h, every z
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("fence.proxy.async.global;" ::: "memory");
       const int r = lane >> 1, h = lane & 1, k2 = d.idx >> 2, q = d.idx & 3;
+      const CUtensorMap* tout = PER_GRID ? touts + d.grid : touts;
+      const int zb = PER_GRID ? 0 : d.grid * N;
       tma_box_hint(dst + (r * 2 + h) * 16384, tout, 2 * (32 * q + 16 * h), k2 + 64 * r,
-                   d.grid * N, fb, once);
+                   zb, fb, once);
     }
     live |= 1u << s;
   }
@@ -309,10 +316,9 @@ __device__ __forceinline__ void signaller(const FusedArgs& a, unsigned long long
   }
 }
 
-template <int N, int DIR>
+template <int N, int DIR, int NM>
 __global__ void __launch_bounds__(Cfg<N>::T, 1)
-    splity_fft3d_kernel(const FusedArgs a, const __grid_constant__ CUtensorMap tin,
-                        const __grid_constant__ CUtensorMap tout) {
+    splity_fft3d_kernel(const FusedArgs a, const __grid_constant__ rowk::TensorMaps<NM> m) {
   using K = Cfg<N>;
   constexpr int NT = K::NTILE, H = K::H;
   constexpr long long NN = (long long)N * N;
@@ -342,7 +348,7 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
 
   if (w < 4) {  // warpgroup 0: control
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(K::REG_CTRL));
-    if (w == 0) sy::producer<N>(a, &tin, &tout, tiles, full, freed, desc, sched);
+    if (w == 0) sy::producer<N, (NM > 1)>(a, m.in, m.out, tiles, full, freed, desc, sched);
     if (w == 1) sy::signaller<N>(a, full, empty, freed, desc);
     return;
   }
@@ -478,11 +484,28 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
 template <int N, int DIR>
 cudaError_t launch(const FusedArgs& a, int grid, cudaStream_t stream) {
   if (a.in_ptrs || a.grid_map || a.grid_off) return cudaErrorInvalidValue;
-  CUtensorMap tin, tout;
-  if (!rowk::encode_map(&tin, a.in, N, a.ngrids, 2 * (N / 2), 1, 2) ||
-      !rowk::encode_map(&tout, a.out, N, a.ngrids, 1, N))
+  rowk::TensorMaps<1> m;
+  if (!rowk::encode_map(&m.in[0], a.in, N, a.ngrids, 2 * (N / 2), 1, 2) ||
+      !rowk::encode_map(&m.out[0], a.out, N, a.ngrids, 1, N))
     return cudaErrorInvalidValue;
-  splity_fft3d_kernel<N, DIR><<<grid, Cfg<N>::T, Cfg<N>::smem, stream>>>(a, tin, tout);
+  splity_fft3d_kernel<N, DIR, 1><<<grid, Cfg<N>::T, Cfg<N>::smem, stream>>>(a, m);
+  return cudaGetLastError();
+}
+
+// A unit of a mixed-edge plan on packed buffers: its grids at element
+// offsets host_off[0 .. ngrids) of in and out (the unit's local grid l is
+// the plan's grid a.grid_map[l], at a.grid_off[that]); one pair of tensor
+// maps per grid, passed with the launch.
+template <int N, int DIR>
+cudaError_t launch_maps(const FusedArgs& a, const long long* host_off, int grid,
+                        cudaStream_t stream) {
+  if (a.in_ptrs || a.ngrids > kMixMaps) return cudaErrorInvalidValue;
+  rowk::TensorMaps<kMixMaps> m;
+  for (int l = 0; l < a.ngrids; ++l)
+    if (!rowk::encode_map(&m.in[l], a.in + host_off[l], N, 1, 2 * (N / 2), 1, 2) ||
+        !rowk::encode_map(&m.out[l], a.out + host_off[l], N, 1, 1, N))
+      return cudaErrorInvalidValue;
+  splity_fft3d_kernel<N, DIR, kMixMaps><<<grid, Cfg<N>::T, Cfg<N>::smem, stream>>>(a, m);
   return cudaGetLastError();
 }
 
@@ -490,7 +513,9 @@ template <int N, int DIR>
 KernelInfo info() {
   KernelInfo k;
   k.launch = &launch<N, DIR>;
-  k.func = (const void*)&splity_fft3d_kernel<N, DIR>;
+  k.launch_maps = &launch_maps<N, DIR>;
+  k.func = (const void*)&splity_fft3d_kernel<N, DIR, 1>;
+  k.func_maps = (const void*)&splity_fft3d_kernel<N, DIR, kMixMaps>;
   k.threads = Cfg<N>::T;
   k.smem = Cfg<N>::smem;
   k.twiddle_entries = N;  // (the codelets need no table; one is uploaded anyway)

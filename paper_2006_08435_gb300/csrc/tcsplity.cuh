@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
 
   if (w < 4) {  // warpgroup 0: control
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(K::REG_CTRL));
-    if (w == 0) sy::producer<N>(a, &tin, &tout, tiles, full, freed, desc, sched);
+    if (w == 0) sy::producer<N, false>(a, &tin, &tout, tiles, full, freed, desc, sched);
     if (w == 1) sy::signaller<N>(a, full, empty, freed, desc);
     return;
   }

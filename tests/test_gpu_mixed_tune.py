@@ -141,3 +141,34 @@ def test_autotune_records_and_plans_use_the_choice(cuda, tmp_path, monkeypatch):
     Plan(64, 64, 64, 16).execute(x, y)
     ref = oracle.dft3d(x[5].cpu().numpy().astype(np.complex128), -1)
     assert oracle.rel_l2(y[5].cpu().numpy(), ref) <= FP32_TOL
+
+
+def test_per_grid_tensor_maps_in_place_and_beyond_the_table(cuda, mixed_env):
+    """One launch per edge on packed buffers: the 128^3 grids run the split-y
+    kernel with one pair of tensor maps per grid, also in place (in == out)
+    with distinct grids; with more 128^3 grids than one launch takes maps for
+    (33 > 32) the unit falls back to the warp-owned kernel.  Sampled grids
+    against the oracle, every grid back through the inverse."""
+    from paper_2006_08435_gb300 import MixedPlan
+    os.environ["FFT3D_MIXED_VARIANT"] = "1"
+    for sizes in ([128, 32, 128, 64, 128, 96, 128], [32] + [128] * 33):
+        grids, packed = _packed(sizes, seed=len(sizes))
+        fwd, inv = MixedPlan(sizes), MixedPlan(sizes, inverse=True)
+        x = packed.clone()
+        fwd.execute(x, x)  # in place
+        torch.cuda.synchronize()
+        assert fwd.device_status() == 0
+        xc = x.cpu().numpy()
+        idx = [i for i, n in enumerate(sizes) if n == 128]
+        for i in (idx[0], idx[-1], 0):
+            n = sizes[i]
+            ref = oracle.dft3d(grids[i].astype(np.complex128), -1)
+            assert oracle.rel_l2(xc[fwd.offsets[i]:fwd.offsets[i + 1]].reshape(n, n, n), ref) <= FP32_TOL
+        back = torch.empty_like(x)
+        inv.execute(x, back)
+        torch.cuda.synchronize()
+        assert inv.device_status() == 0
+        bc, pc = back.cpu().numpy(), packed.cpu().numpy()
+        for i, n in enumerate(sizes):
+            seg = slice(fwd.offsets[i], fwd.offsets[i + 1])
+            assert oracle.rel_l2(bc[seg] / float(n) ** 3, pc[seg]) <= 2 * FP32_TOL
