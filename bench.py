@@ -10,14 +10,15 @@ transform = 16 * N^3 (one read and one write of the grid).
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload 128x32|64x256|128x16|64x64|64x128|256x2] [--no-cpu-baseline]
                   [--no-e2e] [--no-split] [--no-real] [--no-64] [--no-mixed] [--no-batch1]
-                  [--no-general]
+                  [--no-general] [--no-hartree]
 
 The small workloads exist for profiler captures of the same kernels.  Beside
 the headline the line carries sub-objects: split_fp16 (the same batch in
 split FP16), tensor_core_kinds (split BF16, FP16, block floating point
 FP16, split FP8, FP8 on the same batch), real_r2c_fp32 / real_c2r_fp32 (real grids), w64x256 (64^3 x 256 in FP32 and
 split FP16), mixed_c2 (64 mixed-edge grids, forward + inverse in one CUDA
-graph), general_path (256^3 and a non-cubic batch on the per-axis passes)
+graph), general_path (256^3 and a non-cubic batch on the per-axis passes), hartree
+(energy + gradient of real densities, the differentiation workload)
 and batch1 (one grid per launch, L2 flushed, the paper's setting).
 
 Under torchrun each rank transforms its own batch (weak scaling, no
@@ -477,6 +478,45 @@ def run_ours(args, ws, rank, local):
                  "roofline_frac": 2 * 16.0 * pts / (msm / 1e3) / 1e9 / peak}
         del xm, ym, bm, graph, fwd, inv
 
+    # the Hartree energy and its gradient on real densities (the
+    # differentiation workload: 128^3, cell of 10 bohr, densities of 64
+    # Gaussians): forward = real-grid transform + FP64 reduction over the
+    # half spectrum, backward = seed on the half spectrum + real-grid
+    # inverse; a batch of `batch` densities per step, and one density alone
+    hartree = None
+    if not args.no_hartree and n % 2 == 0:
+        import numpy as np
+        from paper_2006_08435_gb300 import hartree_energy
+        rho1 = synth.hartree_density(n, seed=1 + rank)[0].astype(np.float32)
+        hartree = {"cell_bohr": 10.0, "l2": "inputs larger than L2 (no flush)"}
+        for hb in (batch, 1):
+            rho = torch.from_numpy(rho1).to(dev).expand(hb, n, n, n).contiguous()
+            rho = (rho * (1.0 + 0.01 * torch.arange(hb, device=dev).view(-1, 1, 1, 1))).contiguous()
+
+            def step(rho=rho):
+                r = rho.detach().requires_grad_(True)
+                e = hartree_energy(r, 10.0)
+                e.sum().backward()
+                return r.grad
+
+            with torch.cuda.stream(stream):
+                for _ in range(3):
+                    step()
+            barrier()
+            kh = max(2, args.steps // 4)
+            with torch.cuda.stream(stream):  # the binding launches on the current stream
+                msh = timed_ms(step, kh, stream)
+            msh = max_over_ranks(msh, ws, dev)
+            half = n * n * (n // 2 + 1) * 8
+            # algorithmic bytes per density: R2C (4 n^3 + half), reduction
+            # (half), seed (2 half), C2R (half + 4 n^3)
+            hbytes = 8 * n ** 3 + 5 * half
+            hartree[f"batch{hb}"] = {
+                "value": whole_job_rate(ws, hb, 1, msh), "unit": "densities/s (energy + gradient)",
+                "steps": kh, "ms_per_step": msh, "bytes_per_density": hbytes,
+                "roofline_frac": hbytes * hb / (msh / 1e3) / 1e9 / peak}
+            del rho
+
     # the general path (any edge up to 512, non-cubic grids): 256^3 x 4 and
     # a non-cubic batch, one pencil pass per axis (three launches per chunk
     # of grids); roofline fractions of the 16 n^3 bytes and of the passes'
@@ -580,6 +620,8 @@ def run_ours(args, ws, rank, local):
         line["mixed_c2"] = mixed
     if general is not None:
         line["general_path"] = general
+    if hartree is not None:
+        line["hartree"] = hartree
     if batch1 is not None:
         line["batch1"] = batch1
     if ws == 1 and not args.no_cpu_baseline:
@@ -605,6 +647,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-edge graph sub-leg")
     ap.add_argument("--no-batch1", action="store_true", help="skip the batch-1 latency sub-leg")
     ap.add_argument("--no-general", action="store_true", help="skip the general-path sub-leg")
+    ap.add_argument("--no-hartree", action="store_true", help="skip the Hartree sub-leg")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":

@@ -18,6 +18,7 @@
 // reduction order, so repeated calls give bit-identical results.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 
@@ -35,20 +36,6 @@ __host__ __device__ inline int energy_blocks(long long npts) {
 
 __device__ __forceinline__ int signed_index(int k, int n) { return k < (n + 1) / 2 ? k : k - n; }
 
-// |m|^2 of point i of a full spectrum (HALF false: rows of n) or of a half
-// spectrum (HALF true: rows of n / 2 + 1, kx = 0 .. n / 2), and in *w the
-// number of points of the full spectrum the point stands for: a real
-// grid's spectrum has |F(-k)| = |F(k)|, so a half-spectrum point with
-// 0 < kx < n / 2 counts twice (its mirror kx -> n - kx is not stored).
-template <bool HALF>
-__device__ __forceinline__ int m_squared(long long i, int n, int* w = nullptr) {
-  const int h = HALF ? n / 2 + 1 : n;
-  const int kx = (int)(i % h), ky = (int)((i / h) % n), kz = (int)(i / ((long long)h * n));
-  const int mx = signed_index(kx, n), my = signed_index(ky, n), mz = signed_index(kz, n);
-  if (w) *w = HALF && kx != 0 && 2 * kx != n ? 2 : 1;
-  return mx * mx + my * my + mz * mz;
-}
-
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -56,38 +43,64 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // One row of blocks per grid (blockIdx.y).  partials: [batch][gridDim.x];
-// counters: [batch], zero on entry, left at zero by the last block.  npts:
-// points per grid of the (full or half) spectrum.
+// counters: [batch], zero on entry, left at zero by the last block.
+// Each term |F(m)|^2 w / |m|^2 is formed in FP32 (the correctly rounded
+// reciprocal of |m|^2; relative error <= 4 2^-24; the spectrum itself is
+// FP32) and a lane's terms of four rows are summed in FP32 (at most 32
+// terms), then accumulated in FP64: FP64 work is a few operations per
+// hundred points, since FP64 runs at a small fraction of the FP32 rate on
+// this GPU (the per-point FP64 form ran at 0.39 TB/s).  Blocks: about 2048
+// in all, each warp R rows at a time (R independent loads per lane).
 template <bool HALF>
 __global__ void __launch_bounds__(kRedThreads) hartree_energy_kernel(
     const float2* __restrict__ f, int n, long long npts, double half_s,
     double* __restrict__ partials, unsigned* __restrict__ counters, double* __restrict__ energy) {
   const int b = blockIdx.y;
   const float2* fb = f + (long long)b * npts;
+  constexpr int W = kRedThreads / 32, R = 4;  // rows per step of a warp
+  const int h = HALF ? n / 2 + 1 : n, lane = threadIdx.x & 31, rows = n * n;
+  const int rstride = gridDim.x * W;
   double acc = 0.0;
-  for (long long i = (long long)blockIdx.x * kRedThreads + threadIdx.x; i < npts;
-       i += (long long)gridDim.x * kRedThreads) {
-    int w = 1;
-    const int m2 = m_squared<HALF>(i, n, &w);
-    if (m2 != 0) {
-      const float2 v = fb[i];
-      // 1/m2 in FP64: the correctly rounded FP32 reciprocal (relative error
-      // <= 2^-24) refined by one Newton-Raphson step r = r0 + r0 (1 - m2 r0),
-      // which squares the relative error (two FP64 FMAs instead of a
-      // division on the FP64 units)
-      const double r0 = (double)(1.0f / (float)m2);
-      const double inv = fma(r0, fma(-(double)m2, r0, 1.0), r0);
-      acc += ((double)v.x * v.x + (double)v.y * v.y) * (inv * (double)w);
+  // a warp takes R rows at a time (R independent loads per lane per step);
+  // its lanes' FP32 sums of those rows go to the FP64 accumulator
+  for (int row0 = blockIdx.x * W + (threadIdx.x >> 5); row0 < rows; row0 += R * rstride) {
+    int myz[R];
+    const float2* fr[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int row = row0 + r * rstride < rows ? row0 + r * rstride : row0;
+      const int kz = row / n, ky = row - kz * n;
+      const int mz = signed_index(kz, n), my = signed_index(ky, n);
+      myz[r] = row0 + r * rstride < rows ? mz * mz + my * my : -1;  // -1: no such row
+      fr[r] = fb + (long long)row * h;
     }
+    float part = 0.0f;
+    for (int kx = lane; kx < h; kx += 32) {
+      const int mx = signed_index(kx, n);
+      const float w = HALF && kx != 0 && 2 * kx != n ? 2.0f : 1.0f;
+      float2 v[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = myz[r] >= 0 ? __ldcs(fr[r] + kx) : make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int m2 = myz[r] + mx * mx;
+        if (m2 > 0) part = fmaf(fmaf(v[r].x, v[r].x, v[r].y * v[r].y), w * __frcp_rn((float)m2), part);
+      }
+      if ((kx >> 5) % 8 == 7) {  // long rows (h > 256): at most 32 terms per FP32 sum
+        acc += (double)part;
+        part = 0.0f;
+      }
+    }
+    acc += (double)part;
   }
-  __shared__ double warp_part[kRedThreads / 32];
+  __shared__ double warp_part[W];
   __shared__ int is_last;
   acc = warp_sum(acc);
   if ((threadIdx.x & 31) == 0) warp_part[threadIdx.x >> 5] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
     double s = 0.0;
-    for (int w = 0; w < kRedThreads / 32; ++w) s += warp_part[w];
+    for (int w = 0; w < W; ++w) s += warp_part[w];
     partials[(long long)b * gridDim.x + blockIdx.x] = s;
     __threadfence();
     is_last = atomicAdd(&counters[b], 1u) == gridDim.x - 1;
@@ -104,22 +117,44 @@ __global__ void __launch_bounds__(kRedThreads) hartree_energy_kernel(
 }
 
 template <bool HALF>
-__global__ void hartree_seed_kernel(const float2* __restrict__ f, int n, long long npts, double s,
-                                    const double* __restrict__ grad_e, float2* __restrict__ seed) {
+__global__ void __launch_bounds__(kRedThreads) hartree_seed_kernel(
+    const float2* __restrict__ f, int n, long long npts, double s,
+    const double* __restrict__ grad_e, float2* __restrict__ seed) {
   const int b = blockIdx.y;
   const float scale = (float)(s * grad_e[b]);
   const float2* fb = f + (long long)b * npts;
   float2* sb = seed + (long long)b * npts;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < npts;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int m2 = m_squared<HALF>(i, n);
-    float2 o = make_float2(0.0f, 0.0f);
-    if (m2 != 0) {
-      const float2 v = fb[i];
-      const float w = scale / (float)m2;
-      o = make_float2(v.x * w, v.y * w);
+  constexpr int W = kRedThreads / 32, R = 4;  // rows per step of a warp
+  const int h = HALF ? n / 2 + 1 : n, lane = threadIdx.x & 31, rows = n * n;
+  const int rstride = gridDim.x * W;
+  for (int row0 = blockIdx.x * W + (threadIdx.x >> 5); row0 < rows; row0 += R * rstride) {
+    int myz[R];
+    long long off[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int row = row0 + r * rstride < rows ? row0 + r * rstride : row0;
+      const int kz = row / n, ky = row - kz * n;
+      const int mz = signed_index(kz, n), my = signed_index(ky, n);
+      myz[r] = row0 + r * rstride < rows ? mz * mz + my * my : -1;  // -1: no such row
+      off[r] = (long long)row * h;
     }
-    sb[i] = o;
+    for (int kx = lane; kx < h; kx += 32) {
+      const int mx = signed_index(kx, n);
+      float2 v[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = myz[r] >= 0 ? __ldcs(fb + off[r] + kx) : make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (myz[r] < 0) continue;
+        const int m2 = myz[r] + mx * mx;
+        float2 o = make_float2(0.0f, 0.0f);
+        if (m2 != 0) {
+          const float w = scale * __frcp_rn((float)m2);
+          o = make_float2(v[r].x * w, v[r].y * w);
+        }
+        __stcs(sb + off[r] + kx, o);
+      }
+    }
   }
 }
 
@@ -179,8 +214,11 @@ int energy_impl(const void* rhohat, int n, int batch, double L, double* energy, 
   if (reinterpret_cast<uintptr_t>(rhohat) & 7u || reinterpret_cast<uintptr_t>(workspace) & 7u)
     return FFT3D_ERR_MISALIGNED;
   const long long npts = (long long)n * n * (HALF ? n / 2 + 1 : n);
-  const int blocks = energy_blocks(npts);
-  const size_t partial_bytes = sizeof(double) * (size_t)batch * (size_t)blocks;
+  // about 2048 blocks in all (each ends with a fenced counter update, so
+  // many short blocks cost more than the points they read), at most the
+  // workspace's energy_blocks per grid
+  const int blocks = std::max(1, std::min(energy_blocks(npts), (2048 + batch - 1) / batch));
+  const size_t partial_bytes = sizeof(double) * (size_t)batch * (size_t)energy_blocks(npts);
   unsigned char* ws = static_cast<unsigned char*>(workspace);
   unsigned* counters = reinterpret_cast<unsigned*>(ws + ((partial_bytes + 255) & ~size_t(255)));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -203,8 +241,9 @@ int seed_impl(const void* rhohat, int n, int batch, double L, const double* grad
   if (reinterpret_cast<uintptr_t>(rhohat) & 7u || reinterpret_cast<uintptr_t>(seed) & 7u)
     return FFT3D_ERR_MISALIGNED;
   const long long npts = (long long)n * n * (HALF ? n / 2 + 1 : n);
-  const int bx = grid_for(npts, 256) / batch + 1;
-  hartree_seed_kernel<HALF><<<dim3(bx, batch), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+  // about 2048 blocks in all, a warp per row of the spectrum at a time
+  const int bx = std::max(1, std::min((2048 + batch - 1) / batch, (n * n + 7) / 8));
+  hartree_seed_kernel<HALF><<<dim3(bx, batch), kRedThreads, 0, static_cast<cudaStream_t>(stream)>>>(
       static_cast<const float2*>(rhohat), n, npts, hartree_s(n, L), grad_energy,
       static_cast<float2*>(seed));
   if (cudaGetLastError() != cudaSuccess) return FFT3D_ERR_CUDA;
