@@ -46,7 +46,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 // counters: [batch], zero on entry, left at zero by the last block.
 // Each term |F(m)|^2 w / |m|^2 is formed in FP32 (the correctly rounded
 // reciprocal of |m|^2; relative error <= 4 2^-24; the spectrum itself is
-// FP32) and a lane's terms of four rows are summed in FP32 (at most 32
+// FP32) and a lane's terms of R rows are summed in FP32 (at most 32
 // terms), then accumulated in FP64: FP64 work is a few operations per
 // hundred points, since FP64 runs at a small fraction of the FP32 rate on
 // this GPU (the per-point FP64 form ran at 0.39 TB/s).  Blocks: about 2048
@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(kRedThreads) hartree_energy_kernel(
     double* __restrict__ partials, unsigned* __restrict__ counters, double* __restrict__ energy) {
   const int b = blockIdx.y;
   const float2* fb = f + (long long)b * npts;
-  constexpr int W = kRedThreads / 32, R = 4;  // rows per step of a warp
+  constexpr int W = kRedThreads / 32, R = 8;  // rows per step of a warp
   const int h = HALF ? n / 2 + 1 : n, lane = threadIdx.x & 31, rows = n * n;
   const int rstride = gridDim.x * W;
   double acc = 0.0;
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(kRedThreads) hartree_energy_kernel(
         const int m2 = myz[r] + mx * mx;
         if (m2 > 0) part = fmaf(fmaf(v[r].x, v[r].x, v[r].y * v[r].y), w * __frcp_rn((float)m2), part);
       }
-      if ((kx >> 5) % 8 == 7) {  // long rows (h > 256): at most 32 terms per FP32 sum
+      if ((kx >> 5) % 4 == 3) {  // long rows (h > 128): at most 32 terms per FP32 sum
         acc += (double)part;
         part = 0.0f;
       }
