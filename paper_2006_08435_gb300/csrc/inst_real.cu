@@ -1,9 +1,11 @@
-// Real-grid kernels (rgrid.cuh): forward (R2C) and inverse (C2R) at 64^3 and 128^3.
+// Real-grid kernels (rgrid.cuh): forward (R2C) and inverse (C2R) at 16^3 .. 128^3.
 #include "rgrid.cuh"
 
 namespace fft3d {
 
 KernelInfo real_kernel_info(int n, int dir) {
+  if (n == 16) return dir < 0 ? rg::info<16, -1>() : rg::info<16, 1>();
+  if (n == 32) return dir < 0 ? rg::info<32, -1>() : rg::info<32, 1>();
   if (n == 64) return dir < 0 ? rg::info<64, -1>() : rg::info<64, 1>();
   if (n == 128) return dir < 0 ? rg::info<128, -1>() : rg::info<128, 1>();
   return KernelInfo{};

@@ -86,21 +86,23 @@ using rowk::spin_geq;
 
 template <int N>
 struct Cfg {
-  static_assert(N == 64 || N == 128, "the real-grid kernels cover 64^3 and 128^3");
+  static_assert(N == 16 || N == 32 || N == 64 || N == 128, "power-of-two edges 16 .. 128");
   static constexpr int H = N / 2;               // points of each register DFT
   static constexpr int HC = N / 2 + 1;          // complex per half-spectrum row
   // an item is P planes (or P rows ky of every z), 128 rows in all
   static constexpr int P = 128 / N;
   static constexpr int ROWS = P * N;
-  // z items: bytes per tile row (one row ky from float 0 or 2h of its pair,
-  // or, with P = 2, the whole pair); 16-byte multiples
-  static constexpr int PITCH = P == 1 ? (H + 2) * 8 : 16 * HC;
+  // z items: bytes per tile row, one z (one row ky from float 0 or 2h of
+  // its pair, or, with P >= 2, P/2 whole pairs); 16-byte multiples
+  static constexpr int PITCH = P == 1 ? (H + 2) * 8 : 8 * HC * P;
   static constexpr int XP = (H + 2) * 8;        // padded row of a plane (thread-per-row passes)
   static constexpr int MAIN = N * PITCH > ROWS * XP ? N * PITCH : ROWS * XP;
   static constexpr int MIRROR = 2 * P * N * 16; // inverse: mirror boxes of columns 0 and h
   static constexpr int TILE = MAIN + MIRROR;
   static_assert(TILE % 1024 == 0, "tiles 1024-byte aligned (swizzle)");
-  static constexpr int SWB = 32 * ROWS * 4;     // bytes of one swizzled box of the real planes
+  // bytes of one swizzled box of the real planes (32 floats wide: part of a
+  // row, or at 16^3 two rows)
+  static constexpr int SWB = 32 * ROWS * 4 / (N < 32 ? 32 / N : 1);
   static constexpr int GT = ROWS;               // threads per compute group (128)
   static constexpr int GW = GT / 32;
   // compute groups: two warpgroups at 128^3 (64-point DFTs, 224 registers),
@@ -168,11 +170,15 @@ __device__ __forceinline__ void st_keep_f(float* p, float v, unsigned long long 
 
 __device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
 
-// Byte offset of 16-byte chunk j (floats 4j .. 4j+3) of row r of a real
-// plane in its swizzled tile (boxes of 32 floats, 128-byte swizzle).
+// Byte offset of 16-byte chunk j (floats 4j .. 4j+3) of row r of the real
+// planes in their swizzled tile (boxes of 32 floats, 128-byte swizzle; at
+// 16^3 a 128-byte line holds rows 2R and 2R + 1).
 template <int N>
 __device__ __forceinline__ uint32_t swz(int r, int j) {
-  return (uint32_t)((j >> 3) * Cfg<N>::SWB + r * 128 + (((j & 7) ^ (r & 7)) << 4));
+  if constexpr (N >= 32)
+    return (uint32_t)((j >> 3) * Cfg<N>::SWB + r * 128 + (((j & 7) ^ (r & 7)) << 4));
+  const int R = r >> 1, ch = ((r & 1) << 2) + j;
+  return (uint32_t)(R * 128 + ((ch ^ (R & 7)) << 4));
 }
 
 // ------------------------------------------------------------ row algebra
@@ -373,7 +379,7 @@ __device__ __forceinline__ void producer(const FusedArgs& a, const CUtensorMap* 
     if (bulk) {
       if (lane == 0) bulk_row(dst, bulk, tx, fb, once);
     } else if (DIR < 0 && d.phase == 0) {
-      if (lane < N / 32)  // planes i0 ..: box {32 x, all y, P planes}
+      if (lane < (N >= 32 ? N / 32 : 1))  // planes i0 ..: box {32 x, all y, P planes}
         rowk::tma_box_hint(dst + lane * K::SWB, m1, 32 * lane, 0, g * N + i0, fb, once);
     } else {
       // rows i0 .. of every z of grid g (pair i0/2; with P = 1 from float 0
@@ -471,7 +477,12 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
   // row r = gt / N of the item, column c = gt % H, output half h = (gt / H)
   // mod 2 (the same for a whole warp).
   const int g = (w - 4) / K::GW, gt = threadIdx.x - 128 - g * K::GT, lane = threadIdx.x & 31;
-  const int c = gt % H, h = (gt / H) & 1, r = gt / N;
+  // (halves of fewer than 32 columns: half h = warp parity, so that h stays
+  // the same across a warp)
+  const int q = ((gt >> 6) << 5) + lane;
+  const int c = H >= 32 ? gt % H : q % H;
+  const int h = H >= 32 ? (gt / H) & 1 : (gt >> 5) & 1;
+  const int r = H >= 32 ? gt / N : q / H;
   unsigned steps = 0;  // group barriers passed (parity of tr[g])
   auto group_sync = [&]() -> bool {
     __syncwarp();
@@ -507,17 +518,18 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
     bool fail = false;
     if constexpr (DIR > 0) {
       if (pass == 0) {
-        // rows (kz, ky = i0 + r) of the input: columns 0 and H -> their
-        // Hermitian parts, packed into column 0 (thread (r, kz = gt % N))
-        const int kz = gt % N;
-        unsigned char* rk = t + kz * K::PITCH + off;
+        // rows (kz, ky = i0 + rs) of the input: columns 0 and H -> their
+        // Hermitian parts, packed into column 0 (thread (rs, kz = gt % N))
+        const int kz = gt % N, rs = gt / N;
+        const int offs = P == 1 ? off : 8 * HC * rs;
+        unsigned char* rk = t + kz * K::PITCH + offs;
         const float2 T0 = *reinterpret_cast<const float2*>(rk);
         const float2 Th = *reinterpret_cast<const float2*>(rk + 8 * H);
         // mirror row (-kz, -ky): its columns 0 and h from the mirror boxes
-        const int mz = (N - kz) % N, mo = 16 * mz + 8 * (((N - i0 - r) % N) & 1);
-        const float2 M0 = *reinterpret_cast<const float2*>(t + K::MAIN + 2 * r * N * 16 + mo);
+        const int mz = (N - kz) % N, mo = 16 * mz + 8 * (((N - i0 - rs) % N) & 1);
+        const float2 M0 = *reinterpret_cast<const float2*>(t + K::MAIN + 2 * rs * N * 16 + mo);
         const float2 Mh =
-            *reinterpret_cast<const float2*>(t + K::MAIN + (2 * r + 1) * N * 16 + mo);
+            *reinterpret_cast<const float2*>(t + K::MAIN + (2 * rs + 1) * N * 16 + mo);
         const float2 A = make_float2(0.5f * (T0.x + M0.x), 0.5f * (T0.y - M0.y));
         const float2 B = make_float2(0.5f * (Th.x + Mh.x), 0.5f * (Th.y - Mh.y));
         *reinterpret_cast<float2*>(rk) = make_float2(A.x - B.y, A.y + B.x);  // A + i B
@@ -617,8 +629,8 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
             __syncwarp();
             float2* nq = a.aux + (gg * N + z) * H;
 #pragma unroll
-            for (int q = 0; q < H / 32; ++q) {
-              const int kk = c + 32 * q, ky = 2 * kk + h;
+            for (int kk = c; kk < H; kk += 32) {
+              const int ky = 2 * kk + h;
               const float2 cc = scr[kk], m = scr[h == 0 ? (H - kk) % H : H - 1 - kk];
               const float2 A = make_float2(0.5f * (cc.x + m.x), 0.5f * (cc.y - m.y));  // (C + conj M) / 2
               const float2 B = make_float2(0.5f * (cc.y + m.y), 0.5f * (m.x - cc.x));  // (C - conj M) / 2i
@@ -634,33 +646,39 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
 #pragma unroll
           for (int kk = 0; kk < H; ++kk)
             st_stream(dst + (long long)(2 * kk + h) * N * HC, cscale(v[kk], sc));
-        } else if (!idle) {
+        } else {
           // Nyquist pencils: ky = c and its mirror -ky (conjugate, at -kz);
-          // pencil 0 packs ky = 0 and ky = h, separated like column 0 above
+          // pencil 0 packs ky = 0 and ky = h, separated like column 0 above.
+          // Idle lanes (rows r > 0 of the item) store nothing but take part
+          // in the warp's synchronisation: at n < 64 they share warps with
+          // working lanes.
+          if (!idle) {
 #pragma unroll
-          for (int kk = 0; kk < H; ++kk) {
-            const int kz = 2 * kk + h, mz = (N - kz) % N;
-            const float2 o = cscale(v[kk], sc);
-            if (c != 0) {
-              st_stream(og + ((long long)kz * N + c) * HC + H, o);
-              st_stream(og + ((long long)mz * N + (N - c)) * HC + H, conjf2(o));
+            for (int kk = 0; kk < H; ++kk) {
+              const int kz = 2 * kk + h, mz = (N - kz) % N;
+              const float2 o = cscale(v[kk], sc);
+              if (c != 0) {
+                st_stream(og + ((long long)kz * N + c) * HC + H, o);
+                st_stream(og + ((long long)mz * N + (N - c)) * HC + H, conjf2(o));
+              }
             }
           }
           if (c < 32) {
             float2* scr = scratch + ((g * P + r) * 2 + h) * H;
-            if (c == 0) {
+            if (!idle && c == 0) {
 #pragma unroll
               for (int kk = 0; kk < H; ++kk) scr[kk] = v[kk];
             }
             __syncwarp();
-#pragma unroll
-            for (int q = 0; q < H / 32; ++q) {
-              const int kk = c + 32 * q, kz = 2 * kk + h;
-              const float2 cc = scr[kk], m = scr[h == 0 ? (H - kk) % H : H - 1 - kk];
-              const float2 A = make_float2(0.5f * (cc.x + m.x), 0.5f * (cc.y - m.y));
-              const float2 B = make_float2(0.5f * (cc.y + m.y), 0.5f * (m.x - cc.x));
-              st_stream(og + ((long long)kz * N) * HC + H, cscale(A, sc));
-              st_stream(og + ((long long)kz * N + H) * HC + H, cscale(B, sc));
+            if (!idle) {
+              for (int kk = c; kk < H; kk += 32) {
+                const int kz = 2 * kk + h;
+                const float2 cc = scr[kk], m = scr[h == 0 ? (H - kk) % H : H - 1 - kk];
+                const float2 A = make_float2(0.5f * (cc.x + m.x), 0.5f * (cc.y - m.y));
+                const float2 B = make_float2(0.5f * (cc.y + m.y), 0.5f * (m.x - cc.x));
+                st_stream(og + ((long long)kz * N) * HC + H, cscale(A, sc));
+                st_stream(og + ((long long)kz * N + H) * HC + H, cscale(B, sc));
+              }
             }
           }
         }
@@ -724,11 +742,12 @@ inline bool encode(CUtensorMap* m, const void* base, const cuuint64_t dims[3],
 
 // Half spectra of `grids` grids as row pairs: [n * grids][n/2][2 (n/2 + 1)
 // complex] floats.
-inline bool encode_pairs(CUtensorMap* m, const void* base, int n, int grids, unsigned box_x) {
+inline bool encode_pairs(CUtensorMap* m, const void* base, int n, int grids, unsigned box_x,
+                         unsigned box_y = 1) {
   const cuuint64_t hc = n / 2 + 1;
   const cuuint64_t dims[3] = {4 * hc, (cuuint64_t)n / 2, (cuuint64_t)n * grids};
   const cuuint64_t strides[2] = {16 * hc, (cuuint64_t)n * hc * 8};
-  const cuuint32_t box[3] = {box_x, 1, (cuuint32_t)n};
+  const cuuint32_t box[3] = {box_x, box_y, (cuuint32_t)n};
   return encode(m, base, dims, strides, box, false);
 }
 
@@ -736,16 +755,20 @@ template <int N, int DIR>
 cudaError_t launch(const FusedArgs& a, int grid, cudaStream_t stream) {
   if (a.in_ptrs || a.grid_map || a.grid_off) return cudaErrorInvalidValue;
   CUtensorMap m0, m1;
+  using K = Cfg<N>;
+  // z items: P = 1 one row of its pair (box PITCH/4 floats), else P/2 pairs
+  const unsigned zx = K::P == 1 ? K::PITCH / 4 : 4 * K::HC, zy = K::P == 1 ? 1 : K::P / 2;
   if (DIR < 0) {
-    const cuuint64_t dims[3] = {N, N, (cuuint64_t)N * a.ngrids};
-    const cuuint64_t strides[2] = {N * 4, (cuuint64_t)N * N * 4};
-    const cuuint32_t box[3] = {32, N, Cfg<N>::P};
-    if (!encode_pairs(&m0, a.out, N, a.ngrids, Cfg<N>::PITCH / 4) ||
+    // real planes: rows of N floats; at 16^3 viewed as rows of 32 (two rows)
+    const int W = N >= 32 ? N : 32;
+    const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)N * N / W, (cuuint64_t)N * a.ngrids};
+    const cuuint64_t strides[2] = {(cuuint64_t)W * 4, (cuuint64_t)N * N * 4};
+    const cuuint32_t box[3] = {32, (cuuint32_t)(N * N / W), (cuuint32_t)K::P};
+    if (!encode_pairs(&m0, a.out, N, a.ngrids, zx, zy) ||
         !encode(&m1, a.in, dims, strides, box, true))
       return cudaErrorInvalidValue;
   } else {
-    if (!encode_pairs(&m0, a.in, N, a.ngrids, Cfg<N>::PITCH / 4) ||
-        !encode_pairs(&m1, a.in, N, a.ngrids, 4))
+    if (!encode_pairs(&m0, a.in, N, a.ngrids, zx, zy) || !encode_pairs(&m1, a.in, N, a.ngrids, 4))
       return cudaErrorInvalidValue;
   }
   rgrid_fft3d_kernel<N, DIR><<<grid, Cfg<N>::T, Cfg<N>::smem, stream>>>(a, m0, m1);

@@ -1,4 +1,4 @@
-"""Parity of the dedicated real-grid kernels (64^3 and 128^3, FP32:
+"""Parity of the dedicated real-grid kernels (16^3 .. 128^3, FP32:
 half-length row transforms, no pairing) with the FP64 oracle, element by
 element.
 
@@ -17,7 +17,7 @@ from paper_2006_08435_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 FP32_TOL = 5e-6
-EDGES = [64, 128]
+EDGES = [16, 32, 64, 128]
 
 
 def to_dev(a):
