@@ -410,9 +410,10 @@ int fft3d_complex_to_real(const void* in, float* re, int64_t count, void* stream
  * and for any other input the imaginary parts of the self-mirrored bins
  * (kx, ky, kz each 0 or n/2) drop out.  `in` is not modified.
  *
- * At n = 128 in FP32 the transforms run as dedicated kernels: each real row
- * of n points is transformed as n/2 complex points and split into its half
- * spectrum (the even and odd samples' transforms, X[k] = E[k] + W_n^k O[k]),
+ * At n = 16, 32, 64 and 128 in FP32 the transforms run as dedicated kernels:
+ * each real row of n points is transformed as n/2 complex points and split
+ * into its half spectrum (the even and odd samples' transforms,
+ * X[k] = E[k] + W_n^k O[k]),
  * so the y and z transforms run on n/2 (+ 1) columns; one pass over the real
  * grids and one over the half spectra, each grid's error relative to itself.
  * Elsewhere two grids of the batch share one complex transform (c = a + i b;
@@ -433,7 +434,7 @@ typedef struct fft3d_real_plan_s* fft3d_real_plan;
  *               (half spectrum -> real).
  *   norm      : fft3d_norm (1/n^3 or 1/sqrt(n^3) on the output).
  * Validates its arguments before touching the GPU.  Owns its device memory,
- * allocated here and freed by fft3d_real_plan_destroy: at n = 128 in FP32 a
+ * allocated here and freed by fft3d_real_plan_destroy: at n = 16 .. 128 in FP32 a
  * schedule, counters and (forward) batch * n * n/2 complex64 points of
  * workspace; elsewhere a complex plan of ceil(batch/2) grids and a workspace
  * of ceil(batch/2) * n^3 complex64 points.  The environment variable
@@ -447,7 +448,7 @@ int fft3d_real_plan_create(int n, int batch, int precision, int direction, int n
  * 16-byte aligned, not overlapping (forward: in = real grids, out = half
  * spectra; inverse: the other way round).  Asynchronous on `stream`,
  * allocates nothing, capturable in a CUDA graph (a counter reset and one
- * kernel at n = 128 in FP32; elsewhere a packing or rebuilding kernel, the
+ * kernel at n = 16 .. 128 in FP32; elsewhere a packing or rebuilding kernel, the
  * complex plan's launch, a separating or splitting kernel).  A plan may run
  * on one stream at a time.
  */

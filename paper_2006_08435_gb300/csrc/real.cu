@@ -17,7 +17,7 @@
 // spectra A, B are rebuilt as one full spectrum H(A) + i H(B), transformed
 // once, and the real and imaginary parts of the result are the two grids.
 //
-// At 128^3 in FP32 the transforms run instead as dedicated two-phase
+// At 16^3 .. 128^3 in FP32 the transforms run instead as dedicated two-phase
 // kernels (rgrid.cuh: half-length row transforms, one pass over the real
 // grid and one over the half spectrum, a workspace of n^2/2 complex per
 // grid for the Nyquist column of the forward transform); everywhere else the

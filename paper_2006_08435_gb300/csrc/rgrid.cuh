@@ -44,13 +44,13 @@
 //     (scaled), written back with bulk copies.
 //
 // Every item has 128 rows: at 128^3 one plane (or one row ky of every z),
-// at 64^3 two (P = 128/n), so the per-item costs (ticket, barriers,
-// copies) are spread over as much data at both edges.
+// below it P = 128/n (2, 4, 8), so the per-item costs (ticket, barriers,
+// copies) are spread over as much data at every edge.
 //
 // Block: a control warpgroup (producer warp: tickets, schedule lookup,
 // dependency waits, the item's copies; publisher warp: finished phase-0
 // items to the other blocks, in order) and compute groups of 128 threads
-// (two at 128^3, three at 64^3); a ring of three (four) tiles.  Every item
+// (two at 128^3, three below); a ring of three (four) tiles.  Every item
 // arrives with at most five copies (the copy engine's cost is per copy,
 // not per byte, at these sizes):
 //   real planes: n/32 tensor boxes of 32 floats x n rows x P planes,
@@ -106,11 +106,11 @@ struct Cfg {
   static constexpr int GT = ROWS;               // threads per compute group (128)
   static constexpr int GW = GT / 32;
   // compute groups: two warpgroups at 128^3 (64-point DFTs, 224 registers),
-  // three at 64^3 (32-point DFTs, 152 registers)
+  // three below (32-point DFTs or shorter, 152 registers)
   static constexpr int GROUPS = N == 128 ? 2 : 3;
   static constexpr int NTILE = N == 128 ? 3 : 4;  // coprime with GROUPS
   static constexpr int T = 128 + GROUPS * GT;   // control warpgroup + compute
-  // registers: 65536 / T at launch (168 at 128^3, 128 at 64^3); setmaxnreg
+  // registers: 65536 / T at launch (168 at 128^3, 128 below); setmaxnreg
   // moves them from the control warpgroup to the compute ones:
   // 128 * 56 + 256 * 224 = 64512 <= 384 * 168, 128 * 56 + 384 * 152 = 65536
   static constexpr int REG_CTRL = 56, REG_COMP = N == 128 ? 224 : 152;
