@@ -17,10 +17,11 @@
 // spectra A, B are rebuilt as one full spectrum H(A) + i H(B), transformed
 // once, and the real and imaginary parts of the result are the two grids.
 //
-// At 16^3 .. 128^3 in FP32 the transforms run instead as dedicated two-phase
-// kernels (rgrid.cuh: half-length row transforms, one pass over the real
-// grid and one over the half spectrum, a workspace of n^2/2 complex per
-// grid for the Nyquist column of the forward transform); everywhere else the
+// At 16^3 .. 128^3 in FP32 the transforms run instead as dedicated kernels
+// with half-length row transforms: at 16^3 a whole grid per block
+// (rwholegrid.cuh), at 32^3 .. 128^3 two phases (rgrid.cuh: one pass over
+// the real grid and one over the half spectrum, a workspace of n^2/2
+// complex per grid for the Nyquist column of the forward transform); everywhere else the
 // pair scheme above, whose kernels here move data only (pack, separate,
 // rebuild, split) and whose transforms are the library's complex plans.
 // Packing two grids into one makes each grid's rounding error relative to
@@ -177,6 +178,17 @@ __global__ void rebuild_pairs_kernel(const float2* __restrict__ x, float2* __res
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+void set_real_norm(fft3d_real_plan p, int norm, int n) {
+  const double n3 = (double)n * n * n;
+  if (norm == FFT3D_NORM_BY_N) {
+    p->scale = (float)(1.0 / n3);
+    p->do_scale = 1;
+  } else if (norm == FFT3D_NORM_ORTHO) {
+    p->scale = (float)(1.0 / std::sqrt(n3));
+    p->do_scale = 1;
+  }
+}
+
 void free_fused(fft3d_real_plan p) {
   cudaFree(p->d_aux);
   cudaFree(p->d_blocks);
@@ -222,6 +234,28 @@ int create_fused_real(int n, int batch, int direction, int norm, const KernelInf
   }
   const int resident = per_sm * sms;
   const int forward = direction == FFT3D_FORWARD;
+  if (!k.uses_work) {
+    // a kernel without tickets (whole grids per block): no schedule, no
+    // counters, no workspace; a block per grid, up to the resident blocks
+    auto* p = new (std::nothrow) fft3d_real_plan_s();
+    if (!p) return FFT3D_ERR_ALLOC;
+    p->n = n;
+    p->batch = batch;
+    p->direction = direction;
+    p->fused = true;
+    p->kern = k;
+    p->grid = batch < resident ? batch : resident;
+    set_real_norm(p, norm, n);
+    if (cudaMalloc(&p->d_status, sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(p->d_status, 0, sizeof(unsigned)) != cudaSuccess) {
+      cudaGetLastError();
+      free_fused(p);
+      delete p;
+      return FFT3D_ERR_ALLOC;
+    }
+    *out_plan = p;
+    return FFT3D_SUCCESS;
+  }
   const double n3 = (double)n * n * n;
   const double inter = forward ? (double)n * n * (n / 2 + 1) * 8.0 : 4.0 * n3;
   std::vector<int> dims(batch, n), order(batch), plane_end(batch);
@@ -243,13 +277,7 @@ int create_fused_real(int n, int batch, int direction, int norm, const KernelInf
   p->nblocks = nb;
   p->total_items = total;
   p->grid = total < resident ? total : resident;
-  if (norm == FFT3D_NORM_BY_N) {
-    p->scale = (float)(1.0 / n3);
-    p->do_scale = 1;
-  } else if (norm == FFT3D_NORM_ORTHO) {
-    p->scale = (float)(1.0 / std::sqrt(n3));
-    p->do_scale = 1;
-  }
+  set_real_norm(p, norm, n);
   if (cudaMalloc(&p->d_blocks, sizeof(SchedBlock) * (size_t)nb) != cudaSuccess ||
       cudaMalloc(&p->d_count, sizeof(unsigned) * (size_t)(batch + 1)) != cudaSuccess ||
       cudaMalloc(&p->d_status, sizeof(unsigned)) != cudaSuccess ||
@@ -268,7 +296,8 @@ int create_fused_real(int n, int batch, int direction, int norm, const KernelInf
 }
 
 int execute_fused_real(fft3d_real_plan p, const void* in, void* out, cudaStream_t s) {
-  if (cudaMemsetAsync(p->d_count, 0, sizeof(unsigned) * (size_t)(p->batch + 1), s) != cudaSuccess) {
+  if (p->kern.uses_work &&
+      cudaMemsetAsync(p->d_count, 0, sizeof(unsigned) * (size_t)(p->batch + 1), s) != cudaSuccess) {
     cudaGetLastError();
     return FFT3D_ERR_CUDA;
   }

@@ -1,0 +1,225 @@
+// Whole-grid real transforms for 16^3 grids: one block holds a grid in
+// shared memory and runs the three passes of the paper's decomposition, one
+// thread per row or pencil; blocks loop over the grids of the batch.  No
+// block waits for another, so there are no work counters, no schedule and
+// no memset before a launch.
+//
+// Forward (real grid -> half spectrum, kx = 0 .. 8):
+//   x: thread t takes row t = 16 z + y as 8 complex points
+//      w[m] = r[2m] + i r[2m+1], whose 8-point DFT W gives the half spectrum
+//      of the row (E, O the transforms of the even and odd samples,
+//      E[k] = (W[k] + conj W[8-k]) / 2, O[k] = (W[k] - conj W[8-k]) / 2i):
+//        X[k] = E[k] + W_16^k O[k],  k = 0 .. 8  (indices of W mod 8);
+//   y, z: 16-point DFTs of the 144 columns (z, kx) and pencils (ky, kx),
+//      the z results straight to global memory.
+// Inverse (half spectrum -> real grid): Re of the inverse transform of the
+// Hermitian extension.  That extension's real part is the inverse transform
+// of its Hermitian part, which differs from the input only in the planes
+// kx = 0 and 8: there the z pass first takes (X(k) + conj X(-k)) / 2.
+// Inverse 16-point DFTs along z and y; then per row, from X[0 .. 8] (with
+// X[k + 8] = conj X[8 - k]),
+//   V[k] = (X[k] + conj X[8-k]) + i W_16^-k (X[k] - conj X[8-k]),  k < 8,
+// is 2 E[k] + 2 i O[k], and its inverse 8-point DFT is
+// 16 (r[2m] + i r[2m+1]): the unnormalised inverse of the row.
+//
+// Shared memory: the spectrum at S[z * 145 + y * 9 + kx] (a plane of
+// 16 x 9 points and one spare, so that every pass is free of bank
+// conflicts: half-warps take 16 rows y of one z, 16 planes z of one kx, or
+// 16 consecutive pencils); the real rows at a pitch of 20 floats (80 bytes:
+// eight lanes' 16-byte row chunks fall on distinct banks), over the same
+// bytes as the spectrum, with a block barrier between their uses.
+#pragma once
+
+#include "persistent.cuh"
+
+namespace fft3d {
+namespace rwg {
+
+template <int N>
+struct Cfg {
+  static_assert(N == 16, "the whole-grid real kernel covers 16^3");
+  static constexpr int H = N / 2, HC = H + 1;   // 8 complex per row, 9 bins
+  static constexpr int T = N * N;               // one thread per row (256)
+  static constexpr int COLS = N * HC;           // 144 pencils along y and z
+  static constexpr int SY = HC, SZ = N * HC + 1;
+  static constexpr int RP = N + 4;              // real row pitch (floats)
+  static constexpr size_t spec_bytes = sizeof(float2) * (size_t)N * SZ;
+  static constexpr size_t real_bytes = sizeof(float) * (size_t)N * N * RP;
+  static constexpr size_t smem = spec_bytes > real_bytes ? spec_bytes : real_bytes;
+};
+
+// Forward kernel: a.in holds real grids of N^3 floats, a.out half spectra of
+// N * N * (N/2 + 1) complex points.
+template <int N>
+__global__ void __launch_bounds__(Cfg<N>::T, 5) rwholegrid_fwd_kernel(const FusedArgs a) {
+  using K = Cfg<N>;
+  constexpr int H = K::H, HC = K::HC;
+  extern __shared__ __align__(16) float2 S[];
+  float* R = reinterpret_cast<float*>(S);
+  const int t = threadIdx.x;
+  const float sc = a.do_scale ? a.scale : 1.0f;
+  for (int grid = blockIdx.x; grid < a.ngrids; grid += gridDim.x) {
+    const float4* gin =
+        reinterpret_cast<const float4*>(reinterpret_cast<const float*>(a.in) + (long long)grid * N * N * N);
+    float2* gout = a.out + (long long)grid * N * N * HC;
+    // the grid into padded rows: float4 e is row e / 4, quarter e % 4
+#pragma unroll
+    for (int i = 0; i < N * N * N / 4 / K::T; ++i) {
+      const int e = t + K::T * i;
+      *reinterpret_cast<float4*>(R + (e >> 2) * K::RP + 4 * (e & 3)) = __ldcs(gin + e);
+    }
+    __syncthreads();
+    // x: row t
+    float2 w[H];
+#pragma unroll
+    for (int j = 0; j < N / 4; ++j) {
+      const float4 q = *reinterpret_cast<const float4*>(R + t * K::RP + 4 * j);
+      w[2 * j] = make_float2(q.x, q.y);
+      w[2 * j + 1] = make_float2(q.z, q.w);
+    }
+    DFT<H, -1>::run(w);
+    float2 X[HC];
+    X[0] = make_float2(w[0].x + w[0].y, 0.0f);
+    X[H] = make_float2(w[0].x - w[0].y, 0.0f);
+    static_for<1, H>([&](auto KK) {
+      constexpr int k = decltype(KK)::value;
+      const float2 p = w[k], q = make_float2(w[H - k].x, -w[H - k].y);   // W[k], conj W[8-k]
+      const float2 e = make_float2(0.5f * (p.x + q.x), 0.5f * (p.y + q.y));
+      const float2 o = make_float2(0.5f * (p.y - q.y), -0.5f * (p.x - q.x));  // (p - q) / 2i
+      X[k] = cadd(e, twc<k, N, -1>(o));
+    });
+    __syncthreads();  // every row is read before the spectrum overwrites it
+    {
+      float2* row = S + (t / N) * K::SZ + (t % N) * K::SY;
+#pragma unroll
+      for (int k = 0; k < HC; ++k) row[k] = X[k];
+    }
+    __syncthreads();
+    float2 v[N];
+    // y: column (z, kx), z = t % 16, kx = t / 16
+    if (t < K::COLS) {
+      float2* col = S + (t % N) * K::SZ + t / N;
+#pragma unroll
+      for (int y = 0; y < N; ++y) v[y] = col[y * K::SY];
+      DFT<N, -1>::run(v);
+#pragma unroll
+      for (int y = 0; y < N; ++y) col[y * K::SY] = v[y];
+    }
+    __syncthreads();
+    // z: pencil p = 9 ky + kx, to global memory (consecutive threads,
+    // consecutive points)
+    if (t < K::COLS) {
+#pragma unroll
+      for (int z = 0; z < N; ++z) v[z] = S[z * K::SZ + t];
+      DFT<N, -1>::run(v);
+#pragma unroll
+      for (int z = 0; z < N; ++z) st_stream(gout + z * K::COLS + t, cscale(v[z], sc));
+    }
+    __syncthreads();  // the shared copy is rewritten by the next grid
+  }
+}
+
+// Inverse kernel: a.in holds half spectra, a.out real grids.
+template <int N>
+__global__ void __launch_bounds__(Cfg<N>::T, 5) rwholegrid_inv_kernel(const FusedArgs a) {
+  using K = Cfg<N>;
+  constexpr int H = K::H, HC = K::HC;
+  extern __shared__ __align__(16) float2 S[];
+  float* R = reinterpret_cast<float*>(S);
+  const int t = threadIdx.x;
+  const float sc = a.do_scale ? a.scale : 1.0f;
+  for (int grid = blockIdx.x; grid < a.ngrids; grid += gridDim.x) {
+    const float2* gin = a.in + (long long)grid * N * N * HC;
+    float4* gout =
+        reinterpret_cast<float4*>(reinterpret_cast<float*>(a.out) + (long long)grid * N * N * N);
+    // the spectrum: point e is (kz, p) = (e / 144, e % 144), p = 9 ky + kx;
+    // in the planes kx = 0 and 8 its Hermitian part
+    // (X(kz, ky) + conj X(-kz, -ky)) / 2, the mirror read again (from L1 or L2)
+#pragma unroll 3
+    for (int i = 0; i < N * K::COLS / K::T; ++i) {
+      const int e = t + K::T * i, kz = e / K::COLS, p = e % K::COLS, ky = p / HC, kx = p % HC;
+      float2 x = __ldg(gin + e);
+      if (kx == 0 || kx == H) {
+        const float2 c = __ldg(gin + ((N - kz) % N) * K::COLS + ((N - ky) % N) * HC + kx);
+        x = make_float2(0.5f * (x.x + c.x), 0.5f * (x.y - c.y));
+      }
+      S[kz * K::SZ + p] = x;
+    }
+    __syncthreads();
+    float2 v[N];
+    // z: pencil p = 9 ky + kx
+    if (t < K::COLS) {
+#pragma unroll
+      for (int z = 0; z < N; ++z) v[z] = S[z * K::SZ + t];
+      DFT<N, 1>::run(v);
+#pragma unroll
+      for (int z = 0; z < N; ++z) S[z * K::SZ + t] = v[z];
+    }
+    __syncthreads();
+    // y: column (z, kx), z = t % 16, kx = t / 16
+    if (t < K::COLS) {
+      float2* col = S + (t % N) * K::SZ + t / N;
+#pragma unroll
+      for (int y = 0; y < N; ++y) v[y] = col[y * K::SY];
+      DFT<N, 1>::run(v);
+#pragma unroll
+      for (int y = 0; y < N; ++y) col[y * K::SY] = v[y];
+    }
+    __syncthreads();
+    // x: row t = 16 z + y
+    float2 w[H];
+    {
+      const float2* row = S + (t / N) * K::SZ + (t % N) * K::SY;
+      float2 X[HC];
+#pragma unroll
+      for (int k = 0; k < HC; ++k) X[k] = row[k];
+      // X[0] and X[8] are real for the Hermitian part: their real parts
+      w[0] = make_float2(X[0].x + X[H].x, X[0].x - X[H].x);
+      static_for<1, H>([&](auto KK) {
+        constexpr int k = decltype(KK)::value;
+        const float2 p = X[k], q = make_float2(X[H - k].x, -X[H - k].y);  // X[k], conj X[8-k]
+        const float2 d = twc<k, N, 1>(csub(p, q));                        // W_16^-k (p - q)
+        w[k] = cadd(cadd(p, q), mul_i<1>(d));
+      });
+    }
+    DFT<H, 1>::run(w);
+    __syncthreads();  // every row of the spectrum is read before the reals overwrite it
+#pragma unroll
+    for (int j = 0; j < N / 4; ++j)
+      *reinterpret_cast<float4*>(R + t * K::RP + 4 * j) =
+          make_float4(sc * w[2 * j].x, sc * w[2 * j].y, sc * w[2 * j + 1].x, sc * w[2 * j + 1].y);
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < N * N * N / 4 / K::T; ++i) {
+      const int e = t + K::T * i;
+      __stcs(gout + e, *reinterpret_cast<const float4*>(R + (e >> 2) * K::RP + 4 * (e & 3)));
+    }
+    __syncthreads();  // the shared copy is rewritten by the next grid
+  }
+}
+
+template <int N, int DIR>
+cudaError_t launch(const FusedArgs& a, int grid, cudaStream_t stream) {
+  grid = grid < a.ngrids ? grid : a.ngrids;  // one block per grid at most
+  if (DIR < 0)
+    rwholegrid_fwd_kernel<N><<<grid, Cfg<N>::T, Cfg<N>::smem, stream>>>(a);
+  else
+    rwholegrid_inv_kernel<N><<<grid, Cfg<N>::T, Cfg<N>::smem, stream>>>(a);
+  return cudaGetLastError();
+}
+
+template <int N, int DIR>
+KernelInfo info() {
+  KernelInfo k;
+  k.launch = &launch<N, DIR>;
+  k.func = DIR < 0 ? (const void*)&rwholegrid_fwd_kernel<N> : (const void*)&rwholegrid_inv_kernel<N>;
+  k.threads = Cfg<N>::T;
+  k.smem = Cfg<N>::smem;
+  k.sizes[0] = N;
+  k.nsizes = 1;
+  k.uses_work = 0;  // no tickets: no schedule, no counters to clear before a launch
+  return k;
+}
+
+}  // namespace rwg
+}  // namespace fft3d
