@@ -1,4 +1,4 @@
-// Persistent transforms of REAL n^3 grids (n = 64, 128): forward (R2C, sign -1, real
+// Persistent transforms of REAL n^3 grids (n = 32, 64, 128): forward (R2C, sign -1, real
 // grid -> half spectrum kx = 0 .. n/2) and inverse (C2R, sign +1), each in
 // two phases of work items with the ticket schedule and L2-resident
 // intermediate of the complex kernels.  Every 1D transform of n points is
@@ -44,7 +44,7 @@
 //     (scaled), written back with bulk copies.
 //
 // Every item has 128 rows: at 128^3 one plane (or one row ky of every z),
-// below it P = 128/n (2, 4, 8), so the per-item costs (ticket, barriers,
+// below it P = 128/n (2, 4), so the per-item costs (ticket, barriers,
 // copies) are spread over as much data at every edge.
 //
 // Block: a control warpgroup (producer warp: tickets, schedule lookup,
@@ -86,7 +86,7 @@ using rowk::spin_geq;
 
 template <int N>
 struct Cfg {
-  static_assert(N == 16 || N == 32 || N == 64 || N == 128, "power-of-two edges 16 .. 128");
+  static_assert(N == 32 || N == 64 || N == 128, "power-of-two edges 32 .. 128");
   static constexpr int H = N / 2;               // points of each register DFT
   static constexpr int HC = N / 2 + 1;          // complex per half-spectrum row
   // an item is P planes (or P rows ky of every z), 128 rows in all
@@ -100,9 +100,8 @@ struct Cfg {
   static constexpr int MIRROR = 2 * P * N * 16; // inverse: mirror boxes of columns 0 and h
   static constexpr int TILE = MAIN + MIRROR;
   static_assert(TILE % 1024 == 0, "tiles 1024-byte aligned (swizzle)");
-  // bytes of one swizzled box of the real planes (32 floats wide: part of a
-  // row, or at 16^3 two rows)
-  static constexpr int SWB = 32 * ROWS * 4 / (N < 32 ? 32 / N : 1);
+  // bytes of one swizzled box of the real planes (32 floats of each row)
+  static constexpr int SWB = 32 * ROWS * 4;
   static constexpr int GT = ROWS;               // threads per compute group (128)
   static constexpr int GW = GT / 32;
   // compute groups: two warpgroups at 128^3 (64-point DFTs, 224 registers),
@@ -171,14 +170,10 @@ __device__ __forceinline__ void st_keep_f(float* p, float v, unsigned long long 
 __device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
 
 // Byte offset of 16-byte chunk j (floats 4j .. 4j+3) of row r of the real
-// planes in their swizzled tile (boxes of 32 floats, 128-byte swizzle; at
-// 16^3 a 128-byte line holds rows 2R and 2R + 1).
+// planes in their swizzled tile (boxes of 32 floats, 128-byte swizzle).
 template <int N>
 __device__ __forceinline__ uint32_t swz(int r, int j) {
-  if constexpr (N >= 32)
-    return (uint32_t)((j >> 3) * Cfg<N>::SWB + r * 128 + (((j & 7) ^ (r & 7)) << 4));
-  const int R = r >> 1, ch = ((r & 1) << 2) + j;
-  return (uint32_t)(R * 128 + ((ch ^ (R & 7)) << 4));
+  return (uint32_t)((j >> 3) * Cfg<N>::SWB + r * 128 + (((j & 7) ^ (r & 7)) << 4));
 }
 
 // ------------------------------------------------------------ row algebra
@@ -759,11 +754,10 @@ cudaError_t launch(const FusedArgs& a, int grid, cudaStream_t stream) {
   // z items: P = 1 one row of its pair (box PITCH/4 floats), else P/2 pairs
   const unsigned zx = K::P == 1 ? K::PITCH / 4 : 4 * K::HC, zy = K::P == 1 ? 1 : K::P / 2;
   if (DIR < 0) {
-    // real planes: rows of N floats; at 16^3 viewed as rows of 32 (two rows)
-    const int W = N >= 32 ? N : 32;
-    const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)N * N / W, (cuuint64_t)N * a.ngrids};
-    const cuuint64_t strides[2] = {(cuuint64_t)W * 4, (cuuint64_t)N * N * 4};
-    const cuuint32_t box[3] = {32, (cuuint32_t)(N * N / W), (cuuint32_t)K::P};
+    // real planes: rows of N floats, boxes of 32 floats x N rows x P planes
+    const cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)N, (cuuint64_t)N * a.ngrids};
+    const cuuint64_t strides[2] = {(cuuint64_t)N * 4, (cuuint64_t)N * N * 4};
+    const cuuint32_t box[3] = {32, (cuuint32_t)N, (cuuint32_t)K::P};
     if (!encode_pairs(&m0, a.out, N, a.ngrids, zx, zy) ||
         !encode(&m1, a.in, dims, strides, box, true))
       return cudaErrorInvalidValue;
