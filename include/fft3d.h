@@ -204,7 +204,8 @@ int fft3d_plan_grid_offset(fft3d_plan plan, int g, int64_t* offset);
  *   stream  : cudaStream_t or NULL.
  * Asynchronous, allocates nothing, never synchronises, and is capturable in
  * a CUDA graph (per launch unit a memset node for its work counters, when
- * its kernel uses them, and a kernel node).
+ * its kernel uses them, and a kernel node; mixed variant 2 puts the units
+ * on the plan's side streams between event fork and join nodes).
  */
 int fft3d_execute(fft3d_plan plan, const void* in, void* out, void* stream);
 
@@ -289,10 +290,14 @@ int fft3d_selftest_wait_timeout(int64_t timeout_ns);
  * 1D transform of the pencils of one axis in shared-memory tiles (mixed
  * radices 2, 3, 4, 5, 6, 8, 9, 10, 12, 15, 16; fft3d_axis_digit_map);
  * where a plane of at least 4096 points fits shared memory, x and y run as
- * one plane pass (two launches per chunk instead of three).  Mixed plans: 0 one launch of the mixed-edge
- * kernel, 1 one launch per distinct edge (the default; an edge whose
- * default is a tensor-TMA kernel takes variant 0 at 64^3 and 5 at 128^3,
- * which address grids through the plan's map).
+ * one plane pass (two launches per chunk instead of three).  Mixed plans:
+ * 0 one launch of the mixed-edge kernel, 1 one launch per distinct edge (an
+ * edge whose default is a tensor-TMA kernel takes variant 0 at 64^3 and 5
+ * at 128^3 when grids are addressed through pointer arrays), 2 the
+ * launches of 1 as concurrent branches: the plan's own side streams, one
+ * per edge, wait on the caller's stream and the caller's stream waits on
+ * each of them (in a captured graph, parallel branches between a fork and
+ * a join).
  * At create the variant comes from FFT3D_VARIANT / FFT3D_MIXED_VARIANT if
  * set, else from the tuning cache named by FFT3D_TUNE_CACHE (tuned on the
  * spot when FFT3D_TUNE=1 and the entry is missing), else a built-in default.

@@ -1,6 +1,7 @@
 """Mixed-edge batches (64 grids, edges from {32, 48, 64, 80, 96, 128}):
-forward then inverse inside one captured CUDA graph, both launch schedules
-of a mixed plan, and the autotuner on the device."""
+forward then inverse inside one captured CUDA graph, the launch schedules
+of a mixed plan (one launch, one per edge, one per edge as concurrent
+branches), and the autotuner on the device."""
 import json
 import os
 
@@ -68,10 +69,11 @@ def test_config2_forward_inverse_in_one_graph(cuda):
             assert oracle.rel_l2(yc[off[i]:off[i + 1]].reshape(n, n, n), ref) <= FP32_TOL
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 def test_mixed_schedules_agree(cuda, mixed_env, variant):
-    """One mixed-edge launch (0) and one launch per edge (1), packed and
-    pointer-array addressing, give the same spectra."""
+    """One mixed-edge launch (0), one launch per edge (1) and the same as
+    concurrent branches (2), packed and pointer-array addressing, give the
+    same spectra."""
     from paper_2006_08435_gb300 import MixedPlan
     sizes = [128, 32, 48, 128, 64, 96, 80, 32, 64]
     grids, packed = _packed(sizes, seed=2)
@@ -103,7 +105,7 @@ def test_per_edge_schedule_with_many_grids_per_edge(cuda, mixed_env):
     sizes = synth.mixed_sizes(64, seed=0) + [64] * 16
     grids, packed = _packed(sizes, seed=8)
     outs = []
-    for variant in (0, 1):
+    for variant in (0, 1, 2):
         os.environ["FFT3D_MIXED_VARIANT"] = str(variant)
         p = MixedPlan(sizes)
         assert p.variant == variant
@@ -113,6 +115,8 @@ def test_per_edge_schedule_with_many_grids_per_edge(cuda, mixed_env):
         assert p.device_status() == 0
         outs.append(y)
     assert oracle.rel_l2(outs[1].cpu().numpy(), outs[0].cpu().numpy()) <= FP32_TOL
+    # the same kernels on the same grids, concurrently: the same bits
+    assert torch.equal(outs[2], outs[1])
     yc = outs[1].cpu().numpy()
     for i in (sizes.index(128), len(sizes) - 1):
         n = sizes[i]
@@ -127,7 +131,7 @@ def test_autotune_records_and_plans_use_the_choice(cuda, tmp_path, monkeypatch):
     assert best in (0, 1, 5, 7, 8, 10)  # the 64^3 candidates
     sizes = synth.mixed_sizes(16, seed=3)
     best_m = autotune_mixed(sizes, cache_path=cache)
-    assert best_m in (0, 1)
+    assert best_m in (0, 1, 2)
     entries = json.load(open(cache))
     assert len(entries) == 2 and best in entries.values()
     monkeypatch.delenv("FFT3D_VARIANT", raising=False)
@@ -150,8 +154,9 @@ def test_per_grid_tensor_maps_in_place_and_beyond_the_table(cuda, mixed_env):
     (33 > 32) the unit falls back to the warp-owned kernel.  Sampled grids
     against the oracle, every grid back through the inverse."""
     from paper_2006_08435_gb300 import MixedPlan
-    os.environ["FFT3D_MIXED_VARIANT"] = "1"
-    for sizes in ([128, 32, 128, 64, 128, 96, 128], [32] + [128] * 33):
+    for variant, sizes in (("1", [128, 32, 128, 64, 128, 96, 128]), ("2", [128, 32, 128, 64, 128, 96, 128]),
+                           ("1", [32] + [128] * 33)):
+        os.environ["FFT3D_MIXED_VARIANT"] = variant
         grids, packed = _packed(sizes, seed=len(sizes))
         fwd, inv = MixedPlan(sizes), MixedPlan(sizes, inverse=True)
         x = packed.clone()
@@ -172,3 +177,48 @@ def test_per_grid_tensor_maps_in_place_and_beyond_the_table(cuda, mixed_env):
         for i, n in enumerate(sizes):
             seg = slice(fwd.offsets[i], fwd.offsets[i + 1])
             assert oracle.rel_l2(bc[seg] / float(n) ** 3, pc[seg]) <= 2 * FP32_TOL
+
+
+def test_concurrent_branches_in_a_captured_graph(cuda, mixed_env):
+    """Mixed variant 2 (the per-edge launches as concurrent branches on the
+    plan's side streams) captured in a CUDA graph with its inverse: replays
+    give the bits of the eager calls, and the round trip is n^3 times the
+    input."""
+    from paper_2006_08435_gb300 import MixedPlan
+    os.environ["FFT3D_MIXED_VARIANT"] = "2"
+    sizes = [128, 32, 48, 128, 64, 96, 80, 32, 64]
+    grids, packed = _packed(sizes, seed=21)
+    fwd, inv = MixedPlan(sizes), MixedPlan(sizes, inverse=True)
+    assert fwd.variant == 2 and inv.variant == 2
+    y, back = torch.empty_like(packed), torch.empty_like(packed)
+    fwd.execute(packed, y)
+    inv.execute(y, back)
+    torch.cuda.synchronize()
+    y_eager, back_eager = y.clone(), back.clone()
+    y.zero_()
+    back.zero_()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        fwd.execute(packed, y)
+        inv.execute(y, back)
+    torch.cuda.current_stream().wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fwd.execute(packed, y)
+        inv.execute(y, back)
+    y.zero_()
+    back.zero_()
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    assert fwd.device_status() == 0 and inv.device_status() == 0
+    assert torch.equal(y, y_eager) and torch.equal(back, back_eager)
+    bc, pc = back.cpu().numpy(), packed.cpu().numpy()
+    for i, n in enumerate(sizes):
+        seg = slice(fwd.offsets[i], fwd.offsets[i + 1])
+        assert oracle.rel_l2(bc[seg] / float(n) ** 3, pc[seg]) <= 2 * FP32_TOL
+    i = sizes.index(96)
+    ref = oracle.dft3d(grids[i].astype(np.complex128), -1)
+    yc = y.cpu().numpy()
+    assert oracle.rel_l2(yc[fwd.offsets[i]:fwd.offsets[i + 1]].reshape(96, 96, 96), ref) <= FP32_TOL
