@@ -15,7 +15,8 @@ transform = 16 * N^3 (one read and one write of the grid).
 The small workloads exist for profiler captures of the same kernels.  Beside
 the headline the line carries sub-objects: split_fp16 (the same batch in
 split FP16), tensor_core_kinds (split BF16, FP16, block floating point
-FP16, split FP8, FP8 on the same batch), real_r2c_fp32 / real_c2r_fp32 (real grids), w64x256 (64^3 x 256 in FP32 and
+FP16, split FP8, FP8 on the same batch), real_r2c_fp32 / real_c2r_fp32 (real grids),
+real_16cubed_fp32 (16^3 x 16384 real grids), w64x256 (64^3 x 256 in FP32 and
 split FP16), mixed_c2 (64 mixed-edge grids, forward + inverse in one CUDA
 graph), general_path (256^3 and a non-cubic batch on the per-axis passes), hartree
 (energy + gradient of real densities, the differentiation workload)
@@ -386,7 +387,7 @@ def run_ours(args, ws, rank, local):
     # real grids (the real parts of the same batch): forward R2C to half
     # spectra and inverse C2R back, each one kernel of the real-grid path
     # after a counter reset (128^3 FP32)
-    real = None
+    real = real16 = None
     if not args.no_real:
         from paper_2006_08435_gb300 import RealPlan
         xr = x.real.contiguous()
@@ -413,6 +414,35 @@ def run_ours(args, ws, rank, local):
                           "bytes_per_transform": 4 * n ** 3 + 8 * n * n * (n // 2 + 1)}
             del rplan
         del xr, yr, br
+        # the paper's smallest edge as real grids: 16^3 x 16384 (268 MB of
+        # reals in, 302 MB of half spectra out, larger than L2), one block
+        # per grid
+        n16, b16 = 16, 16384
+        gen = torch.Generator(device=dev).manual_seed(16 + rank)
+        x16 = torch.randn((b16, n16, n16, n16), generator=gen, device=dev, dtype=torch.float32)
+        y16 = torch.empty((b16, n16, n16, n16 // 2 + 1), dtype=torch.complex64, device=dev)
+        o16 = torch.empty_like(x16)
+        real16 = {"workload": "real_16cubed_batch16384", "n": n16, "batch_per_gpu": b16,
+                  "bytes_per_transform": 4 * n16 ** 3 + 8 * n16 * n16 * (n16 // 2 + 1)}
+        for name, rplan, src, dst in (("r2c", RealPlan(n16, b16), x16, y16),
+                                      ("c2r", RealPlan(n16, b16, inverse=True), y16, o16)):
+            for _ in range(3):
+                rplan.execute(src, dst, stream)
+            barrier()
+            kr = max(1, args.steps // 8)
+            r0 = torch.cuda.Event(enable_timing=True)
+            r1 = torch.cuda.Event(enable_timing=True)
+            r0.record(stream)
+            for _ in range(kr):
+                rplan.execute(src, dst, stream)
+            r1.record(stream)
+            barrier()
+            msr = max_over_ranks(r0.elapsed_time(r1) / kr, ws, dev)
+            assert rplan.device_status() == 0
+            real16[name] = {"value": whole_job_rate(ws, b16, 1, msr), "unit": "transforms/s",
+                            "steps": kr, "ms_per_step": msr, "launches_per_step": 1}
+            del rplan
+        del x16, y16, o16
 
     peak, peak_kind = measured_peaks()
 
@@ -614,6 +644,12 @@ def run_ours(args, ws, rank, local):
             r["roofline_frac"] = (r["bytes_per_transform"] * batch / (r["ms_per_step"] / 1e3)
                                   / 1e9 / peak)
             line[f"real_{name}_fp32"] = r
+    if real16 is not None:
+        for name in ("r2c", "c2r"):
+            r = real16[name]
+            r["roofline_frac"] = (real16["bytes_per_transform"] * real16["batch_per_gpu"]
+                                  / (r["ms_per_step"] / 1e3) / 1e9 / peak)
+        line["real_16cubed_fp32"] = real16
     if w64 is not None:
         line["w64x256"] = w64
     if mixed is not None:

@@ -25,9 +25,12 @@
 // Shared memory: the spectrum at S[z * 145 + y * 9 + kx] (a plane of
 // 16 x 9 points and one spare, so that every pass is free of bank
 // conflicts: half-warps take 16 rows y of one z, 16 planes z of one kx, or
-// 16 consecutive pencils); the real rows at a pitch of 20 floats (80 bytes:
-// eight lanes' 16-byte row chunks fall on distinct banks), over the same
-// bytes as the spectrum, with a block barrier between their uses.
+// 16 consecutive pencils).  The forward transform reads its rows straight
+// from global memory and the inverse its pencils; the inverse's real rows
+// go out through shared memory at a pitch of 20 floats (80 bytes: eight
+// lanes' 16-byte row chunks fall on distinct banks), over the same bytes as
+// the spectrum, with a block barrier between their uses, so that the
+// stores are coalesced.
 #pragma once
 
 #include "persistent.cuh"
@@ -55,25 +58,19 @@ __global__ void __launch_bounds__(Cfg<N>::T, 5) rwholegrid_fwd_kernel(const Fuse
   using K = Cfg<N>;
   constexpr int H = K::H, HC = K::HC;
   extern __shared__ __align__(16) float2 S[];
-  float* R = reinterpret_cast<float*>(S);
   const int t = threadIdx.x;
   const float sc = a.do_scale ? a.scale : 1.0f;
   for (int grid = blockIdx.x; grid < a.ngrids; grid += gridDim.x) {
     const float4* gin =
         reinterpret_cast<const float4*>(reinterpret_cast<const float*>(a.in) + (long long)grid * N * N * N);
     float2* gout = a.out + (long long)grid * N * N * HC;
-    // the grid into padded rows: float4 e is row e / 4, quarter e % 4
-#pragma unroll
-    for (int i = 0; i < N * N * N / 4 / K::T; ++i) {
-      const int e = t + K::T * i;
-      *reinterpret_cast<float4*>(R + (e >> 2) * K::RP + 4 * (e & 3)) = __ldcs(gin + e);
-    }
-    __syncthreads();
-    // x: row t
+    // x: row t straight from global memory, four 16-byte loads (a warp's
+    // rows are 2 KB of consecutive bytes; the second load of each 32-byte
+    // sector finds it in L1)
     float2 w[H];
 #pragma unroll
     for (int j = 0; j < N / 4; ++j) {
-      const float4 q = *reinterpret_cast<const float4*>(R + t * K::RP + 4 * j);
+      const float4 q = __ldg(gin + t * (N / 4) + j);
       w[2 * j] = make_float2(q.x, q.y);
       w[2 * j + 1] = make_float2(q.z, q.w);
     }
@@ -88,7 +85,6 @@ __global__ void __launch_bounds__(Cfg<N>::T, 5) rwholegrid_fwd_kernel(const Fuse
       const float2 o = make_float2(0.5f * (p.y - q.y), -0.5f * (p.x - q.x));  // (p - q) / 2i
       X[k] = cadd(e, twc<k, N, -1>(o));
     });
-    __syncthreads();  // every row is read before the spectrum overwrites it
     {
       float2* row = S + (t / N) * K::SZ + (t % N) * K::SY;
 #pragma unroll
@@ -121,7 +117,7 @@ __global__ void __launch_bounds__(Cfg<N>::T, 5) rwholegrid_fwd_kernel(const Fuse
 
 // Inverse kernel: a.in holds half spectra, a.out real grids.
 template <int N>
-__global__ void __launch_bounds__(Cfg<N>::T, 5) rwholegrid_inv_kernel(const FusedArgs a) {
+__global__ void __launch_bounds__(Cfg<N>::T, 4) rwholegrid_inv_kernel(const FusedArgs a) {
   using K = Cfg<N>;
   constexpr int H = K::H, HC = K::HC;
   extern __shared__ __align__(16) float2 S[];
@@ -132,25 +128,23 @@ __global__ void __launch_bounds__(Cfg<N>::T, 5) rwholegrid_inv_kernel(const Fuse
     const float2* gin = a.in + (long long)grid * N * N * HC;
     float4* gout =
         reinterpret_cast<float4*>(reinterpret_cast<float*>(a.out) + (long long)grid * N * N * N);
-    // the spectrum: point e is (kz, p) = (e / 144, e % 144), p = 9 ky + kx;
-    // in the planes kx = 0 and 8 its Hermitian part
-    // (X(kz, ky) + conj X(-kz, -ky)) / 2, the mirror read again (from L1 or L2)
-#pragma unroll 3
-    for (int i = 0; i < N * K::COLS / K::T; ++i) {
-      const int e = t + K::T * i, kz = e / K::COLS, p = e % K::COLS, ky = p / HC, kx = p % HC;
-      float2 x = __ldg(gin + e);
-      if (kx == 0 || kx == H) {
-        const float2 c = __ldg(gin + ((N - kz) % N) * K::COLS + ((N - ky) % N) * HC + kx);
-        x = make_float2(0.5f * (x.x + c.x), 0.5f * (x.y - c.y));
-      }
-      S[kz * K::SZ + p] = x;
-    }
-    __syncthreads();
     float2 v[N];
-    // z: pencil p = 9 ky + kx
+    // z: pencil p = 9 ky + kx straight from global memory (consecutive
+    // threads, consecutive points); in the planes kx = 0 and 8 its Hermitian
+    // part (X(kz, ky) + conj X(-kz, -ky)) / 2, the mirror pencil read again
+    // (from L1 or L2)
     if (t < K::COLS) {
+      const int ky = t / HC, kx = t % HC;
 #pragma unroll
-      for (int z = 0; z < N; ++z) v[z] = S[z * K::SZ + t];
+      for (int z = 0; z < N; ++z) v[z] = __ldg(gin + z * K::COLS + t);
+      if (kx == 0 || kx == H) {
+        const float2* mir = gin + ((N - ky) % N) * HC + kx;
+#pragma unroll
+        for (int z = 0; z < N; ++z) {
+          const float2 c = __ldg(mir + ((N - z) % N) * K::COLS);
+          v[z] = make_float2(0.5f * (v[z].x + c.x), 0.5f * (v[z].y - c.y));
+        }
+      }
       DFT<N, 1>::run(v);
 #pragma unroll
       for (int z = 0; z < N; ++z) S[z * K::SZ + t] = v[z];
