@@ -419,9 +419,10 @@ int fft3d_complex_to_real(const void* in, float* re, int64_t count, void* stream
  * each real row of n points is transformed as n/2 complex points and split
  * into its half spectrum (the even and odd samples' transforms,
  * X[k] = E[k] + W_n^k O[k]),
- * so the y and z transforms run on n/2 (+ 1) columns; at n = 16 one block
- * transforms a whole grid, at 32 .. 128 one pass runs over the real grids
- * and one over the half spectra; each grid's error is relative to itself.
+ * so the y and z transforms run on n/2 (+ 1) columns; at n = 16 and 32 one
+ * block transforms a whole grid, at 64 and 128 one pass runs over the real
+ * grids and one over the half spectra; each grid's error is relative to
+ * itself.
  * Elsewhere two grids of the batch share one complex transform (c = a + i b;
  * the pair is separated with the symmetry above), so a grid's rounding error
  * is relative to the larger of its pair; cost per pair: a packing pass, one
@@ -440,9 +441,9 @@ typedef struct fft3d_real_plan_s* fft3d_real_plan;
  *               (half spectrum -> real).
  *   norm      : fft3d_norm (1/n^3 or 1/sqrt(n^3) on the output).
  * Validates its arguments before touching the GPU.  Owns its device memory,
- * allocated here and freed by fft3d_real_plan_destroy: at n = 32 .. 128 in
- * FP32 a schedule, counters and (forward) batch * n * n/2 complex64 points
- * of workspace, at n = 16 a status word only; elsewhere a complex plan of ceil(batch/2) grids and a workspace
+ * allocated here and freed by fft3d_real_plan_destroy: at n = 64 and 128
+ * in FP32 a schedule, counters and (forward) batch * n * n/2 complex64
+ * points of workspace, at n = 16 and 32 a status word only; elsewhere a complex plan of ceil(batch/2) grids and a workspace
  * of ceil(batch/2) * n^3 complex64 points.  The environment variable
  * FFT3D_REAL_PATH=pairs selects the pair scheme everywhere (for testing).
  */
@@ -453,8 +454,8 @@ int fft3d_real_plan_create(int n, int batch, int precision, int direction, int n
  * Transform every grid of the plan.  `in` and `out` are DEVICE pointers,
  * 16-byte aligned, not overlapping (forward: in = real grids, out = half
  * spectra; inverse: the other way round).  Asynchronous on `stream`,
- * allocates nothing, capturable in a CUDA graph (one kernel at n = 16, a
- * counter reset and one kernel at n = 32 .. 128 in FP32; elsewhere a packing
+ * allocates nothing, capturable in a CUDA graph (one kernel at n = 16 and
+ * 32, a counter reset and one kernel at n = 64 and 128 in FP32; elsewhere a packing
  * or rebuilding kernel, the complex plan's launch, a separating or splitting
  * kernel).  A plan may run
  * on one stream at a time.

@@ -18,8 +18,8 @@
 // once, and the real and imaginary parts of the result are the two grids.
 //
 // At 16^3 .. 128^3 in FP32 the transforms run instead as dedicated kernels
-// with half-length row transforms: at 16^3 a whole grid per block
-// (rwholegrid.cuh), at 32^3 .. 128^3 two phases (rgrid.cuh: one pass over
+// with half-length row transforms: at 16^3 and 32^3 a whole grid per block
+// (rwholegrid.cuh), at 64^3 and 128^3 two phases (rgrid.cuh: one pass over
 // the real grid and one over the half spectrum, a workspace of n^2/2
 // complex per grid for the Nyquist column of the forward transform); everywhere else the
 // pair scheme above, whose kernels here move data only (pack, separate,

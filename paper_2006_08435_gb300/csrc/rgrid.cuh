@@ -1,4 +1,4 @@
-// Persistent transforms of REAL n^3 grids (n = 32, 64, 128): forward (R2C, sign -1, real
+// Persistent transforms of REAL n^3 grids (n = 64, 128): forward (R2C, sign -1, real
 // grid -> half spectrum kx = 0 .. n/2) and inverse (C2R, sign +1), each in
 // two phases of work items with the ticket schedule and L2-resident
 // intermediate of the complex kernels.  Every 1D transform of n points is
@@ -44,13 +44,13 @@
 //     (scaled), written back with bulk copies.
 //
 // Every item has 128 rows: at 128^3 one plane (or one row ky of every z),
-// below it P = 128/n (2, 4), so the per-item costs (ticket, barriers,
+// at 64^3 two (P = 128/n), so the per-item costs (ticket, barriers,
 // copies) are spread over as much data at every edge.
 //
 // Block: a control warpgroup (producer warp: tickets, schedule lookup,
 // dependency waits, the item's copies; publisher warp: finished phase-0
 // items to the other blocks, in order) and compute groups of 128 threads
-// (two at 128^3, three below); a ring of three (four) tiles.  Every item
+// (two at 128^3, three at 64^3); a ring of three (four) tiles.  Every item
 // arrives with at most five copies (the copy engine's cost is per copy,
 // not per byte, at these sizes):
 //   real planes: n/32 tensor boxes of 32 floats x n rows x P planes,
@@ -86,7 +86,7 @@ using rowk::spin_geq;
 
 template <int N>
 struct Cfg {
-  static_assert(N == 32 || N == 64 || N == 128, "power-of-two edges 32 .. 128");
+  static_assert(N == 64 || N == 128, "edges 64 and 128");
   static constexpr int H = N / 2;               // points of each register DFT
   static constexpr int HC = N / 2 + 1;          // complex per half-spectrum row
   // an item is P planes (or P rows ky of every z), 128 rows in all
@@ -105,11 +105,11 @@ struct Cfg {
   static constexpr int GT = ROWS;               // threads per compute group (128)
   static constexpr int GW = GT / 32;
   // compute groups: two warpgroups at 128^3 (64-point DFTs, 224 registers),
-  // three below (32-point DFTs or shorter, 152 registers)
+  // three at 64^3 (32-point DFTs, 152 registers)
   static constexpr int GROUPS = N == 128 ? 2 : 3;
   static constexpr int NTILE = N == 128 ? 3 : 4;  // coprime with GROUPS
   static constexpr int T = 128 + GROUPS * GT;   // control warpgroup + compute
-  // registers: 65536 / T at launch (168 at 128^3, 128 below); setmaxnreg
+  // registers: 65536 / T at launch (168 at 128^3, 128 at 64^3); setmaxnreg
   // moves them from the control warpgroup to the compute ones:
   // 128 * 56 + 256 * 224 = 64512 <= 384 * 168, 128 * 56 + 384 * 152 = 65536
   static constexpr int REG_CTRL = 56, REG_COMP = N == 128 ? 224 : 152;
@@ -472,12 +472,7 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
   // row r = gt / N of the item, column c = gt % H, output half h = (gt / H)
   // mod 2 (the same for a whole warp).
   const int g = (w - 4) / K::GW, gt = threadIdx.x - 128 - g * K::GT, lane = threadIdx.x & 31;
-  // (halves of fewer than 32 columns: half h = warp parity, so that h stays
-  // the same across a warp)
-  const int q = ((gt >> 6) << 5) + lane;
-  const int c = H >= 32 ? gt % H : q % H;
-  const int h = H >= 32 ? (gt / H) & 1 : (gt >> 5) & 1;
-  const int r = H >= 32 ? gt / N : q / H;
+  const int c = gt % H, h = (gt / H) & 1, r = gt / N;
   unsigned steps = 0;  // group barriers passed (parity of tr[g])
   auto group_sync = [&]() -> bool {
     __syncwarp();
@@ -644,9 +639,7 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
         } else {
           // Nyquist pencils: ky = c and its mirror -ky (conjugate, at -kz);
           // pencil 0 packs ky = 0 and ky = h, separated like column 0 above.
-          // Idle lanes (rows r > 0 of the item) store nothing but take part
-          // in the warp's synchronisation: at n < 64 they share warps with
-          // working lanes.
+          // Idle lanes (rows r > 0 of the item, whole warps) store nothing.
           if (!idle) {
 #pragma unroll
             for (int kk = 0; kk < H; ++kk) {

@@ -187,7 +187,7 @@ class RealPlan:
     Inverse (``inverse=True``): x is the half spectrum and out the float32
     grids, the real part of the inverse transform of the Hermitian extension.
     At 16^3 .. 128^3 in FP32 the library runs dedicated real-grid kernels (a
-    whole grid per block at 16^3); elsewhere
+    whole grid per block at 16^3 and 32^3); elsewhere
     two grids share one complex transform."""
 
     def __init__(self, n: int, batch: int = 1, precision: str = "fp32", inverse: bool = False,
