@@ -198,7 +198,9 @@ std::vector<int> variant_candidates(bool mixed, int n, int precision) {
     case 32: return {0, 1, 3, 4, kGeneralVariant};
     case 64: return {0, 1, 5, 7, 8, kGeneralVariant};
     case 128: return {0, 5, 6, kGeneralVariant};
-    default: return {0, 1, 4, kGeneralVariant};  // 48, 80, 96
+    case 80:
+    case 96: return {0, 1, 4, kGeneralVariant, 13};
+    default: return {0, 1, 4, kGeneralVariant};  // 48
   }
 }
 
@@ -206,8 +208,9 @@ std::vector<int> variant_candidates(bool mixed, int n, int precision) {
 // (back-to-back executes; one grid also with L2 flushed):
 //   16^3: plain persistent for one grid, whole grid per block from 2;
 //   32^3: plain persistent below 64 grids, cluster-fused from 64;
-//   48^3, 96^3: plain persistent;  80^3: plain persistent for one grid,
-//     the double-buffered persistent kernel from 4 (0.67x the time at 256);
+//   48^3: plain persistent;  80^3: plain persistent for one grid, the
+//     double-buffered persistent kernel from 4, the thread-pair kernel from
+//     8;  96^3: plain persistent below 4 grids, the thread-pair kernel from 4;
 //   64^3: warp-owned for one grid, the persistent kernel with twice the
 //     threads below 16, thread-per-pencil below 64, two-plane from 64;
 //   128^3: warp-owned for one grid, split-y from 2;
@@ -229,9 +232,14 @@ int builtin_default_variant(bool mixed, int n, int batch, int precision) {
     case 16: return batch >= 2 ? 12 : 0;
     case 32: return batch >= 64 ? 3 : 0;
     case 64: return batch == 1 ? 5 : batch < 16 ? 1 : batch < 64 ? 7 : 8;
-    case 80: return batch >= 4 ? 4 : 0;
+    // 80^3, 96^3: the thread-pair kernel from 8 (80) and 4 (96) grids (x 256:
+    // 0.57 / 0.62 of the roofline against 0.30 / 0.25; x 12-14: 0.41-0.43
+    // against 0.25-0.27); below, the double-buffered kernel (80) or the
+    // plain persistent one
+    case 80: return batch >= 8 ? 13 : batch >= 4 ? 4 : 0;
+    case 96: return batch >= 4 ? 13 : 0;
     case 128: return batch == 1 ? 5 : 6;
-    default: return 0;  // 48, 96
+    default: return 0;  // 48
   }
 }
 
@@ -810,15 +818,20 @@ int create_mixed(int count, const int* dims, int direction, int norm, int varian
       // and calls with pointer arrays use the warp-owned kernel (5) in a
       // unit of their own; at 64^3 (7, 8) the plain persistent kernel (0),
       // as fast at the grid counts of a mixed batch
-      int v = builtin_default_variant(false, n, (int)u.grids.size(), FFT3D_FP32);
-      const bool maps = n == 128 && v == 6 && (int)u.grids.size() <= kMixMaps;
-      if ((n == 64 && (v == 7 || v == 8)) || (n == 128 && v == 6 && !maps)) v = n == 64 ? 0 : 5;
+      const int ng = (int)u.grids.size();
+      int v = builtin_default_variant(false, n, ng, FFT3D_FP32);
+      // the tensor-map kernels with per-grid maps: split-y (128^3) and the
+      // thread-pair kernel (80^3, 96^3); for pointer arrays a kernel that
+      // addresses grids through the plan's map
+      const bool maps = (v == 6 || v == 13) && ng <= kMixMaps;
+      const int v_ptr = n == 128 ? 5 : (n == 80 && ng >= 4) ? 4 : 0;
+      if ((n == 64 && (v == 7 || v == 8)) || ((v == 6 || v == 13) && !maps)) v = n == 64 ? 0 : v_ptr;
       u.kernel = fused_kernel_info(n, direction, v);
       Unit w = u;
       if (maps) {
         u.use_maps = true;
         for (int g : u.grids) u.host_off.push_back(p->offsets[g]);
-        w.kernel = fused_kernel_info(n, direction, 5);
+        w.kernel = fused_kernel_info(n, direction, v_ptr);
         any_maps = true;
       }
       p->units.push_back(u);

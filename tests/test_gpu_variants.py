@@ -3,7 +3,7 @@ oracle: 0 plain persistent, 1 twice the threads (16^3 .. 96^3), 3
 cluster-fused single pass (16^3, 32^3), 4 double-buffered persistent
 (32^3, 48^3, 80^3, 96^3), 5 warp-owned two-phase (64^3, 128^3), 6 split-y
 (128^3), 7 and 8 thread-per-pencil one- and two-plane (64^3), 12
-whole grid per block (16^3).  Odd batch
+whole grid per block (16^3), 13 thread-pair planes (80^3, 96^3).  Odd batch
 sizes leave a ragged tail of work items / clusters."""
 import numpy as np
 import pytest
@@ -18,6 +18,7 @@ FP32_TOL = 5e-6
 CASES = [(n, v) for n in (16, 32, 48, 64, 80, 96) for v in (0, 1)] + [(128, 0)]
 CASES += [(16, 3), (32, 3), (16, 12)]
 CASES += [(32, 4), (48, 4), (80, 4), (96, 4), (64, 5), (128, 5), (64, 7), (64, 8), (128, 6)]
+CASES += [(80, 13), (96, 13)]
 
 
 @pytest.mark.parametrize("n,variant", CASES)
@@ -40,13 +41,14 @@ def test_variant_matches_oracle(cuda, monkeypatch, n, variant):
             assert oracle.rel_l2(yc[b], ref[b]) <= FP32_TOL
 
 
-@pytest.mark.parametrize("n,variant", [(16, 3), (32, 3), (16, 12), (64, 7), (64, 8), (128, 6)])
+@pytest.mark.parametrize("n,variant", [(16, 3), (32, 3), (16, 12), (64, 7), (64, 8), (128, 6),
+                                       (80, 13), (96, 13)])
 def test_variant_in_place_and_many_grids(cuda, monkeypatch, n, variant):
     """More grids than blocks or clusters (every block goes many times round
     its tiles or loops over grids) and in == out."""
     from paper_2006_08435_gb300 import Plan
     monkeypatch.setenv("FFT3D_VARIANT", str(variant))
-    batch = {64: 200, 128: 40}.get(n, 700)
+    batch = {64: 200, 80: 100, 96: 60, 128: 40}.get(n, 700)
     x = torch.from_numpy(synth.uniform_grids(n, 1, seed=n)).cuda().repeat(batch, 1, 1, 1)
     x = (x * torch.arange(1, batch + 1, device="cuda").view(-1, 1, 1, 1)).contiguous()
     ref0 = oracle.dft3d(x[0].cpu().numpy().astype(np.complex128), -1)
@@ -82,8 +84,9 @@ def test_tensor_kernels_schedule_beyond_shared_table(cuda, monkeypatch, variant)
 
 
 @pytest.mark.parametrize("n,variant,precision,batch",
-                         [(64, 8, "fp32", 64), (128, 6, "fp32", 8),
-                          (64, 9, "split_fp16", 64), (128, 9, "split_fp16", 8)])
+                         [(64, 8, "fp32", 64), (128, 6, "fp32", 8), (96, 13, "fp32", 8),
+                          (80, 13, "fp32", 8), (64, 9, "split_fp16", 64),
+                          (128, 9, "split_fp16", 8)])
 def test_back_to_back_launches_stay_live(cuda, monkeypatch, n, variant, precision, batch):
     """Thousands of launches in a row of the kernels whose three tiles serve
     two compute groups in turn (a tile barrier per group and tile): no
