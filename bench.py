@@ -50,6 +50,8 @@ WORKLOADS = {
     "64x128": (64, 128),
     # the general path (edges without a fused kernel), for profiler captures
     "256x2": (256, 2),
+    # the thread-pair kernel (96^3), for profiler captures
+    "96x16": (96, 16),
 }
 METRIC = "batched 3D FFT transforms/s and % of HBM roofline at 64^3/128^3 (FP32 vs split-FP16)"
 # The sources each default FP32 kernel is built from (its own file and the
@@ -62,7 +64,8 @@ _COMMON_SOURCES = ["paper_2006_08435_gb300/csrc/persistent.cuh",
 KERNEL_SOURCES = {128: ["paper_2006_08435_gb300/csrc/splity.cuh"] + _COMMON_SOURCES,
                   64: ["paper_2006_08435_gb300/csrc/rowfft2.cuh"] + _COMMON_SOURCES}
 KERNEL_NAMES = {128: "splity_fft3d_kernel<128,-1>", 64: "rowfft2_fft3d_kernel<64,-1>",
-                256: "axis_pass_kernel<-1,2> (general path, three passes)"}
+                256: "axis_pass_kernel<-1,2> (general path, three passes)",
+                96: "pairfft_fft3d_kernel<96,-1>"}
 
 
 def dist_env():
