@@ -100,7 +100,8 @@ def test_per_edge_schedule_with_many_grids_per_edge(cuda, mixed_env):
     """One launch per edge (variant 1) when an edge has enough grids that its
     default kernel would be a tensor-map kernel (which needs one packed
     batch): the 64 grids of the mixed workload agree with the one-launch
-    schedule, and sampled grids with the oracle."""
+    schedule, and sampled grids with the oracle; calls with pointer arrays
+    (other kernels for those edges) agree with the packed ones."""
     from paper_2006_08435_gb300 import MixedPlan
     sizes = synth.mixed_sizes(64, seed=0) + [64] * 16
     grids, packed = _packed(sizes, seed=8)
@@ -117,6 +118,19 @@ def test_per_edge_schedule_with_many_grids_per_edge(cuda, mixed_env):
     assert oracle.rel_l2(outs[1].cpu().numpy(), outs[0].cpu().numpy()) <= FP32_TOL
     # the same kernels on the same grids, concurrently: the same bits
     assert torch.equal(outs[2], outs[1])
+    # pointer arrays: the edges whose packed units use per-grid tensor maps
+    # (128^3 split-y, 96^3 / 80^3 thread pairs) run kernels that address
+    # grids through pointers instead; every grid agrees with the packed call
+    ins = [packed[p.offsets[i]:p.offsets[i + 1]].clone() for i in range(len(sizes))]
+    res = [torch.empty_like(t) for t in ins]
+    ip = torch.tensor([t.data_ptr() for t in ins], dtype=torch.int64, device="cuda")
+    op = torch.tensor([t.data_ptr() for t in res], dtype=torch.int64, device="cuda")
+    p.execute_ptrs(ip, op)
+    torch.cuda.synchronize()
+    assert p.device_status() == 0
+    for i in range(len(sizes)):
+        seg = outs[2][p.offsets[i]:p.offsets[i + 1]]
+        assert oracle.rel_l2(res[i].cpu().numpy(), seg.cpu().numpy()) <= FP32_TOL, i
     yc = outs[1].cpu().numpy()
     for i in (sizes.index(128), len(sizes) - 1):
         n = sizes[i]
