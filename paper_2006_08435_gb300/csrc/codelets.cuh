@@ -3,7 +3,7 @@
 //
 // DFT<R, DIR>::run(v) replaces v[0..R) by X[k] = sum_n v[n] W_R^(n k),
 // W_R = exp(DIR * 2 pi i / R), natural order in and out, R in
-// {1,2,3,4,5,6,8,9,10,12,15,16,32,40,48,64}.  Radices 2, 3, 4, 5 are written out;
+// {1,2,3,4,5,6,8,9,10,12,15,16,24,32,40,48,64}.  Radices 2, 3, 4, 5 are written out;
 // composite R = R1*R2 is the four-step split
 //   a[n1][k2] = DFT_R2 over n2 of v[n1 + R1 n2],   a[n1][k2] *= W_R^(n1 k2),
 //   X[k2 + R2 k1] = DFT_R1 over n1 of a[n1][k2],
@@ -151,14 +151,14 @@ FFT3D_HD float2 twc(float2 a) {
 
 // ------------------------------------------------------------------ codelets
 __host__ __device__ constexpr int first_factor(int R) {
-  return R == 64 ? 8 : R == 48 ? 4 : R == 40 ? 8 : R == 32 ? 4 : R == 16 ? 4 : R == 12 ? 4
-         : R % 2 == 0 ? 2 : R % 3 == 0 ? 3 : R;
+  return R == 64 ? 8 : R == 48 ? 4 : R == 40 ? 8 : R == 32 ? 4 : R == 24 ? 8 : R == 16 ? 4
+         : R == 12 ? 4 : R % 2 == 0 ? 2 : R % 3 == 0 ? 3 : R;
 }
 
 template <int R, int DIR>
 struct DFT {
   static_assert(R == 6 || R == 8 || R == 9 || R == 10 || R == 12 || R == 15 || R == 16 ||
-                    R == 32 || R == 40 || R == 48 || R == 64,
+                    R == 24 || R == 32 || R == 40 || R == 48 || R == 64,
                 "unsupported codelet radix");
   static constexpr int R1 = first_factor(R);
   static constexpr int R2 = R / R1;

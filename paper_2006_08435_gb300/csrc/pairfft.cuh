@@ -1,17 +1,17 @@
-// Persistent 3D FFT kernel for 80^3 and 96^3 grids with every 1D transform
+// Persistent 3D FFT kernel for 48^3, 80^3 and 96^3 grids with every 1D transform
 // of n points in a pair of threads: thread p of the pair holds the points
 // p + 2 m (m < h = n/2), runs the h-point DFT of them in registers (E for
 // p = 0, O for p = 1), and the pair finishes with one radix-2 step,
 //   X[k] = E[k] + W_n^k O[k],  X[k + h] = E[k] - W_n^k O[k],
 // after exchanging half of their values with warp shuffles (the thread pair
-// of the split-y kernel, for h = 48 and 40).  A whole n-point pencil in one
-// thread would need 2n registers for its points alone.
+// of the split-y kernel, for h = 24, 40 and 48).  A whole n-point pencil in
+// one thread would need 2n registers for its points alone.
 //
 // Items are those of the thread-per-pencil kernels: a plane (x, then y, the
 // y results straight to global memory as rows of the intermediate, kept in
 // L2) and a slab (row y of every z: the z transforms, to the output).  A
-// plane is 50 KB (80^3) or 72 KB (96^3) and arrives as n/16 tensor boxes of
-// 16 complex x n rows, 128-byte swizzled.  Lanes:
+// plane is 18 KB (48^3), 50 KB (80^3) or 72 KB (96^3) and arrives as n/16
+// tensor boxes of 16 complex x n rows, 128-byte swizzled.  Lanes:
 //   x: row r = gt / 2, p = gt % 2 (adjacent lanes);
 //   y and z: column c = 16 w + lane % 16 of warp w of the group,
 //     p = lane / 16 (lanes l and l ^ 16), so that a half-warp reads or
@@ -20,8 +20,9 @@
 //
 // Block: two compute groups of 2n threads (items k = g, g + 2, ...), a
 // producer warp (tickets, slab dependencies, the item's tensor copies into
-// a ring of three tiles; full barriers per (group, tile), as in the split-y
-// kernel) and a signaller warp (frees tiles, publishes finished planes).
+// a ring of three tiles, seven at 48^3; full barriers per (group, tile), as
+// in the split-y kernel) and a signaller warp (frees tiles, publishes
+// finished planes).
 // Bounded waits as in the other persistent kernels.  In place is safe by
 // construction: a plane item writes only the plane it read, a slab only its
 // own row of every z.
@@ -48,7 +49,7 @@ using sy::sts4;
 
 template <int N>
 struct Cfg {
-  static_assert(N == 80 || N == 96, "thread-pair kernel covers 80 and 96");
+  static_assert(N == 48 || N == 80 || N == 96, "thread-pair kernel covers 48, 80 and 96");
   static constexpr int H = N / 2;               // points per thread
   static constexpr int Q = H / 2;               // outputs of each half per thread
   static_assert(Q % 2 == 0, "outputs handed over two at a time");
@@ -57,7 +58,7 @@ struct Cfg {
   static constexpr int REGION = N * 128;        // bytes of one box
   static constexpr int TILE = NSEG * REGION;    // bytes of one item (a plane or slab)
   static_assert(REGION % 1024 == 0, "boxes 1024-byte aligned (swizzle)");
-  static constexpr int NTILE = 3;
+  static constexpr int NTILE = N == 48 ? 7 : 3;  // odd: coprime with the two groups
   static constexpr int GROUPS = 2;
   static constexpr int GT = 2 * N;              // threads per compute group
   static constexpr int GW = GT / 32;

@@ -198,9 +198,7 @@ std::vector<int> variant_candidates(bool mixed, int n, int precision) {
     case 32: return {0, 1, 3, 4, kGeneralVariant};
     case 64: return {0, 1, 5, 7, 8, kGeneralVariant};
     case 128: return {0, 5, 6, kGeneralVariant};
-    case 80:
-    case 96: return {0, 1, 4, kGeneralVariant, 13};
-    default: return {0, 1, 4, kGeneralVariant};  // 48
+    default: return {0, 1, 4, kGeneralVariant, 13};  // 48, 80, 96
   }
 }
 
@@ -208,7 +206,8 @@ std::vector<int> variant_candidates(bool mixed, int n, int precision) {
 // (back-to-back executes; one grid also with L2 flushed):
 //   16^3: plain persistent for one grid, whole grid per block from 2;
 //   32^3: plain persistent below 64 grids, cluster-fused from 64;
-//   48^3: plain persistent;  80^3: plain persistent for one grid, the
+//   48^3: plain persistent below 32 grids, thread pairs from 32;  80^3:
+//     plain persistent for one grid, the
 //     double-buffered persistent kernel from 4, the thread-pair kernel from
 //     8;  96^3: plain persistent below 4 grids, the thread-pair kernel from 4;
 //   64^3: warp-owned for one grid, the persistent kernel with twice the
@@ -238,8 +237,11 @@ int builtin_default_variant(bool mixed, int n, int batch, int precision) {
     // plain persistent one
     case 80: return batch >= 8 ? 13 : batch >= 4 ? 4 : 0;
     case 96: return batch >= 4 ? 13 : 0;
+    // 48^3: 18 KB planes; the thread-pair kernel from 32 grids (x 64: 0.35
+    // against 0.28; x 256: 0.38 against 0.30), the plain kernel below
+    case 48: return batch >= 32 ? 13 : 0;
     case 128: return batch == 1 ? 5 : 6;
-    default: return 0;  // 48
+    default: return 0;
   }
 }
 
