@@ -19,7 +19,8 @@ FP16, split FP8, FP8 on the same batch), real_r2c_fp32 / real_c2r_fp32 (real gri
 real_16cubed_fp32 (16^3 x 16384 real grids), w64x256 (64^3 x 256 in FP32 and
 split FP16), mixed_c2 (64 mixed-edge grids, forward + inverse in one CUDA
 graph), general_path (256^3 and a non-cubic batch on the per-axis passes), hartree
-(energy + gradient of real densities, the differentiation workload)
+(energy + gradient of real densities, the differentiation workload; one
+density also replayed from a captured CUDA graph)
 and batch1 (one grid per launch, L2 flushed, the paper's setting).
 
 Under torchrun each rank transforms its own batch (weak scaling, no
@@ -548,6 +549,25 @@ def run_ours(args, ws, rank, local):
                 "value": whole_job_rate(ws, hb, 1, msh), "unit": "densities/s (energy + gradient)",
                 "steps": kh, "ms_per_step": msh, "bytes_per_density": hbytes,
                 "roofline_frac": hbytes * hb / (msh / 1e3) / 1e9 / peak}
+            if hb == 1:
+                # one density is bound by the host (autograd and the binding's
+                # calls take longer than the GPU work): the same step captured
+                # once in a CUDA graph (forward, energy, backward) and replayed
+                graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(graph, stream=stream):
+                    step()
+                with torch.cuda.stream(stream):  # replays launch on the current stream
+                    for _ in range(3):
+                        graph.replay()
+                barrier()
+                with torch.cuda.stream(stream):
+                    msg = timed_ms(graph.replay, kh, stream)
+                msg = max_over_ranks(msg, ws, dev)
+                hartree["batch1_graph"] = {
+                    "value": whole_job_rate(ws, 1, 1, msg), "unit": "densities/s (energy + gradient)",
+                    "steps": kh, "ms_per_step": msg, "bytes_per_density": hbytes,
+                    "roofline_frac": hbytes / (msg / 1e3) / 1e9 / peak}
+                del graph
             del rho
 
     # the general path (any edge up to 512, non-cubic grids): 256^3 x 4 and
