@@ -553,15 +553,23 @@ def run_ours(args, ws, rank, local):
                 # one density is bound by the host (autograd and the binding's
                 # calls take longer than the GPU work): the same step captured
                 # once in a CUDA graph (forward, energy, backward) and replayed
+                # (captured on a side stream, whose plans and workspaces the
+                # warm-up steps create: plans are kept per stream)
+                gs = torch.cuda.Stream()
+                gs.wait_stream(stream)
+                with torch.cuda.stream(gs):
+                    for _ in range(3):
+                        step()
                 graph = torch.cuda.CUDAGraph()
-                with torch.cuda.graph(graph, stream=stream):
+                with torch.cuda.graph(graph, stream=gs):
                     step()
-                with torch.cuda.stream(stream):  # replays launch on the current stream
+                with torch.cuda.stream(gs):  # replays launch on the current stream
                     for _ in range(3):
                         graph.replay()
                 barrier()
-                with torch.cuda.stream(stream):
-                    msg = timed_ms(graph.replay, kh, stream)
+                with torch.cuda.stream(gs):
+                    msg = timed_ms(graph.replay, kh, gs)
+                stream.wait_stream(gs)
                 msg = max_over_ranks(msg, ws, dev)
                 hartree["batch1_graph"] = {
                     "value": whole_job_rate(ws, 1, 1, msg), "unit": "densities/s (energy + gradient)",
