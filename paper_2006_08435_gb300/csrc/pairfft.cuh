@@ -7,25 +7,26 @@
 // of the split-y kernel, for h = 24, 40 and 48).  A whole n-point pencil in
 // one thread would need 2n registers for its points alone.
 //
-// Items are those of the thread-per-pencil kernels: a plane (x, then y, the
-// y results straight to global memory as rows of the intermediate, kept in
-// L2) and a slab (row y of every z: the z transforms, to the output).  A
-// plane is 18 KB (48^3), 50 KB (80^3) or 72 KB (96^3) and arrives as n/16
-// tensor boxes of 16 complex x n rows, 128-byte swizzled.  Lanes:
+// Items are those of the thread-per-pencil kernels: P planes (x, then y,
+// the y results straight to global memory as rows of the intermediate, kept
+// in L2) or P slabs (rows y of every z: the z transforms, to the output);
+// P = 2 at 48^3 (36 KB items), 1 at 80^3 and 96^3 (50 and 72 KB).  An item
+// arrives as n/16 tensor boxes of 16 complex x n rows x P, 128-byte
+// swizzled; tile row r is n pz + y for planes, P z + y for slabs.  Lanes:
 //   x: row r = gt / 2, p = gt % 2 (adjacent lanes);
-//   y and z: column c = 16 w + lane % 16 of warp w of the group,
-//     p = lane / 16 (lanes l and l ^ 16), so that a half-warp reads or
-//     writes 16 consecutive complex (128 bytes).
+//   y and z: plane (slab) w / (n/16), column c = 16 (w mod n/16) + lane % 16
+//     of warp w of the group, p = lane / 16 (lanes l and l ^ 16), so that a
+//     half-warp reads or writes 16 consecutive complex (128 bytes).
 // Every shared-memory access moves its bytes in the fewest wavefronts.
 //
-// Block: two compute groups of 2n threads (items k = g, g + 2, ...), a
+// Block: two compute groups of 2 P n threads (items k = g, g + 2, ...), a
 // producer warp (tickets, slab dependencies, the item's tensor copies into
-// a ring of three tiles, seven at 48^3; full barriers per (group, tile), as
+// a ring of three tiles, five at 48^3; full barriers per (group, tile), as
 // in the split-y kernel) and a signaller warp (frees tiles, publishes
 // finished planes).
 // Bounded waits as in the other persistent kernels.  In place is safe by
-// construction: a plane item writes only the plane it read, a slab only its
-// own row of every z.
+// construction: a plane item writes only the planes it read, a slab only its
+// own rows of every z.
 #pragma once
 
 #include "splity.cuh"
@@ -53,18 +54,20 @@ struct Cfg {
   static constexpr int H = N / 2;               // points per thread
   static constexpr int Q = H / 2;               // outputs of each half per thread
   static_assert(Q % 2 == 0, "outputs handed over two at a time");
+  static constexpr int P = N == 48 ? 2 : 1;     // planes (slabs) per item
+  static constexpr int ROWS = P * N;            // tile rows of an item
   static constexpr int SEG = 16;                // complex per 128-byte box row
   static constexpr int NSEG = N / SEG;          // tensor boxes per item
-  static constexpr int REGION = N * 128;        // bytes of one box
-  static constexpr int TILE = NSEG * REGION;    // bytes of one item (a plane or slab)
+  static constexpr int REGION = ROWS * 128;     // bytes of one box
+  static constexpr int TILE = NSEG * REGION;    // bytes of one item
   static_assert(REGION % 1024 == 0, "boxes 1024-byte aligned (swizzle)");
-  static constexpr int NTILE = N == 48 ? 7 : 3;  // odd: coprime with the two groups
+  static constexpr int NTILE = N == 48 ? 5 : 3;  // odd: coprime with the two groups
   static constexpr int GROUPS = 2;
-  static constexpr int GT = 2 * N;              // threads per compute group
+  static constexpr int GT = 2 * ROWS;           // threads per compute group
   static constexpr int GW = GT / 32;
   static constexpr int NCW = GROUPS * GW;       // compute warps
   static constexpr int T = 32 * (NCW + 2);      // plus producer and signaller
-  static constexpr int ITEMS = N;               // items per phase of a grid
+  static constexpr int ITEMS = N / P;           // items per phase of a grid
   static constexpr int SCHED = 4096;            // schedule blocks kept in shared memory
   static constexpr int NFULL = NTILE * GROUPS;  // full barriers, one per (group, tile)
   // barriers: full (NFULL), empty, freed (NTILE each), tr (GROUPS)
@@ -206,12 +209,12 @@ __device__ __forceinline__ void producer(const FusedArgs& a, const CUtensorMap* 
       if (d.phase == 1) asm volatile("fence.proxy.async.global;" ::: "memory");
       const uint32_t dst = tiles + (uint32_t)(s * K::TILE + lane * K::REGION);
       const int zb = PER_GRID ? 0 : d.grid * N;
-      if (d.phase == 0)  // plane z = idx: box {16 x, all y} at z
-        tma_box_hint(dst, PER_GRID ? tins + d.grid : tins, 2 * K::SEG * lane, 0, zb + d.idx, fb,
-                     once);
-      else  // slab y = idx: box {16 x, all z} at y
-        tma_box_hint(dst, PER_GRID ? touts + d.grid : touts, 2 * K::SEG * lane, d.idx, zb, fb,
-                     once);
+      if (d.phase == 0)  // planes z = P idx ..: box {16 x, all y, P z}
+        tma_box_hint(dst, PER_GRID ? tins + d.grid : tins, 2 * K::SEG * lane, 0,
+                     zb + K::P * d.idx, fb, once);
+      else  // slabs y = P idx ..: box {16 x, P y, all z}
+        tma_box_hint(dst, PER_GRID ? touts + d.grid : touts, 2 * K::SEG * lane, K::P * d.idx, zb,
+                     fb, once);
     }
     live |= 1u << s;
   }
@@ -294,7 +297,9 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
   // compute group g (warps g GW .. g GW + GW - 1), thread gt of 2n
   const int g = w / K::GW, wl = w - g * K::GW, gt = threadIdx.x - g * K::GT;
   const int lane = threadIdx.x & 31;
-  const int cy = 16 * wl + (lane & 15), py = lane >> 4;  // column passes
+  // column passes: plane (slab) qy of the item, column cy
+  const int qy = K::P == 1 ? 0 : wl / (N / 16);
+  const int cy = 16 * (K::P == 1 ? wl : wl % (N / 16)) + (lane & 15), py = lane >> 4;
   unsigned planes = 0;  // plane items of this group (parity of its barrier)
   for (int k = g;; k += K::GROUPS) {
     const int s = k % NT;
@@ -311,9 +316,9 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
     // The passes of the item (plane: x, then y; slab: z) share one copy of
     // the h-point DFT and of the pair step:
     //   x: row r = gt / 2, points p + 2 m, back into the tile;
-    //   y: column cy of the plane, rows py + 2 m, to rows of the
+    //   y: column cy of plane qy, rows py + 2 m, to rows of the
     //      intermediate (kept in L2 for its slabs);
-    //   z: column cy of slab y = idx, planes py + 2 m, to the output.
+    //   z: column cy of slab qy, planes py + 2 m, to the output.
     const int npass = d.phase == 0 ? 2 : 1;
     bool fail = false;
 #pragma unroll 1
@@ -324,9 +329,12 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
         const int r = gt >> 1;
 #pragma unroll
         for (int j = 0; j < H; ++j) v[j] = lds2(t + off<N>(r, p + 2 * j));
+      } else if (kind == 1) {
+#pragma unroll
+        for (int j = 0; j < H; ++j) v[j] = lds2(t + off<N>(qy * N + py + 2 * j, cy));
       } else {
 #pragma unroll
-        for (int j = 0; j < H; ++j) v[j] = lds2(t + off<N>(py + 2 * j, cy));
+        for (int j = 0; j < H; ++j) v[j] = lds2(t + off<N>((py + 2 * j) * K::P + qy, cy));
       }
       DFT<H, DIR>::run(v);
       pf::pair_radix2<N, DIR>(v, p, kind == 0 ? 1 : 16);
@@ -348,9 +356,9 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
         }
         ++planes;
       } else if (kind == 1) {
-        // rows k = j + Q py (and + h) of plane idx of the intermediate
+        // rows k = j + Q py (and + h) of plane P idx + qy of the intermediate
         const unsigned long long keep = policy_evict_last();
-        float2* dst = gout + (long long)d.idx * NN + (long long)(Q * py) * N + cy;
+        float2* dst = gout + (long long)(K::P * d.idx + qy) * NN + (long long)(Q * py) * N + cy;
 #pragma unroll
         for (int j = 0; j < Q; ++j) {
           asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(dst + (long long)j * N),
@@ -361,8 +369,8 @@ __global__ void __launch_bounds__(Cfg<N>::T, 1)
                        : "memory");
         }
       } else {
-        // planes k = j + Q py (and + h) of row y = idx, column cy
-        float2* dst = gout + (long long)d.idx * N + cy + (long long)(Q * py) * NN;
+        // planes k = j + Q py (and + h) of row y = P idx + qy, column cy
+        float2* dst = gout + (long long)(K::P * d.idx + qy) * N + cy + (long long)(Q * py) * NN;
         const float sc = a.do_scale ? a.scale : 1.0f;
 #pragma unroll
         for (int j = 0; j < Q; ++j) {
@@ -382,8 +390,8 @@ template <int N, int DIR>
 cudaError_t launch(const FusedArgs& a, int grid, cudaStream_t stream) {
   if (a.in_ptrs || a.grid_map || a.grid_off) return cudaErrorInvalidValue;
   rowk::TensorMaps<1> m;
-  if (!rowk::encode_map(&m.in[0], a.in, N, a.ngrids, N, 1) ||
-      !rowk::encode_map(&m.out[0], a.out, N, a.ngrids, 1, N))
+  if (!rowk::encode_map(&m.in[0], a.in, N, a.ngrids, N, Cfg<N>::P) ||
+      !rowk::encode_map(&m.out[0], a.out, N, a.ngrids, Cfg<N>::P, N))
     return cudaErrorInvalidValue;
   pairfft_fft3d_kernel<N, DIR, 1><<<grid, Cfg<N>::T, Cfg<N>::smem, stream>>>(a, m);
   return cudaGetLastError();
@@ -398,8 +406,8 @@ cudaError_t launch_maps(const FusedArgs& a, const long long* host_off, int grid,
   if (a.in_ptrs || a.ngrids > kMixMaps) return cudaErrorInvalidValue;
   rowk::TensorMaps<kMixMaps> m;
   for (int l = 0; l < a.ngrids; ++l)
-    if (!rowk::encode_map(&m.in[l], a.in + host_off[l], N, 1, N, 1) ||
-        !rowk::encode_map(&m.out[l], a.out + host_off[l], N, 1, 1, N))
+    if (!rowk::encode_map(&m.in[l], a.in + host_off[l], N, 1, N, Cfg<N>::P) ||
+        !rowk::encode_map(&m.out[l], a.out + host_off[l], N, 1, Cfg<N>::P, N))
       return cudaErrorInvalidValue;
   pairfft_fft3d_kernel<N, DIR, kMixMaps><<<grid, Cfg<N>::T, Cfg<N>::smem, stream>>>(a, m);
   return cudaGetLastError();

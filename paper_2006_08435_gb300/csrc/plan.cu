@@ -237,8 +237,9 @@ int builtin_default_variant(bool mixed, int n, int batch, int precision) {
     // plain persistent one
     case 80: return batch >= 8 ? 13 : batch >= 4 ? 4 : 0;
     case 96: return batch >= 4 ? 13 : 0;
-    // 48^3: 18 KB planes; the thread-pair kernel from 32 grids (x 64: 0.35
-    // against 0.28; x 256: 0.38 against 0.30), the plain kernel below
+    // 48^3: the thread-pair kernel (two-plane items of 36 KB) from 32 grids
+    // (x 64: 0.39 against 0.28; x 256: 0.52 against 0.30), the plain kernel
+    // below
     case 48: return batch >= 32 ? 13 : 0;
     case 128: return batch == 1 ? 5 : 6;
     default: return 0;
