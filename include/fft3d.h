@@ -276,9 +276,9 @@ int fft3d_selftest_wait_timeout(int64_t timeout_ns);
  * tensor TMA; 64^3), 8 the same with two-plane items and a register split
  * (64^3); for 128^3, 6 is the split-y kernel (64 KB items: half-planes and
  * quarter-slabs, 128-point FFTs by thread pairs); 13 the thread-pair plane
- * kernel (48^3, 80^3, 96^3: whole planes and slabs by tensor TMA, every
+ * kernel (32^3 .. 96^3: whole planes and slabs by tensor TMA, every
  * n-point pencil in a pair of threads).  The tensor-TMA variants (64^3: 7,
- * 8; 128^3: 6; 48^3, 80^3, 96^3: 13) need packed, 16-byte aligned buffers of one
+ * 8; 128^3: 6; 32^3, 48^3, 80^3, 96^3: 13) need packed, 16-byte aligned buffers of one
  * batch (they encode tensor maps of `in` and `out` at each execute).
  * Tensor-core precision plans (64^3, 128^3): 0 the plain persistent kernel
  * (mma.sync radix-16 stage), 9 the tensor-TMA items with tcgen05 products,
@@ -294,9 +294,9 @@ int fft3d_selftest_wait_timeout(int64_t timeout_ns);
  * where a plane of at least 4096 points fits shared memory, x and y run as
  * one plane pass (two launches per chunk instead of three).  Mixed plans:
  * 0 one launch of the mixed-edge kernel, 1 one launch per distinct edge (the
- * tensor-TMA kernels of 128^3 and 48^3 / 80^3 / 96^3 take one pair of
+ * tensor-TMA kernels of 128^3 and 32^3 .. 96^3 take one pair of
  * tensor maps per grid, up to 32 grids of an edge; an edge whose default is
- * a tensor-TMA kernel otherwise takes variant 0 at 48^3, 64^3, 80^3 and 96^3
+ * a tensor-TMA kernel otherwise takes variant 0 at 32^3 .. 96^3
  * (4 at 80^3 from 4 grids) and 5 at 128^3, as do calls with pointer
  * arrays), 2 the
  * launches of 1 as concurrent branches: the plan's own side streams, one

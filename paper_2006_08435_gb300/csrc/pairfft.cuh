@@ -1,16 +1,17 @@
-// Persistent 3D FFT kernel for 48^3, 80^3 and 96^3 grids with every 1D transform
+// Persistent 3D FFT kernel for 32^3 .. 96^3 grids with every 1D transform
 // of n points in a pair of threads: thread p of the pair holds the points
 // p + 2 m (m < h = n/2), runs the h-point DFT of them in registers (E for
 // p = 0, O for p = 1), and the pair finishes with one radix-2 step,
 //   X[k] = E[k] + W_n^k O[k],  X[k + h] = E[k] - W_n^k O[k],
 // after exchanging half of their values with warp shuffles (the thread pair
-// of the split-y kernel, for h = 24, 40 and 48).  A whole n-point pencil in
-// one thread would need 2n registers for its points alone.
+// of the split-y kernel, for h = 16, 24, 40 and 48).  A whole n-point pencil
+// in one thread would need 2n registers for its points alone.
 //
 // Items are those of the thread-per-pencil kernels: P planes (x, then y,
 // the y results straight to global memory as rows of the intermediate, kept
 // in L2) or P slabs (rows y of every z: the z transforms, to the output);
-// P = 2 at 48^3 (36 KB items), 1 at 80^3 and 96^3 (50 and 72 KB).  An item
+// P = 4 at 32^3 (32 KB items), 2 at 48^3 (36 KB), 1 at 80^3 and 96^3 (50
+// and 72 KB).  An item
 // arrives as n/16 tensor boxes of 16 complex x n rows x P, 128-byte
 // swizzled; tile row r is n pz + y for planes, P z + y for slabs.  Lanes:
 //   x: row r = gt / 2, p = gt % 2 (adjacent lanes);
@@ -21,7 +22,7 @@
 //
 // Block: two compute groups of 2 P n threads (items k = g, g + 2, ...), a
 // producer warp (tickets, slab dependencies, the item's tensor copies into
-// a ring of three tiles, five at 48^3; full barriers per (group, tile), as
+// a ring of three tiles, five at 32^3 and 48^3; full barriers per (group, tile), as
 // in the split-y kernel) and a signaller warp (frees tiles, publishes
 // finished planes).
 // Bounded waits as in the other persistent kernels.  In place is safe by
@@ -50,18 +51,19 @@ using sy::sts4;
 
 template <int N>
 struct Cfg {
-  static_assert(N == 48 || N == 80 || N == 96, "thread-pair kernel covers 48, 80 and 96");
+  static_assert(N == 32 || N == 48 || N == 80 || N == 96,
+                "thread-pair kernel covers 32, 48, 80 and 96");
   static constexpr int H = N / 2;               // points per thread
   static constexpr int Q = H / 2;               // outputs of each half per thread
   static_assert(Q % 2 == 0, "outputs handed over two at a time");
-  static constexpr int P = N == 48 ? 2 : 1;     // planes (slabs) per item
+  static constexpr int P = N == 32 ? 4 : N == 48 ? 2 : 1;  // planes (slabs) per item
   static constexpr int ROWS = P * N;            // tile rows of an item
   static constexpr int SEG = 16;                // complex per 128-byte box row
   static constexpr int NSEG = N / SEG;          // tensor boxes per item
   static constexpr int REGION = ROWS * 128;     // bytes of one box
   static constexpr int TILE = NSEG * REGION;    // bytes of one item
   static_assert(REGION % 1024 == 0, "boxes 1024-byte aligned (swizzle)");
-  static constexpr int NTILE = N == 48 ? 5 : 3;  // odd: coprime with the two groups
+  static constexpr int NTILE = N <= 48 ? 5 : 3;  // odd: coprime with the two groups
   static constexpr int GROUPS = 2;
   static constexpr int GT = 2 * ROWS;           // threads per compute group
   static constexpr int GW = GT / 32;

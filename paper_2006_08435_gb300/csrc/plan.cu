@@ -195,7 +195,7 @@ std::vector<int> variant_candidates(bool mixed, int n, int precision) {
   if (!fused_size(n)) return {kGeneralVariant};
   switch (n) {
     case 16: return {0, 1, 3, kGeneralVariant, 12};
-    case 32: return {0, 1, 3, 4, kGeneralVariant};
+    case 32: return {0, 1, 3, 4, kGeneralVariant, 13};
     case 64: return {0, 1, 5, 7, 8, kGeneralVariant};
     case 128: return {0, 5, 6, kGeneralVariant};
     default: return {0, 1, 4, kGeneralVariant, 13};  // 48, 80, 96
@@ -205,7 +205,8 @@ std::vector<int> variant_candidates(bool mixed, int n, int precision) {
 // The fastest variant measured on the GB300 for each edge and batch
 // (back-to-back executes; one grid also with L2 flushed):
 //   16^3: plain persistent for one grid, whole grid per block from 2;
-//   32^3: plain persistent below 64 grids, cluster-fused from 64;
+//   32^3: plain persistent below 64 grids, cluster-fused from 64, thread
+//     pairs from 128;
 //   48^3: plain persistent below 32 grids, thread pairs from 32;  80^3:
 //     plain persistent for one grid, the
 //     double-buffered persistent kernel from 4, the thread-pair kernel from
@@ -229,7 +230,9 @@ int builtin_default_variant(bool mixed, int n, int batch, int precision) {
     // persistent kernel (L2 flushed: 11.9 us against 15.0 us, its grid
     // spread over 32 blocks instead of one)
     case 16: return batch >= 2 ? 12 : 0;
-    case 32: return batch >= 64 ? 3 : 0;
+    // 32^3: the thread-pair kernel (four-plane items of 32 KB) from 128
+    // grids (x 256: 0.46 against 0.33; x 1024: 0.51 against 0.38)
+    case 32: return batch >= 128 ? 13 : batch >= 64 ? 3 : 0;
     case 64: return batch == 1 ? 5 : batch < 16 ? 1 : batch < 64 ? 7 : 8;
     // 80^3, 96^3: the thread-pair kernel from 8 (80) and 4 (96) grids (x 256:
     // 0.57 / 0.62 of the roofline against 0.30 / 0.25; x 12-14: 0.41-0.43
@@ -827,7 +830,7 @@ int create_mixed(int count, const int* dims, int direction, int norm, int varian
       // thread-pair kernel (80^3, 96^3); for pointer arrays a kernel that
       // addresses grids through the plan's map
       const bool maps = (v == 6 || v == 13) && ng <= kMixMaps;
-      const int v_ptr = n == 128 ? 5 : (n == 80 && ng >= 4) ? 4 : 0;
+      const int v_ptr = n == 128 ? 5 : (n == 80 && ng >= 4) ? 4 : (n == 32 && ng >= 64) ? 3 : 0;
       if ((n == 64 && (v == 7 || v == 8)) || ((v == 6 || v == 13) && !maps)) v = n == 64 ? 0 : v_ptr;
       u.kernel = fused_kernel_info(n, direction, v);
       Unit w = u;
