@@ -165,11 +165,12 @@ def test_per_grid_tensor_maps_in_place_and_beyond_the_table(cuda, mixed_env):
     """One launch per edge on packed buffers: the 128^3 grids run the split-y
     kernel with one pair of tensor maps per grid, also in place (in == out)
     with distinct grids; with more 128^3 grids than one launch takes maps for
-    (33 > 32) the unit falls back to the warp-owned kernel.  Sampled grids
-    against the oracle, every grid back through the inverse."""
+    (33 > 32) the unit falls back to the warp-owned kernel; 96^3 and 80^3
+    grids (4 and 9 of them) run the thread-pair kernel with per-grid maps.
+    Sampled grids against the oracle, every grid back through the inverse."""
     from paper_2006_08435_gb300 import MixedPlan
     for variant, sizes in (("1", [128, 32, 128, 64, 128, 96, 128]), ("2", [128, 32, 128, 64, 128, 96, 128]),
-                           ("1", [32] + [128] * 33)):
+                           ("1", [32] + [128] * 33), ("2", [96, 48, 96, 96, 80, 96] + [80] * 8)):
         os.environ["FFT3D_MIXED_VARIANT"] = variant
         grids, packed = _packed(sizes, seed=len(sizes))
         fwd, inv = MixedPlan(sizes), MixedPlan(sizes, inverse=True)
@@ -178,8 +179,9 @@ def test_per_grid_tensor_maps_in_place_and_beyond_the_table(cuda, mixed_env):
         torch.cuda.synchronize()
         assert fwd.device_status() == 0
         xc = x.cpu().numpy()
-        idx = [i for i, n in enumerate(sizes) if n == 128]
-        for i in (idx[0], idx[-1], 0):
+        big = 128 if 128 in sizes else 96
+        idx = [i for i, n in enumerate(sizes) if n == big]
+        for i in (idx[0], idx[-1], 0, len(sizes) - 1):
             n = sizes[i]
             ref = oracle.dft3d(grids[i].astype(np.complex128), -1)
             assert oracle.rel_l2(xc[fwd.offsets[i]:fwd.offsets[i + 1]].reshape(n, n, n), ref) <= FP32_TOL

@@ -83,6 +83,27 @@ def test_tensor_kernels_schedule_beyond_shared_table(cuda, monkeypatch, variant)
     torch.cuda.empty_cache()
 
 
+def test_thread_pair_kernel_schedule_beyond_shared_table(cuda, monkeypatch):
+    """More schedule blocks (2 per grid) than the thread-pair kernel keeps in
+    shared memory (4096): 2100 grids of 32^3 (four-plane items), the
+    producer reads the schedule from global memory; three grids against the
+    oracle."""
+    from paper_2006_08435_gb300 import Plan
+    monkeypatch.setenv("FFT3D_VARIANT", "13")
+    n, batch = 32, 2100
+    base = torch.from_numpy(synth.uniform_grids(n, 1, seed=78)).cuda()
+    x = base.repeat(batch, 1, 1, 1)
+    x.mul_(torch.arange(1, batch + 1, device="cuda", dtype=torch.float32).view(-1, 1, 1, 1))
+    y = torch.empty_like(x)
+    p = Plan(n, n, n, batch)
+    assert p.variant == 13
+    p.execute(x, y)
+    assert p.device_status() == 0
+    ref0 = oracle.dft3d(base[0].cpu().numpy().astype(np.complex128), -1)
+    for b in (0, 1049, batch - 1):
+        assert oracle.rel_l2(y[b].cpu().numpy(), (b + 1) * ref0) <= FP32_TOL
+
+
 @pytest.mark.parametrize("n,variant,precision,batch",
                          [(64, 8, "fp32", 64), (128, 6, "fp32", 8), (96, 13, "fp32", 8),
                           (80, 13, "fp32", 8), (64, 9, "split_fp16", 64),
