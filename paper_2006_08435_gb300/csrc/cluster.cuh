@@ -1,4 +1,4 @@
-// Cluster-fused single-pass 3D FFT for small cubic grids (n <= 64).
+// Cluster-fused single-pass 3D FFT for small cubic grids (16^3, 32^3).
 //
 // The paper's design keeps the whole 3D FFT in the FPGA's local memory when
 // it fits, so the 3D transpose happens on chip (section "Approach").  Here a
@@ -10,8 +10,15 @@
 // The grid crosses HBM once in and once out; no block ever waits for
 // another cluster.  Clusters loop over the grids of the batch.
 //
-// Shapes: 16^3 in one block (C = 1), 32^3 over 4 blocks, 64^3 over 16
-// blocks (a non-portable cluster size, 166 KB of shared memory each).
+// Shapes: 16^3 over 8 blocks, 32^3 over 16 (a non-portable cluster size),
+// two planes per block: for the few grids this kernel serves (it is the
+// default below 64 grids at 16^3 and below 128 at 32^3), spreading a grid
+// over more multiprocessors cuts the x-y and z steps to a fraction, and
+// the cluster barrier between them costs less than the counters, memset
+// and inter-block waits of the persistent kernels (one grid with L2
+// flushed: 8.9 us at 16^3 against 11.9 us; 10.9 us at 32^3 against 11.9).
+// Narrower clusters (16^3 in one block, 32^3 over 4) were slower at every
+// batch.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -24,11 +31,14 @@ namespace clus {
 namespace cg = cooperative_groups;
 
 template <int N>
-constexpr int cluster_size() { return N == 16 ? 1 : N == 32 ? 4 : 16; }
+constexpr int cluster_size() {
+  static_assert(N == 16 || N == 32, "cluster-fused kernel covers 16^3 and 32^3");
+  return N == 16 ? 8 : 16;
+}
 
-template <int N>
+template <int N, int CS = cluster_size<N>()>
 struct Cfg {
-  static constexpr int C = cluster_size<N>();
+  static constexpr int C = CS;
   static constexpr int PL = N / C;        // planes (and slabs) per block
   static constexpr int P = N + 1;         // plane row pitch (complex)
   static constexpr int L1 = split_l1(N), L2 = split_l2(N);
@@ -39,7 +49,7 @@ struct Cfg {
 // In-place x then y transform of one n x n plane with row pitch P.
 template <int N, int DIR>
 __device__ __forceinline__ void plane_xy(float2* pl, const float2* tw) {
-  using K = Cfg<N>;
+  using K = Cfg<N>;  // (the pitch and the split do not depend on C)
   constexpr int L1 = K::L1, L2 = K::L2, P = K::P, T = K::T;
   const int tid = threadIdx.x;
   // x, first step (lanes walk rows; each item reads and writes its own points)
@@ -124,9 +134,9 @@ __device__ __forceinline__ void plane_xy(float2* pl, const float2* tw) {
   __syncthreads();
 }
 
-template <int N, int DIR>
-__global__ void __launch_bounds__(Cfg<N>::T) cluster_fft3d_kernel(const FusedArgs a) {
-  using K = Cfg<N>;
+template <int N, int DIR, int CS>
+__global__ void __launch_bounds__(Cfg<N, CS>::T) cluster_fft3d_kernel(const FusedArgs a) {
+  using K = Cfg<N, CS>;
   constexpr int L1 = K::L1, L2 = K::L2, P = K::P, T = K::T, PL = K::PL;
   constexpr long long NN = (long long)N * N;
   extern __shared__ __align__(16) float2 smem[];
@@ -189,9 +199,9 @@ __global__ void __launch_bounds__(Cfg<N>::T) cluster_fft3d_kernel(const FusedArg
   }
 }
 
-template <int N, int DIR>
+template <int N, int DIR, int CS>
 cudaError_t launch(const FusedArgs& a, int grid, cudaStream_t stream) {
-  using K = Cfg<N>;
+  using K = Cfg<N, CS>;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -204,20 +214,20 @@ cudaError_t launch(const FusedArgs& a, int grid, cudaStream_t stream) {
   cfg.stream = stream;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, cluster_fft3d_kernel<N, DIR>, a);
+  return cudaLaunchKernelEx(&cfg, cluster_fft3d_kernel<N, DIR, CS>, a);
 }
 
-template <int N, int DIR>
+template <int N, int DIR, int CS = cluster_size<N>()>
 KernelInfo info() {
   KernelInfo k;
-  k.launch = &launch<N, DIR>;
-  k.func = (const void*)&cluster_fft3d_kernel<N, DIR>;
-  k.threads = Cfg<N>::T;
-  k.smem = Cfg<N>::smem;
+  k.launch = &launch<N, DIR, CS>;
+  k.func = (const void*)&cluster_fft3d_kernel<N, DIR, CS>;
+  k.threads = Cfg<N, CS>::T;
+  k.smem = Cfg<N, CS>::smem;
   k.twiddle_entries = N;
   k.sizes[0] = N;
   k.nsizes = 1;
-  k.cluster = Cfg<N>::C;
+  k.cluster = Cfg<N, CS>::C;
   return k;
 }
 

@@ -204,9 +204,8 @@ std::vector<int> variant_candidates(bool mixed, int n, int precision) {
 
 // The fastest variant measured on the GB300 for each edge and batch
 // (back-to-back executes; one grid also with L2 flushed):
-//   16^3: plain persistent for one grid, whole grid per block from 2;
-//   32^3: plain persistent below 64 grids, cluster-fused from 64, thread
-//     pairs from 128;
+//   16^3: cluster-fused below 64 grids, whole grid per block from 64;
+//   32^3: cluster-fused below 128 grids, thread pairs from 128;
 //   48^3: plain persistent below 32 grids, thread pairs from 32;  80^3:
 //     plain persistent for one grid, the
 //     double-buffered persistent kernel from 4, the thread-pair kernel from
@@ -225,14 +224,16 @@ int builtin_default_variant(bool mixed, int n, int batch, int precision) {
   if (precision >= FFT3D_BFP16) return 9;
   if (precision != FFT3D_FP32) return (n == 64 && batch >= 16) || (n == 128 && batch >= 2) ? 9 : 0;
   switch (n) {
-    // 16^3: the whole-grid kernel from 2 grids (x 4096: 74 us against 111 us
-    // for the cluster kernel; 0.53 of the roofline); one grid: the
-    // persistent kernel (L2 flushed: 11.9 us against 15.0 us, its grid
-    // spread over 32 blocks instead of one)
-    case 16: return batch >= 2 ? 12 : 0;
-    // 32^3: the thread-pair kernel (four-plane items of 32 KB) from 128
-    // grids (x 256: 0.46 against 0.33; x 1024: 0.51 against 0.38)
-    case 32: return batch >= 128 ? 13 : batch >= 64 ? 3 : 0;
+    // 16^3: the cluster-fused kernel (8 blocks per grid) below 64 grids (one
+    // grid, L2 flushed: 8.9 us against 11.9 for the persistent kernel;
+    // 2-16 grids: 9.3-9.9 us against 11.2-11.7 for the whole-grid kernel),
+    // the whole-grid kernel from 64 (x 4096: 0.53 of the roofline)
+    case 16: return batch >= 64 ? 12 : 3;
+    // 32^3: the cluster-fused kernel (16 blocks per grid) below 128 grids
+    // (one grid, L2 flushed: 10.9 us against 11.9; 2-64 grids: 11.6-23.2 us
+    // against 13.0-26.6 for the persistent kernel), the thread-pair kernel
+    // (four-plane items of 32 KB) from 128 (x 256: 0.46; x 1024: 0.51)
+    case 32: return batch >= 128 ? 13 : 3;
     case 64: return batch == 1 ? 5 : batch < 16 ? 1 : batch < 64 ? 7 : 8;
     // 80^3, 96^3: the thread-pair kernel from 8 (80) and 4 (96) grids (x 256:
     // 0.57 / 0.62 of the roofline against 0.30 / 0.25; x 12-14: 0.41-0.43
@@ -830,7 +831,7 @@ int create_mixed(int count, const int* dims, int direction, int norm, int varian
       // thread-pair kernel (80^3, 96^3); for pointer arrays a kernel that
       // addresses grids through the plan's map
       const bool maps = (v == 6 || v == 13) && ng <= kMixMaps;
-      const int v_ptr = n == 128 ? 5 : (n == 80 && ng >= 4) ? 4 : (n == 32 && ng >= 64) ? 3 : 0;
+      const int v_ptr = n == 128 ? 5 : (n == 80 && ng >= 4) ? 4 : n == 32 ? 3 : 0;
       if ((n == 64 && (v == 7 || v == 8)) || ((v == 6 || v == 13) && !maps)) v = n == 64 ? 0 : v_ptr;
       u.kernel = fused_kernel_info(n, direction, v);
       Unit w = u;
