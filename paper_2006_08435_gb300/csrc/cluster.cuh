@@ -12,13 +12,14 @@
 //
 // Shapes: 16^3 over 8 blocks, 32^3 over 16 (a non-portable cluster size),
 // two planes per block: for the few grids this kernel serves (it is the
-// default below 64 grids at 16^3 and below 128 at 32^3), spreading a grid
+// default below 128 grids at 16^3 and 32^3), spreading a grid
 // over more multiprocessors cuts the x-y and z steps to a fraction, and
 // the cluster barrier between them costs less than the counters, memset
 // and inter-block waits of the persistent kernels (one grid with L2
 // flushed: 8.9 us at 16^3 against 11.9 us; 10.9 us at 32^3 against 11.9).
 // Narrower clusters (16^3 in one block, 32^3 over 4) were slower at every
-// batch.
+// batch; from 128 grids the whole-grid (16^3) and thread-pair (32^3)
+// kernels take over.
 #pragma once
 
 #include <cooperative_groups.h>

@@ -204,7 +204,7 @@ std::vector<int> variant_candidates(bool mixed, int n, int precision) {
 
 // The fastest variant measured on the GB300 for each edge and batch
 // (back-to-back executes; one grid also with L2 flushed):
-//   16^3: cluster-fused below 64 grids, whole grid per block from 64;
+//   16^3: cluster-fused below 128 grids, whole grid per block from 128;
 //   32^3: cluster-fused below 128 grids, thread pairs from 128;
 //   48^3: plain persistent below 32 grids, thread pairs from 32;  80^3:
 //     plain persistent for one grid, the
@@ -224,11 +224,12 @@ int builtin_default_variant(bool mixed, int n, int batch, int precision) {
   if (precision >= FFT3D_BFP16) return 9;
   if (precision != FFT3D_FP32) return (n == 64 && batch >= 16) || (n == 128 && batch >= 2) ? 9 : 0;
   switch (n) {
-    // 16^3: the cluster-fused kernel (8 blocks per grid) below 64 grids (one
+    // 16^3: the cluster-fused kernel (8 blocks per grid) below 128 grids (one
     // grid, L2 flushed: 8.9 us against 11.9 for the persistent kernel;
-    // 2-16 grids: 9.3-9.9 us against 11.2-11.7 for the whole-grid kernel),
-    // the whole-grid kernel from 64 (x 4096: 0.53 of the roofline)
-    case 16: return batch >= 64 ? 12 : 3;
+    // 2-64 grids: 8.3-9.9 us against 9.6-11.7 for the whole-grid kernel),
+    // the whole-grid kernel from 128 (x 256: 0.29 against 0.15; x 4096:
+    // 0.53 against 0.17)
+    case 16: return batch >= 128 ? 12 : 3;
     // 32^3: the cluster-fused kernel (16 blocks per grid) below 128 grids
     // (one grid, L2 flushed: 10.9 us against 11.9; 2-64 grids: 11.6-23.2 us
     // against 13.0-26.6 for the persistent kernel), the thread-pair kernel
