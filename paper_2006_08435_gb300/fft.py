@@ -21,10 +21,45 @@ _NORM = {"none": L.FFT3D_NORM_NONE, "n": L.FFT3D_NORM_BY_N, "by_n": L.FFT3D_NORM
          "ortho": L.FFT3D_NORM_ORTHO}
 
 
+# The current stream's raw handle and the current device, read without the
+# Stream object and device-index normalisation of torch.cuda.current_stream()
+# (a few microseconds of host time per call, several calls per transform);
+# the public calls where these accessors are missing.
+_raw_stream = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+_current_device = getattr(torch._C, "_cuda_getDevice", None)
+
+
+def _current_stream_handle(device_index: int | None = None) -> int:
+    """Raw handle of the current stream of `device_index` (default: the
+    current device)."""
+    if _raw_stream is not None and _current_device is not None:
+        return int(_raw_stream(_current_device() if device_index is None else device_index))
+    s = torch.cuda.current_stream() if device_index is None else torch.cuda.current_stream(device_index)
+    return int(s.cuda_stream)
+
+
 def _stream_handle(stream) -> int:
     if stream is None:
-        stream = torch.cuda.current_stream()
+        return _current_stream_handle()
     return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+class _on_device:
+    """Make `index` the current device for the block, switching only when
+    it is not already (the launches must be issued on the stream's device)."""
+
+    def __init__(self, index: int):
+        self.index, self.prev = index, None
+
+    def __enter__(self):
+        cur = _current_device() if _current_device is not None else torch.cuda.current_device()
+        if cur != self.index:
+            self.prev = cur
+            torch.cuda.set_device(self.index)
+
+    def __exit__(self, *exc):
+        if self.prev is not None:
+            torch.cuda.set_device(self.prev)
 
 
 def _check_tensor(t: torch.Tensor, name: str) -> None:
@@ -272,9 +307,10 @@ def fft3d(x: torch.Tensor, inverse: bool = False, norm: str = "none", precision:
         out = torch.empty_like(x)
     if batch == 0:
         return out
-    with torch.cuda.device(x.device):
-        stream = torch.cuda.current_stream()
-        plan = get_plan(nx, ny, nz, batch, precision, inverse, norm, x.device.index, stream)
+    dev = x.device.index
+    with _on_device(dev):
+        stream = _current_stream_handle(dev)
+        plan = get_plan(nx, ny, nz, batch, precision, inverse, norm, dev, stream)
         return plan.execute(x, out, stream)
 
 
@@ -318,9 +354,10 @@ def rfft3d(x: torch.Tensor, norm: str = "none", precision: str = "fp32",
         out = torch.empty(x.shape[:-1] + (n // 2 + 1,), dtype=torch.complex64, device=x.device)
     if batch == 0:
         return out
-    with torch.cuda.device(x.device):
-        stream = torch.cuda.current_stream()
-        p = _get_real_plan(n, batch, precision, False, norm, x.device.index, stream)
+    dev = x.device.index
+    with _on_device(dev):
+        stream = _current_stream_handle(dev)
+        p = _get_real_plan(n, batch, precision, False, norm, dev, stream)
         return p.execute(x, out, stream)
 
 
@@ -340,9 +377,10 @@ def irfft3d(x: torch.Tensor, norm: str = "none", precision: str = "fp32",
         out = torch.empty(x.shape[:-1] + (n,), dtype=torch.float32, device=x.device)
     if batch == 0:
         return out
-    with torch.cuda.device(x.device):
-        stream = torch.cuda.current_stream()
-        p = _get_real_plan(n, batch, precision, True, norm, x.device.index, stream)
+    dev = x.device.index
+    with _on_device(dev):
+        stream = _current_stream_handle(dev)
+        p = _get_real_plan(n, batch, precision, True, norm, dev, stream)
         return p.execute(x, out, stream)
 
 
