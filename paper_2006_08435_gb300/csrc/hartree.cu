@@ -23,6 +23,7 @@
 #include <cstdint>
 
 #include "fft3d.h"
+#include "internal.h"
 
 namespace fft3d {
 namespace {
@@ -42,62 +43,62 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// n / d for n < 2^32 with the multiplier and shift of make_fastdiv
+// (Granlund and Montgomery, 1994).
+__device__ __forceinline__ unsigned udiv(unsigned x, FastDiv d) {
+  return (unsigned)(((unsigned long long)__umulhi(x, d.mul) + x) >> d.shift);
+}
+
 // One row of blocks per grid (blockIdx.y).  partials: [batch][gridDim.x];
 // counters: [batch], zero on entry, left at zero by the last block, whose
 // threads sum the grid's partials together (one thread reading them one
 // after another took 38 us for the 512 partials of one 128^3 grid).
-// Each term |F(m)|^2 w / |m|^2 is formed in FP32 (the correctly rounded
-// reciprocal of |m|^2; relative error <= 4 2^-24; the spectrum itself is
-// FP32) and a lane's terms of R rows are summed in FP32 (at most 32
-// terms), then accumulated in FP64: FP64 work is a few operations per
-// hundred points, since FP64 runs at a small fraction of the FP32 rate on
-// this GPU (the per-point FP64 form ran at 0.39 TB/s).  Blocks: about 2048
-// in all, each warp R rows at a time (R independent loads per lane).
+// The spectrum is read as a flat array, U points per thread per step at a
+// grid stride (every warp load 256 consecutive bytes); a point's (kz, ky,
+// kx) come from its index by multiply-shift divisions by the row length
+// and by n.  (Rows of n/2 + 1 points taken one warp at a time left a
+// third pass over each row with one lane of 32 busy: 0.41 of the HBM
+// bandwidth at 32 grids of 128^3.)  Each term |F(m)|^2 w / |m|^2 is
+// formed in FP32 (the correctly rounded reciprocal of |m|^2; relative
+// error <= 4 2^-24; the spectrum itself is FP32) and a thread's U terms of
+// a step are summed in FP32, then accumulated in FP64: FP64 work is a few
+// operations per hundred points, since FP64 runs at a small fraction of the
+// FP32 rate on this GPU (the per-point FP64 form ran at 0.39 TB/s).
 template <bool HALF>
 __global__ void __launch_bounds__(kRedThreads) hartree_energy_kernel(
     const float2* __restrict__ f, int n, long long npts, double half_s,
-    double* __restrict__ partials, unsigned* __restrict__ counters, double* __restrict__ energy) {
+    double* __restrict__ partials, unsigned* __restrict__ counters, double* __restrict__ energy,
+    FastDiv div_h, FastDiv div_n) {
   const int b = blockIdx.y;
   const float2* fb = f + (long long)b * npts;
-  constexpr int W = kRedThreads / 32, R = 8;  // rows per step of a warp
-  const int h = HALF ? n / 2 + 1 : n, lane = threadIdx.x & 31, rows = n * n;
-  const int rstride = gridDim.x * W;
+  constexpr int W = kRedThreads / 32, U = 8;  // points per thread per step
+  const int h = HALF ? n / 2 + 1 : n;
+  const unsigned np = (unsigned)npts, stride = gridDim.x * kRedThreads;
   double acc = 0.0;
-  // a warp takes R rows at a time (R independent loads per lane per step);
-  // its lanes' FP32 sums of those rows go to the FP64 accumulator
-  for (int row0 = blockIdx.x * W + (threadIdx.x >> 5); row0 < rows; row0 += R * rstride) {
-    int myz[R];
-    const float2* fr[R];
+  for (unsigned i0 = blockIdx.x * kRedThreads + threadIdx.x; i0 < np; i0 += U * stride) {
+    float2 v[U];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int row = row0 + r * rstride < rows ? row0 + r * rstride : row0;
-      const int kz = row / n, ky = row - kz * n;
-      const int mz = signed_index(kz, n), my = signed_index(ky, n);
-      myz[r] = row0 + r * rstride < rows ? mz * mz + my * my : -1;  // -1: no such row
-      fr[r] = fb + (long long)row * h;
+    for (int u = 0; u < U; ++u) {
+      const unsigned i = i0 + u * stride;
+      v[u] = i < np ? __ldcs(fb + i) : make_float2(0.0f, 0.0f);
     }
     float part = 0.0f;
-    for (int kx = lane; kx < h; kx += 32) {
-      const int mx = signed_index(kx, n);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const unsigned i = i0 + u * stride;
+      const unsigned row = udiv(i, div_h), kz = udiv(row, div_n);
+      const int kx = (int)(i - row * h), ky = (int)(row - kz * n);
+      const int mx = signed_index(kx, n), my = signed_index(ky, n), mz = signed_index((int)kz, n);
+      const int m2 = mx * mx + my * my + mz * mz;
       const float w = HALF && kx != 0 && 2 * kx != n ? 2.0f : 1.0f;
-      float2 v[R];
-#pragma unroll
-      for (int r = 0; r < R; ++r) v[r] = myz[r] >= 0 ? __ldcs(fr[r] + kx) : make_float2(0.0f, 0.0f);
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int m2 = myz[r] + mx * mx;
-        if (m2 > 0) part = fmaf(fmaf(v[r].x, v[r].x, v[r].y * v[r].y), w * __frcp_rn((float)m2), part);
-      }
-      if ((kx >> 5) % 4 == 3) {  // long rows (h > 128): at most 32 terms per FP32 sum
-        acc += (double)part;
-        part = 0.0f;
-      }
+      if (i < np && m2 > 0)
+        part = fmaf(fmaf(v[u].x, v[u].x, v[u].y * v[u].y), w * __frcp_rn((float)m2), part);
     }
     acc += (double)part;
   }
+  acc = warp_sum(acc);
   __shared__ double warp_part[W];
   __shared__ int is_last;
-  acc = warp_sum(acc);
   if ((threadIdx.x & 31) == 0) warp_part[threadIdx.x >> 5] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -237,7 +238,8 @@ int energy_impl(const void* rhohat, int n, int batch, double L, double* energy, 
   }
   hartree_energy_kernel<HALF><<<dim3(blocks, batch), kRedThreads, 0, s>>>(
       static_cast<const float2*>(rhohat), n, npts, 0.5 * hartree_s(n, L),
-      reinterpret_cast<double*>(ws), counters, energy);
+      reinterpret_cast<double*>(ws), counters, energy,
+      make_fastdiv((unsigned)(HALF ? n / 2 + 1 : n)), make_fastdiv((unsigned)n));
   if (cudaGetLastError() != cudaSuccess) return FFT3D_ERR_CUDA;
   return FFT3D_SUCCESS;
 }
