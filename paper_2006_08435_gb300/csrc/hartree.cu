@@ -126,44 +126,40 @@ __global__ void __launch_bounds__(kRedThreads) hartree_energy_kernel(
   }
 }
 
+// The seed: the spectrum as a flat array, U points per thread per step at a
+// grid stride (coalesced loads and stores), indices as in the energy kernel.
 template <bool HALF>
 __global__ void __launch_bounds__(kRedThreads) hartree_seed_kernel(
     const float2* __restrict__ f, int n, long long npts, double s,
-    const double* __restrict__ grad_e, float2* __restrict__ seed) {
+    const double* __restrict__ grad_e, float2* __restrict__ seed, FastDiv div_h, FastDiv div_n) {
   const int b = blockIdx.y;
   const float scale = (float)(s * grad_e[b]);
   const float2* fb = f + (long long)b * npts;
   float2* sb = seed + (long long)b * npts;
-  constexpr int W = kRedThreads / 32, R = 4;  // rows per step of a warp
-  const int h = HALF ? n / 2 + 1 : n, lane = threadIdx.x & 31, rows = n * n;
-  const int rstride = gridDim.x * W;
-  for (int row0 = blockIdx.x * W + (threadIdx.x >> 5); row0 < rows; row0 += R * rstride) {
-    int myz[R];
-    long long off[R];
+  constexpr int U = 4;  // points per thread per step
+  const int h = HALF ? n / 2 + 1 : n;
+  const unsigned np = (unsigned)npts, stride = gridDim.x * kRedThreads;
+  for (unsigned i0 = blockIdx.x * kRedThreads + threadIdx.x; i0 < np; i0 += U * stride) {
+    float2 v[U];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int row = row0 + r * rstride < rows ? row0 + r * rstride : row0;
-      const int kz = row / n, ky = row - kz * n;
-      const int mz = signed_index(kz, n), my = signed_index(ky, n);
-      myz[r] = row0 + r * rstride < rows ? mz * mz + my * my : -1;  // -1: no such row
-      off[r] = (long long)row * h;
+    for (int u = 0; u < U; ++u) {
+      const unsigned i = i0 + u * stride;
+      v[u] = i < np ? __ldcs(fb + i) : make_float2(0.0f, 0.0f);
     }
-    for (int kx = lane; kx < h; kx += 32) {
-      const int mx = signed_index(kx, n);
-      float2 v[R];
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[r] = myz[r] >= 0 ? __ldcs(fb + off[r] + kx) : make_float2(0.0f, 0.0f);
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        if (myz[r] < 0) continue;
-        const int m2 = myz[r] + mx * mx;
-        float2 o = make_float2(0.0f, 0.0f);
-        if (m2 != 0) {
-          const float w = scale * __frcp_rn((float)m2);
-          o = make_float2(v[r].x * w, v[r].y * w);
-        }
-        __stcs(sb + off[r] + kx, o);
+    for (int u = 0; u < U; ++u) {
+      const unsigned i = i0 + u * stride;
+      if (i >= np) continue;
+      const unsigned row = udiv(i, div_h), kz = udiv(row, div_n);
+      const int kx = (int)(i - row * h), ky = (int)(row - kz * n);
+      const int mx = signed_index(kx, n), my = signed_index(ky, n), mz = signed_index((int)kz, n);
+      const int m2 = mx * mx + my * my + mz * mz;
+      float2 o = make_float2(0.0f, 0.0f);
+      if (m2 != 0) {
+        const float w = scale * __frcp_rn((float)m2);
+        o = make_float2(v[u].x * w, v[u].y * w);
       }
+      __stcs(sb + i, o);
     }
   }
 }
@@ -252,11 +248,14 @@ int seed_impl(const void* rhohat, int n, int batch, double L, const double* grad
   if (reinterpret_cast<uintptr_t>(rhohat) & 7u || reinterpret_cast<uintptr_t>(seed) & 7u)
     return FFT3D_ERR_MISALIGNED;
   const long long npts = (long long)n * n * (HALF ? n / 2 + 1 : n);
-  // about 2048 blocks in all, a warp per row of the spectrum at a time
-  const int bx = std::max(1, std::min((2048 + batch - 1) / batch, (n * n + 7) / 8));
+  // about 2048 blocks in all, no more than one step of U = 4 points per thread covers
+  const long long per_block = (long long)kRedThreads * 4;
+  const int bx = (int)std::max(1LL, std::min((long long)(2048 + batch - 1) / batch,
+                                            (npts + per_block - 1) / per_block));
   hartree_seed_kernel<HALF><<<dim3(bx, batch), kRedThreads, 0, static_cast<cudaStream_t>(stream)>>>(
       static_cast<const float2*>(rhohat), n, npts, hartree_s(n, L), grad_energy,
-      static_cast<float2*>(seed));
+      static_cast<float2*>(seed), make_fastdiv((unsigned)(HALF ? n / 2 + 1 : n)),
+      make_fastdiv((unsigned)n));
   if (cudaGetLastError() != cudaSuccess) return FFT3D_ERR_CUDA;
   return FFT3D_SUCCESS;
 }
