@@ -37,6 +37,15 @@ __host__ __device__ inline int energy_blocks(long long npts) {
 
 __device__ __forceinline__ int signed_index(int k, int n) { return k < (n + 1) / 2 ? k : k - n; }
 
+// 1 / x by the hardware's approximate reciprocal (within 1 ulp by the PTX
+// ISA's bound; the callers' x = |m|^2 is a positive integer below 2^24,
+// exact in FP32).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -59,11 +68,14 @@ __device__ __forceinline__ unsigned udiv(unsigned x, FastDiv d) {
 // and by n.  (Rows of n/2 + 1 points taken one warp at a time left a
 // third pass over each row with one lane of 32 busy: 0.41 of the HBM
 // bandwidth at 32 grids of 128^3.)  Each term |F(m)|^2 w / |m|^2 is
-// formed in FP32 (the correctly rounded reciprocal of |m|^2; relative
-// error <= 4 2^-24; the spectrum itself is FP32) and a thread's U terms of
-// a step are summed in FP32, then accumulated in FP64: FP64 work is a few
-// operations per hundred points, since FP64 runs at a small fraction of the
-// FP32 rate on this GPU (the per-point FP64 form ran at 0.39 TB/s).
+// formed in FP32 (the approximate reciprocal of |m|^2: one instruction
+// where the correctly rounded one takes several, and the loop is nearly
+// as much instruction work as memory traffic; a term's relative error
+// stays below 6 2^-24, against the FP32 rounding the spectrum already
+// carries) and a thread's U terms of a step are summed in FP32, then
+// accumulated in FP64: FP64 work is a few operations per hundred points,
+// since FP64 runs at a small fraction of the FP32 rate on this GPU (the
+// per-point FP64 form ran at 0.39 TB/s).
 template <bool HALF>
 __global__ void __launch_bounds__(kRedThreads) hartree_energy_kernel(
     const float2* __restrict__ f, int n, long long npts, double half_s,
@@ -92,7 +104,7 @@ __global__ void __launch_bounds__(kRedThreads) hartree_energy_kernel(
       const int m2 = mx * mx + my * my + mz * mz;
       const float w = HALF && kx != 0 && 2 * kx != n ? 2.0f : 1.0f;
       if (i < np && m2 > 0)
-        part = fmaf(fmaf(v[u].x, v[u].x, v[u].y * v[u].y), w * __frcp_rn((float)m2), part);
+        part = fmaf(fmaf(v[u].x, v[u].x, v[u].y * v[u].y), w * rcp_approx((float)m2), part);
     }
     acc += (double)part;
   }
@@ -124,6 +136,25 @@ __global__ void __launch_bounds__(kRedThreads) hartree_energy_kernel(
       counters[b] = 0u;
     }
   }
+}
+
+// Blocks of the energy kernel the device holds at once (one wave), found
+// once per process; 2048 if the runtime cannot say.
+template <bool HALF>
+int energy_resident_blocks() {
+  static const int r = [] {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hartree_energy_kernel<HALF>,
+                                                      kRedThreads, 0) != cudaSuccess ||
+        sms < 1 || per_sm < 1) {
+      cudaGetLastError();
+      return 2048;
+    }
+    return sms * per_sm;
+  }();
+  return r;
 }
 
 // The seed: the spectrum as a flat array, U points per thread per step at a
@@ -220,10 +251,12 @@ int energy_impl(const void* rhohat, int n, int batch, double L, double* energy, 
   if (reinterpret_cast<uintptr_t>(rhohat) & 7u || reinterpret_cast<uintptr_t>(workspace) & 7u)
     return FFT3D_ERR_MISALIGNED;
   const long long npts = (long long)n * n * (HALF ? n / 2 + 1 : n);
-  // about 2048 blocks in all (each ends with a fenced counter update, so
-  // many short blocks cost more than the points they read), at most the
-  // workspace's energy_blocks per grid
-  const int blocks = std::max(1, std::min(energy_blocks(npts), (2048 + batch - 1) / batch));
+  // one wave of resident blocks in all (each ends with a fenced counter
+  // update, so many short blocks cost more than the points they read; 2048
+  // blocks, 2.7 waves at 128^3 x 32, left the last wave a third empty), at
+  // most the workspace's energy_blocks per grid
+  const int blocks =
+      std::max(1, std::min(energy_blocks(npts), energy_resident_blocks<HALF>() / batch));
   const size_t partial_bytes = sizeof(double) * (size_t)batch * (size_t)energy_blocks(npts);
   unsigned char* ws = static_cast<unsigned char*>(workspace);
   unsigned* counters = reinterpret_cast<unsigned*>(ws + ((partial_bytes + 255) & ~size_t(255)));
