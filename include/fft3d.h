@@ -357,8 +357,11 @@ size_t fft3d_hartree_workspace_bytes(int n, int batch);
 
 /*
  * energy[b] = E_H of grid b, for `batch` spectra rhohat = F(rho) (device,
- * complex64, batch * n^3 points, 8-byte aligned).  Accumulated in FP64 in a
- * fixed order (bit-reproducible).  energy: DEVICE array of `batch` doubles.
+ * complex64, batch * n^3 points, 8-byte aligned).  Each term formed in FP32
+ * (relative error below 6 * 2^-24), eight at a time summed in FP32, those
+ * sums accumulated in FP64 in an order fixed by (n, batch) and the device
+ * (bit-reproducible from call to call).  energy: DEVICE array of `batch`
+ * doubles.
  * workspace: DEVICE buffer of at least fft3d_hartree_workspace_bytes(n,
  * batch) bytes, owned by the caller; it may be reused by later calls on the
  * same stream.  Asynchronous on `stream`.
