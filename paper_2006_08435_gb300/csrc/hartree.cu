@@ -138,27 +138,9 @@ __global__ void __launch_bounds__(kRedThreads) hartree_energy_kernel(
   }
 }
 
-// Blocks of the energy kernel the device holds at once (one wave), found
-// once per process; 2048 if the runtime cannot say.
-template <bool HALF>
-int energy_resident_blocks() {
-  static const int r = [] {
-    int dev = 0, sms = 0, per_sm = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hartree_energy_kernel<HALF>,
-                                                      kRedThreads, 0) != cudaSuccess ||
-        sms < 1 || per_sm < 1) {
-      cudaGetLastError();
-      return 2048;
-    }
-    return sms * per_sm;
-  }();
-  return r;
-}
-
 // The seed: the spectrum as a flat array, U points per thread per step at a
-// grid stride (coalesced loads and stores), indices as in the energy kernel.
+// grid stride (coalesced loads and stores), indices and reciprocal as in
+// the energy kernel.
 template <bool HALF>
 __global__ void __launch_bounds__(kRedThreads) hartree_seed_kernel(
     const float2* __restrict__ f, int n, long long npts, double s,
@@ -187,12 +169,32 @@ __global__ void __launch_bounds__(kRedThreads) hartree_seed_kernel(
       const int m2 = mx * mx + my * my + mz * mz;
       float2 o = make_float2(0.0f, 0.0f);
       if (m2 != 0) {
-        const float w = scale * __frcp_rn((float)m2);
+        const float w = scale * rcp_approx((float)m2);
         o = make_float2(v[u].x * w, v[u].y * w);
       }
       __stcs(sb + i, o);
     }
   }
+}
+
+// Blocks of the energy (SEED false) or seed kernel the device holds at
+// once (one wave), found once per process; 2048 if the runtime cannot say.
+template <bool HALF, bool SEED>
+int resident_blocks() {
+  static const int r = [] {
+    const void* fn = SEED ? reinterpret_cast<const void*>(hartree_seed_kernel<HALF>)
+                          : reinterpret_cast<const void*>(hartree_energy_kernel<HALF>);
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kRedThreads, 0) != cudaSuccess ||
+        sms < 1 || per_sm < 1) {
+      cudaGetLastError();
+      return 2048;
+    }
+    return sms * per_sm;
+  }();
+  return r;
 }
 
 __global__ void real_to_complex_kernel(const float* __restrict__ re, float2* __restrict__ out,
@@ -256,7 +258,7 @@ int energy_impl(const void* rhohat, int n, int batch, double L, double* energy, 
   // blocks, 2.7 waves at 128^3 x 32, left the last wave a third empty), at
   // most the workspace's energy_blocks per grid
   const int blocks =
-      std::max(1, std::min(energy_blocks(npts), energy_resident_blocks<HALF>() / batch));
+      std::max(1, std::min(energy_blocks(npts), resident_blocks<HALF, false>() / batch));
   const size_t partial_bytes = sizeof(double) * (size_t)batch * (size_t)energy_blocks(npts);
   unsigned char* ws = static_cast<unsigned char*>(workspace);
   unsigned* counters = reinterpret_cast<unsigned*>(ws + ((partial_bytes + 255) & ~size_t(255)));
@@ -281,9 +283,10 @@ int seed_impl(const void* rhohat, int n, int batch, double L, const double* grad
   if (reinterpret_cast<uintptr_t>(rhohat) & 7u || reinterpret_cast<uintptr_t>(seed) & 7u)
     return FFT3D_ERR_MISALIGNED;
   const long long npts = (long long)n * n * (HALF ? n / 2 + 1 : n);
-  // about 2048 blocks in all, no more than one step of U = 4 points per thread covers
+  // one wave of resident blocks in all, no more than one step of U = 4
+  // points per thread covers
   const long long per_block = (long long)kRedThreads * 4;
-  const int bx = (int)std::max(1LL, std::min((long long)(2048 + batch - 1) / batch,
+  const int bx = (int)std::max(1LL, std::min((long long)resident_blocks<HALF, true>() / batch,
                                             (npts + per_block - 1) / per_block));
   hartree_seed_kernel<HALF><<<dim3(bx, batch), kRedThreads, 0, static_cast<cudaStream_t>(stream)>>>(
       static_cast<const float2*>(rhohat), n, npts, hartree_s(n, L), grad_energy,
