@@ -8,7 +8,6 @@ mistake in the oracle (dropped term, wrong sign, transposed axis, wrong
 root of unity per axis) fails at least one of them.
 """
 import itertools
-import math
 
 import numpy as np
 import pytest

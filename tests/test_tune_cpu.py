@@ -3,8 +3,6 @@ timer: no GPU needed."""
 import ctypes
 import json
 
-import pytest
-
 from paper_2006_08435_gb300 import _lib as L
 
 
