@@ -344,3 +344,33 @@ def test_real_valid_args_reach_device_check(fft3d_lib):
         pytest.skip("has a GPU")
     rc, h = _create_real(fft3d_lib, 64, 3, 0, -1, 0)
     assert rc == L.FFT3D_ERR_NO_DEVICE and h is None
+
+
+def test_noalloc_validates_before_device(fft3d_lib):
+    f = fft3d_lib.fft3d_execute_noalloc
+    P = 1 << 20
+    fwd, none = L.FFT3D_FORWARD, L.FFT3D_NORM_NONE
+    assert f(64, 1, fwd, none, None, P, None) == L.FFT3D_ERR_NULL_PTR
+    assert f(64, 1, fwd, none, P, None, None) == L.FFT3D_ERR_NULL_PTR
+    assert f(64, 1, fwd, none, P + 8, P, None) == L.FFT3D_ERR_MISALIGNED  # 16-byte rule
+    assert f(64, 1, fwd, none, P, P + 8, None) == L.FFT3D_ERR_MISALIGNED
+    assert f(64, 1, 0, none, P, P, None) == L.FFT3D_ERR_INVALID_ARG
+    assert f(64, 1, fwd, 3, P, P, None) == L.FFT3D_ERR_INVALID_ARG
+    assert f(100, 1, fwd, none, P, P, None) == L.FFT3D_ERR_UNSUPPORTED_SIZE  # general path only
+    assert f(64, 0, fwd, none, P, P, None) == L.FFT3D_ERR_INVALID_ARG
+    for n in FUSED:
+        assert f(n, L.FFT3D_NOALLOC_MAX_BATCH + 1, fwd, none, P, P, None) == \
+            L.FFT3D_ERR_EXCEEDS_STATIC_SCRATCH
+
+
+def test_noalloc_limit_is_reachable(fft3d_lib):
+    """Every fused edge at the documented maximum batch passes the static
+    scratch check (and, without a GPU, stops at the device check)."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("has a GPU")
+    P = 1 << 20
+    for n in FUSED:
+        rc = fft3d_lib.fft3d_execute_noalloc(n, L.FFT3D_NOALLOC_MAX_BATCH, L.FFT3D_FORWARD,
+                                             L.FFT3D_NORM_NONE, P, P, None)
+        assert rc == L.FFT3D_ERR_NO_DEVICE, (n, rc)
