@@ -204,6 +204,17 @@ def test_synth_deterministic_and_in_range():
     assert (s >= 0.3).all() and (s <= 1.0).all() and (rho > 0).all()
 
 
+def test_hartree_density_holds_its_electrons():
+    """The density's grid sum times the cell volume per point is the total
+    charge: for normalised periodic Gaussians sampled at spacing h the
+    error is of order exp(-2 pi^2 sigma^2 / h^2) (Poisson summation), about
+    1e-8 at sigma >= 0.3 bohr and h = 10/32 bohr."""
+    for seed in (0, 1):
+        rho, _, _, w = synth.hartree_density(32, 10.0, seed=seed)
+        assert rho.sum() * (10.0 / 32) ** 3 == pytest.approx(w.sum(), rel=1e-6)
+        assert w.sum() == pytest.approx(128.0, rel=1e-12)
+
+
 # ------------------------------------------------ single outputs (dft3d_points)
 
 @pytest.mark.parametrize("shape", SHAPES_TINY + [(3, 4, 5)])
