@@ -8,7 +8,8 @@ than L2, so no flush is needed between steps).  Roofline bytes per
 transform = 16 * N^3 (one read and one write of the grid).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload 128x32|64x256|128x16|64x64|64x128|256x2] [--no-cpu-baseline]
+                  [--workload 128x32|64x256|128x16|64x64|64x128|256x2|96x16]
+                  [--no-cpu-baseline]
                   [--no-e2e] [--no-split] [--no-real] [--no-64] [--no-mixed] [--no-batch1]
                   [--no-general] [--no-hartree]
 
