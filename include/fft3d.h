@@ -72,7 +72,7 @@ typedef enum { FFT3D_NORM_NONE = 0, FFT3D_NORM_BY_N = 1, FFT3D_NORM_ORTHO = 2 } 
 enum {
   FFT3D_SUCCESS = 0,
   FFT3D_ERR_INVALID_ARG = -1,      /* a count, enum or plan handle is out of range */
-  FFT3D_ERR_UNSUPPORTED_SIZE = -2, /* an edge this build does not plan (see fft3d_size_supported) */
+  FFT3D_ERR_UNSUPPORTED_SIZE = -2, /* an edge the library does not plan (see fft3d_size_supported) */
   FFT3D_ERR_NULL_PTR = -3,         /* a required pointer is NULL */
   FFT3D_ERR_MISALIGNED = -4,       /* a data pointer is not 16-byte aligned */
   FFT3D_ERR_CUDA = -5,             /* a CUDA runtime call or kernel launch failed */

@@ -21,7 +21,7 @@ def make_fastdiv(fft3d_lib):
     try:
         f = getattr(fft3d_lib, "_ZN5fft3d12make_fastdivEj")  # fft3d::make_fastdiv(unsigned)
     except AttributeError:
-        pytest.skip("make_fastdiv is not an exported symbol of this build")
+        pytest.skip("make_fastdiv is not an exported symbol of the library")
     f.restype = _FastDiv
     f.argtypes = [ctypes.c_uint]
     return f
