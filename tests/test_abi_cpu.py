@@ -374,3 +374,49 @@ def test_noalloc_limit_is_reachable(fft3d_lib):
         rc = fft3d_lib.fft3d_execute_noalloc(n, L.FFT3D_NOALLOC_MAX_BATCH, L.FFT3D_FORWARD,
                                              L.FFT3D_NORM_NONE, P, P, None)
         assert rc == L.FFT3D_ERR_NO_DEVICE, (n, rc)
+
+
+def _header_declarations():
+    src = open(os.path.join(ROOT, "include", "fft3d.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for ret, name, params in re.findall(
+            r"([A-Za-z_][\w \t\*]*?)\b(fft3d_[a-z0-9_]+)\s*\(([^;{()]*)\)\s*;", src, flags=re.S):
+        ps = [" ".join(p.split()) for p in params.split(",")]
+        ps = [] if ps == ["void"] or ps == [""] else [re.sub(r"\s*\b\w+$", "", p) for p in ps]
+        out[name] = (" ".join(ret.split()), ps)
+    return out
+
+
+_P = ctypes.POINTER
+_C_TYPES = {
+    "int": {ctypes.c_int}, "size_t": {ctypes.c_size_t}, "int64_t": {ctypes.c_int64},
+    "double": {ctypes.c_double}, "const char*": {ctypes.c_char_p},
+    "int*": {_P(ctypes.c_int), ctypes.c_void_p}, "const int*": {_P(ctypes.c_int), ctypes.c_void_p},
+    "float*": {_P(ctypes.c_float), ctypes.c_void_p}, "const float*": {_P(ctypes.c_float), ctypes.c_void_p},
+    "double*": {_P(ctypes.c_double), ctypes.c_void_p},
+    "const double*": {_P(ctypes.c_double), ctypes.c_void_p},
+    "uint16_t*": {_P(ctypes.c_uint16), ctypes.c_void_p},
+    "int64_t*": {_P(ctypes.c_int64), ctypes.c_void_p},
+    "void*": {ctypes.c_void_p}, "const void*": {ctypes.c_void_p},
+    "void* const*": {ctypes.c_void_p, _P(ctypes.c_void_p)},
+    "const void* const*": {ctypes.c_void_p, _P(ctypes.c_void_p)},
+    "fft3d_plan": {ctypes.c_void_p}, "fft3d_real_plan": {ctypes.c_void_p},
+    "fft3d_plan*": {_P(ctypes.c_void_p)}, "fft3d_real_plan*": {_P(ctypes.c_void_p)},
+    "fft3d_tune_timer": {ctypes.c_void_p},
+}
+
+
+def test_binding_signatures_match_the_header():
+    """Every ctypes declaration of the binding has the header's argument
+    count and, per argument and result, a ctypes type of the C type's size
+    and kind (a mismatch would marshal garbage without any error)."""
+    decls = _header_declarations()
+    assert sorted(decls) == sorted(L._SIGS)
+    for name, (res, args) in L._SIGS.items():
+        cret, cparams = decls[name]
+        assert len(args) == len(cparams), (name, cparams)
+        assert res in _C_TYPES[cret], (name, cret, res)
+        for i, (a, c) in enumerate(zip(args, cparams)):
+            assert c in _C_TYPES, (name, c)
+            assert a in _C_TYPES[c], (name, i, c, a)
