@@ -349,6 +349,12 @@ int fft3d_autotune_mixed(int count, const int* dims, int direction, const char* 
  *   E_H = (Omega/2) sum_{G!=0} 4 pi |F(rho)(G)/n^3|^2 / |G|^2
  *       = (s/2) sum_{m!=0} |F(rho)(m)|^2 / |m|^2,
  *   dE_H/drho = Re F^H( s F(rho) / |m|^2 ).
+ * The energy and seed kernels each run one wave of the blocks the device
+ * holds at once: the first call of each of the four entry points in a
+ * process asks the runtime for that kernel's occupancy (with the call's
+ * device current), so make it before any stream capture.  Later calls
+ * allocate nothing, never synchronise and are capturable (the energy: a
+ * memset of its counters and one kernel; the seed: one kernel).
  * ---------------------------------------------------------------------------
  */
 
