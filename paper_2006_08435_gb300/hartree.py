@@ -9,7 +9,10 @@ works on half spectra: real-grid forward transform, FP64 energy reduction
 over the half spectrum (mirrored points counted twice); seed on the half
 spectrum, real-grid inverse transform.  For odd n: real->complex, complex
 forward transform, full-spectrum reduction; seed, complex inverse,
-complex->real.
+complex->real.  To capture a step in a CUDA graph, run it once eagerly
+first with the same shapes and stream: that call allocates the reduction
+workspace and the transform plans and has the library query its kernels'
+occupancy, none of which belongs in a capture.
 """
 from __future__ import annotations
 
