@@ -609,18 +609,22 @@ int launch(fft3d_plan p, const float2* in, float2* out, const float2* const* in_
     cudaGetLastError();
     return FFT3D_ERR_CUDA;
   }
+  int rc = FFT3D_SUCCESS;
   for (size_t i = units.size(); i-- > 0;) {
     if (cudaStreamWaitEvent(p->side[i], p->fork, 0) != cudaSuccess) {
       cudaGetLastError();
       return FFT3D_ERR_CUDA;
     }
-    const int rc = launch_unit(p, units[i], in, out, in_ptrs, out_ptrs, p->side[i]);
-    if (rc) return rc;
+    rc = launch_unit(p, units[i], in, out, in_ptrs, out_ptrs, p->side[i]);
+    // a forked branch is joined even when its launch failed: the caller's
+    // stream then still waits for every branch already launched, and a
+    // capture does not end with an unjoined stream
     if (cudaEventRecord(p->join[i], p->side[i]) != cudaSuccess ||
         cudaStreamWaitEvent(stream, p->join[i], 0) != cudaSuccess) {
       cudaGetLastError();
-      return FFT3D_ERR_CUDA;
+      if (!rc) rc = FFT3D_ERR_CUDA;
     }
+    if (rc) return rc;
   }
   return FFT3D_SUCCESS;
 }
